@@ -1,0 +1,102 @@
+"""FP64 CPU oracle of the stencil tendencies (test infrastructure only).
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may import
+this package.  The product path (paper_2303_12374_gb300) never does; the two
+share no code.  `build()` compiles oracle.c with gcc into oracle/_build/.
+
+Arrays are numpy float64 in (nz, ny, nx) order (x fastest), interior only,
+unless a name says "padded".
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c (plain C, FP64, no FMA contraction) into a shared library."""
+    src = os.path.join(_HERE, "oracle.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        os.makedirs(os.path.dirname(_SO), exist_ok=True)
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                               "-shared", "-o", tmp, src, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_SO)
+        dp = ctypes.POINTER(ctypes.c_double)
+        lib.or_zprofile.argtypes = [ctypes.c_int] * 3 + [dp, dp, dp]
+        lib.or_fill_ghosts.argtypes = [ctypes.c_int] * 6 + [dp]
+        lib.or_tendency.argtypes = ([ctypes.c_int] * 5 + [ctypes.c_double] * 2 + [dp, dp]
+                                    + [ctypes.c_int] * 2 + [ctypes.c_double] + [dp] * 7)
+        lib.or_diag.argtypes = [ctypes.c_size_t, dp, dp, dp, dp]
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def zprofile(nz: int, g: int, walls: bool, zh: np.ndarray):
+    """dz_k and dzh_k for k in [-g, nz+g), index k+g."""
+    lib = _load()
+    zh = np.ascontiguousarray(zh, dtype=np.float64)
+    dz = np.empty(nz + 2 * g)
+    dzh = np.empty(nz + 2 * g)
+    lib.or_zprofile(nz, g, int(walls), _p(zh), _p(dz), _p(dzh))
+    return dz, dzh
+
+
+def pad(a: np.ndarray, g: int, walls: bool, odd: bool) -> np.ndarray:
+    """Padded copy of an interior field with its ghost cells filled."""
+    lib = _load()
+    nz, ny, nx = a.shape
+    out = np.zeros((nz + 2 * g, ny + 2 * g, nx + 2 * g))
+    out[g:g + nz, g:g + ny, g:g + nx] = a
+    lib.or_fill_ghosts(nx, ny, nz, g, int(walls), int(odd), _p(out))
+    return out
+
+
+def tendencies(u, v, w, *, adv: int, diff: int, g: int, walls: bool, dx: float,
+               dy: float, zh: np.ndarray, nu: float = 0.0, nu_field=None):
+    """(ut, vt, wt) on the interior; inputs are interior fields (nz, ny, nx)."""
+    lib = _load()
+    nz, ny, nx = u.shape
+    u, v, w = (np.ascontiguousarray(x, dtype=np.float64) for x in (u, v, w))
+    up, vp, wp = pad(u, g, walls, False), pad(v, g, walls, False), pad(w, g, walls, True)
+    np_ = pad(np.ascontiguousarray(nu_field, dtype=np.float64), g, walls, False) \
+        if nu_field is not None else None
+    dz, dzh = zprofile(nz, g, walls, zh)
+    ut, vt, wt = (np.empty((nz, ny, nx)) for _ in range(3))
+    lib.or_tendency(nx, ny, nz, g, int(walls), dx, dy, _p(dz), _p(dzh), adv, diff, nu,
+                    _p(up), _p(vp), _p(wp), _p(np_), _p(ut), _p(vt), _p(wt))
+    return ut, vt, wt
+
+
+def diag(t: np.ndarray, ref: np.ndarray | None = None, wgt: np.ndarray | None = None):
+    """[max|t-r|, rms(t-r), max|r|, rms(r), sum t, sum t*wgt] in FP64."""
+    lib = _load()
+    t = np.ascontiguousarray(t, dtype=np.float64).ravel()
+    r = None if ref is None else np.ascontiguousarray(ref, dtype=np.float64).ravel()
+    wv = None if wgt is None else np.ascontiguousarray(wgt, dtype=np.float64).ravel()
+    out = np.zeros(6)
+    lib.or_diag(t.size, _p(t), _p(r), _p(wv), _p(out))
+    return out
