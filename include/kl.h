@@ -1,0 +1,233 @@
+/*
+ * kl.h -- C ABI of libkl: tunable structured-grid stencil tendencies with
+ * capture, tuning, wisdom files and run-time (NVRTC) kernel selection.
+ *
+ * The operations follow the workflow of Kernel Launcher (Heldens et al.,
+ * arXiv 2303.12374): a kernel definition with a configuration space (Sec. 4.1),
+ * capturing a launch so it can be replayed offline (Sec. 4.2), tuning it
+ * (Sec. 4.3) into a wisdom file of per-device, per-problem-size records
+ * (Sec. 4.4), and, at launch, selecting a record and compiling it at run time
+ * with NVRTC, cached per problem size (Sec. 4.5).  The kernels are the CFD
+ * stencils the paper tunes (Sec. 5.2: MicroHH advec_u and diff_uvw),
+ * generalised to the u, v, w momentum tendencies.
+ *
+ * Conventions for every call:
+ *  - Device pointers are CUDA global-memory pointers on the context's device;
+ *    host pointers are ordinary process memory.  Each argument says which.
+ *  - The caller owns every buffer and stream; the library owns contexts,
+ *    compiled modules, internal device buffers and returned strings.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    asynchronous on that stream unless their comment says they synchronise.
+ *  - Errors are returned, never aborted on; kl_last_error() gives the text.
+ *    Arguments are validated on the host before any launch; a rejected call
+ *    launches nothing.
+ *  - Not thread-safe per context: use one context per host thread, or
+ *    serialise calls on a shared context.
+ */
+#ifndef KL_H
+#define KL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int kl_status;
+#define KL_OK                0
+#define KL_ERR_INVALID_ARG  -1   /* bad pointer, size, stride, option or config */
+#define KL_ERR_CUDA         -2   /* a CUDA runtime/driver call failed */
+#define KL_ERR_NVRTC        -3   /* run-time compilation failed; log in kl_last_error */
+#define KL_ERR_IO           -4   /* a file could not be read or written */
+#define KL_ERR_WISDOM_PARSE -5   /* malformed wisdom or capture file */
+#define KL_ERR_UNSUPPORTED  -6   /* valid request this build or device cannot run */
+#define KL_ERR_BOUNDS       -7   /* strides/extent do not hold the stencil footprint */
+#define KL_ERR_TIMEOUT      -8   /* a bounded device wait gave up */
+#define KL_ERR_OOM          -9   /* a library-internal allocation failed */
+
+typedef enum { KL_F64 = 0, KL_F32 = 1, KL_BF16 = 2, KL_F16 = 3 } kl_dtype;
+
+/*
+ * What to compute.  adv: 0 none, 2 centred 2nd-order, 5 upwind-biased
+ * 5th-order interpolation in flux-form momentum advection ("second order
+ * advection scheme with fifth order interpolation", Sec. 5.2).  diff: 0 none,
+ * 1 constant-nu Laplacian, 2 variable-nu stress divergence (the Smagorinsky
+ * diffusion of Sec. 5.2 with a given nu field).  dtype: storage type of every
+ * field; f64 computes in f64, the others in f32.  accumulate: 0 writes
+ * t = tendency, 1 adds t += tendency.
+ */
+typedef struct {
+    int32_t adv;
+    int32_t diff;
+    int32_t dtype;
+    int32_t accumulate;
+} kl_op;
+
+/*
+ * Grid and memory layout, shared by every field of a call.
+ * Interior points i in [0,nx), j in [0,ny), k in [0,nz); g ghost cells on each
+ * side of every axis (g >= 3 for adv = 5, g >= 1 otherwise).  Element
+ * (i,j,k) of a field lives at base[origin + i + j*sj + k*sk] (x stride 1);
+ * negative i, j, k down to -g and up to n-1+g address the ghosts.  extent is
+ * the number of elements of each buffer; every addressed element must lie in
+ * [0, extent) and extent must be < 2^31.  Staggering is Arakawa C: u at
+ * (i dx, (j+1/2) dy, z_k), v at ((i+1/2) dx, j dy, z_k), w at ((i+1/2) dx,
+ * (j+1/2) dy, zh_k), nu at cell centres.  x and y are periodic; zbc = 0
+ * periodic z, zbc = 1 free-slip walls at zh_0 and zh_nz (w = 0 there; the w
+ * value stored at k = 0 must be 0).  zh (HOST, nz+1 face heights, increasing)
+ * gives a stretched grid; zh = NULL means uniform spacing dz.  nu is the
+ * constant viscosity for diff = 1.
+ */
+typedef struct {
+    int32_t nx, ny, nz;
+    int32_t g;
+    int64_t sj, sk;
+    int64_t origin;
+    int64_t extent;
+    int32_t zbc;
+    int32_t reserved;
+    double dx, dy, dz;
+    double nu;
+    const double *zh;
+} kl_grid;
+
+/* Device pointers to the base (element 0) of each buffer.  nu is read only
+ * for diff = 2 (may be NULL otherwise).  Outputs are written on interior
+ * points only; their ghosts are untouched. */
+typedef struct {
+    const void *u, *v, *w, *nu;
+    void *ut, *vt, *wt;
+} kl_fields;
+
+typedef struct kl_ctx kl_ctx;
+
+/* Create a context on CUDA device `device`.  wisdom_dir (host string, may be
+ * NULL) is where kl_launch looks for wisdom files; NULL uses $KL_WISDOM_DIR,
+ * else no wisdom (default configurations).  *out receives the context. */
+kl_status kl_create(kl_ctx **out, int device, const char *wisdom_dir);
+
+/* Free the context: unloads compiled modules, frees internal device buffers.
+ * Synchronises the device.  NULL is ignored. */
+void kl_destroy(kl_ctx *ctx);
+
+/* Text of the last error on this host thread (library-owned, never NULL). */
+const char *kl_last_error(void);
+
+/* Recommended layout for a field (host arithmetic only): the interior x start
+ * and the row pitch are 128-byte aligned.  Writes sj, sk, origin, extent. */
+kl_status kl_layout(int32_t nx, int32_t ny, int32_t nz, int32_t g, int32_t dtype,
+                    int64_t *sj, int64_t *sk, int64_t *origin, int64_t *extent);
+
+/*
+ * Fill the ghost cells of u, v, w (and nu when non-NULL) in place (device
+ * pointers, layout `grid`, storage `dtype`): periodic copies in x and y (and z
+ * for zbc = 0); at walls u, v, nu are mirrored evenly, w oddly with w = 0 on
+ * the top wall face.  Every ghost point is copied straight from an interior
+ * point, so edges and corners are filled in the same single launch.
+ */
+kl_status kl_fill_ghosts(kl_ctx *ctx, int32_t dtype, const kl_grid *grid,
+                         void *u, void *v, void *w, void *nu, void *stream);
+
+/*
+ * Tendencies ut, vt, wt of (u, v, w) on the interior (Sec. 5.2 stencils),
+ * ghosts of the inputs already filled.  The configuration is selected from
+ * the wisdom file of (op, dtype) by the heuristic of Sec. 4.5 and compiled
+ * with NVRTC on the first call per problem size; later calls reuse it.
+ */
+kl_status kl_launch(kl_ctx *ctx, const kl_op *op, const kl_grid *grid,
+                    const kl_fields *fields, void *stream);
+
+/* As kl_launch with an explicit configuration string (see kl_config_help);
+ * "default" is the untuned default configuration. */
+kl_status kl_launch_with_config(kl_ctx *ctx, const kl_op *op, const char *config,
+                                const kl_grid *grid, const kl_fields *fields, void *stream);
+
+/*
+ * n independent grids (HOST arrays grids[n], fields[n]) of one op: each grid
+ * gets the configuration of its nearest tuned size (Sec. 4.5 fuzzy matching,
+ * Sec. 6), grids sharing a configuration run in one launch over a device tile
+ * table, and the launches of all size classes are issued on `stream`.
+ */
+kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_grid *grids,
+                            const kl_fields *fields, void *stream);
+
+/*
+ * Capture (Sec. 4.2): synchronise `stream`, copy every input buffer of the
+ * launch device->host and write the definition, problem, layout, scalars and
+ * data to `path` (host string).  The launch can then be replayed by kl_tune.
+ * If $KERNEL_LAUNCHER_CAPTURE lists "tendency" (comma-separated), kl_launch
+ * captures into $KL_CAPTURE_DIR (default ".") before it launches.
+ */
+kl_status kl_capture(kl_ctx *ctx, const kl_op *op, const kl_grid *grid,
+                     const kl_fields *fields, const char *path, void *stream);
+
+/*
+ * Tune (Sec. 4.3): replay the capture at capture_path, search the
+ * configuration space with the strategy in opts (host string of key=value
+ * pairs: strategy=random|exhaustive|local, budget_s, max_evals, seed,
+ * family=direct|zmarch|all, verify_tol, log=<path of a JSON-lines log>),
+ * verify each candidate against the default configuration's output, and
+ * append the best record with provenance to the wisdom file wisdom_path.
+ * Synchronous; uses its own device buffers.
+ */
+kl_status kl_tune(kl_ctx *ctx, const char *capture_path, const char *opts,
+                  const char *wisdom_path);
+
+/*
+ * FP64 diagnostics on the device of a tendency t (device, layout grid, type
+ * dtype) against ref (device, same layout, f64; NULL = zero), over the
+ * interior: out[6] (host) = {max|t-ref|, rms(t-ref), max|ref|, rms(ref),
+ * sum t, sum t*dz}, dz = dz_k (level = 0) or dzh_k (level = 1, w points).
+ * Synchronises `stream`.
+ */
+kl_status kl_diag(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, int32_t level,
+                  const void *t, const double *ref, double out[6], void *stream);
+
+/* Context statistics as JSON into buf (host, n bytes): cache hits/misses,
+ * the four first-launch stage times of Sec. 5.6 (wisdom read, NVRTC,
+ * module load, launch), launches, and the last selected record. */
+kl_status kl_stats(kl_ctx *ctx, char *buf, size_t n);
+
+/* ---- host-only helpers (no GPU needed) -------------------------------- */
+
+/* Normalised text of a configuration ("default" expands to the default of
+ * Table 2) into buf; KL_ERR_INVALID_ARG if it violates the space's
+ * constraints for op.  family: 0 direct, 1 zmarch. */
+kl_status kl_config_normalize(const kl_op *op, const char *config, char *buf, size_t n);
+
+/* Number of configurations of the declared space for op and family, and the
+ * idx-th (0-based, constraint-satisfying ones first counted) into buf. */
+kl_status kl_space_size(const kl_op *op, int32_t family, int64_t *count);
+kl_status kl_space_config(const kl_op *op, int32_t family, int64_t idx, char *buf, size_t n);
+
+/* Compile a configuration with NVRTC for sm_103a without loading it; the
+ * compiler log (with ptxas register/spill lines) goes to log (host, n). */
+kl_status kl_compile_only(const kl_op *op, const char *config, int32_t zbc, int32_t zuni,
+                          char *log, size_t n);
+
+/*
+ * Wisdom selection (Sec. 4.5) over the file at path: the record matching
+ * device name and size; else the same device, nearest size (Euclidean);
+ * else the same architecture (compute capability), nearest size; else any
+ * record, nearest size; else (empty, missing or unreadable file) the
+ * default.  Records of another zbc are never chosen.  Writes the chosen
+ * configuration to cfg (host, n) and the rule that fired (1..5) to *rule.
+ */
+kl_status kl_wisdom_select(const char *path, const char *device, int32_t cc_major,
+                           int32_t cc_minor, int32_t zbc, int32_t nx, int32_t ny, int32_t nz,
+                           char *cfg, size_t n, int32_t *rule);
+
+/* Append one record (host strings) to the wisdom file at path, creating it. */
+kl_status kl_wisdom_append(const char *path, const char *device, int32_t cc_major,
+                           int32_t cc_minor, int32_t zbc, int32_t nx, int32_t ny, int32_t nz,
+                           const char *config, double time_us, const char *extra);
+
+/* Library version string (static). */
+const char *kl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KL_H */

@@ -42,7 +42,8 @@ def _load():
         lib.or_zprofile.argtypes = [ctypes.c_int] * 3 + [dp, dp, dp]
         lib.or_fill_ghosts.argtypes = [ctypes.c_int] * 6 + [dp]
         lib.or_tendency.argtypes = ([ctypes.c_int] * 5 + [ctypes.c_double] * 2 + [dp, dp]
-                                    + [ctypes.c_int] * 2 + [ctypes.c_double] + [dp] * 7)
+                                    + [ctypes.c_int] * 2 + [ctypes.c_double] + [dp] * 4
+                                    + [ctypes.c_int] * 2 + [dp] * 3)
         lib.or_diag.argtypes = [ctypes.c_size_t, dp, dp, dp, dp]
         _lib = lib
     return _lib
@@ -76,8 +77,12 @@ def pad(a: np.ndarray, g: int, walls: bool, odd: bool) -> np.ndarray:
 
 
 def tendencies(u, v, w, *, adv: int, diff: int, g: int, walls: bool, dx: float,
-               dy: float, zh: np.ndarray, nu: float = 0.0, nu_field=None):
-    """(ut, vt, wt) on the interior; inputs are interior fields (nz, ny, nx)."""
+               dy: float, zh: np.ndarray, nu: float = 0.0, nu_field=None, levels=None):
+    """(ut, vt, wt) on the interior; inputs are interior fields (nz, ny, nx).
+
+    levels=(k0, k1) computes only interior levels k0 <= k < k1 (outputs of
+    shape (k1-k0, ny, nx)); the default is every level.
+    """
     lib = _load()
     nz, ny, nx = u.shape
     u, v, w = (np.ascontiguousarray(x, dtype=np.float64) for x in (u, v, w))
@@ -85,9 +90,11 @@ def tendencies(u, v, w, *, adv: int, diff: int, g: int, walls: bool, dx: float,
     np_ = pad(np.ascontiguousarray(nu_field, dtype=np.float64), g, walls, False) \
         if nu_field is not None else None
     dz, dzh = zprofile(nz, g, walls, zh)
-    ut, vt, wt = (np.empty((nz, ny, nx)) for _ in range(3))
+    k0, k1 = (0, nz) if levels is None else levels
+    assert 0 <= k0 < k1 <= nz
+    ut, vt, wt = (np.empty((k1 - k0, ny, nx)) for _ in range(3))
     lib.or_tendency(nx, ny, nz, g, int(walls), dx, dy, _p(dz), _p(dzh), adv, diff, nu,
-                    _p(up), _p(vp), _p(wp), _p(np_), _p(ut), _p(vt), _p(wt))
+                    _p(up), _p(vp), _p(wp), _p(np_), k0, k1, _p(ut), _p(vt), _p(wt))
     return ut, vt, wt
 
 

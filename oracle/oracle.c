@@ -310,22 +310,23 @@ static double Syz(const dctx *D, int i, int j, int k)
 /* ------------------------------------------------------------ tendencies */
 
 /*
- * ut, vt, wt (interior, nx*ny*nz, x fastest) from padded u, v, w (and nu for
- * diff = 2) whose ghosts are already filled.  With walls, wt = 0 at k = 0.
+ * ut, vt, wt on interior levels k0 <= k < k1 (arrays of (k1-k0)*ny*nx, x
+ * fastest) from padded u, v, w (and nu for diff = 2) whose ghosts are already
+ * filled.  With walls, wt = 0 at k = 0.
  */
 void or_tendency(int nx, int ny, int nz, int g, int zbc, double dx, double dy,
                  const double *dz, const double *dzh, int adv, int diff, double nu,
                  const double *u, const double *v, const double *w, const double *nuf,
-                 double *ut, double *vt, double *wt)
+                 int k0, int k1, double *ut, double *vt, double *wt)
 {
     ogrid G = {nx, ny, nz, g, zbc, dx, dy, dz, dzh};
     actx A = {&G, u, v, w, adv};
     dctx D = {&G, u, v, w, nuf};
     const actx *C = &A;
-    for (int k = 0; k < nz; ++k)
+    for (int k = k0; k < k1; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
-                size_t o = (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * (size_t)k);
+                size_t o = (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * (size_t)(k - k0));
                 double tu = 0.0, tv = 0.0, tw = 0.0;
                 double dzk = dz[k + g], dzhk = dzh[k + g];
                 int wall_w = (zbc == 1 && k == 0);

@@ -1,0 +1,679 @@
+// kl_api.cpp -- contexts, run-time compilation and module cache, launches,
+// ghost fill and diagnostics entry points of the C ABI.
+#include <nvrtc.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <sstream>
+
+#include "kl_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+// NVRTC source of the tendency kernels, embedded at build time.
+const char *kSource =
+#include "kl_source.inc"
+    ;
+
+double ms_since(std::chrono::steady_clock::time_point t0)
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+bool env_lists(const char *var, const char *name)
+{
+    const char *v = getenv(var);
+    if (!v) return false;
+    std::stringstream ss(v);
+    std::string item;
+    while (std::getline(ss, item, ','))
+        if (item == name || item == "*") return true;
+    return false;
+}
+
+}  // namespace
+
+namespace kl {
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+kl_status fail(kl_status code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+kl_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(KL_ERR_CUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" +
+                                 cudaGetErrorString(e) + ")");
+}
+
+kl_status cu_fail(CUresult r, const char *what)
+{
+    return fail(KL_ERR_CUDA, std::string(what) + ": CUresult " + std::to_string((int)r));
+}
+
+// ------------------------------------------------------------ driver API
+
+kl_status driver_load(Driver *d)
+{
+    struct Sym {
+        const char *name;
+        void **slot;
+    } syms[] = {
+        {"cuModuleLoadData", (void **)&d->ModuleLoadData},
+        {"cuModuleUnload", (void **)&d->ModuleUnload},
+        {"cuModuleGetFunction", (void **)&d->ModuleGetFunction},
+        {"cuLaunchKernel", (void **)&d->LaunchKernel},
+        {"cuFuncSetAttribute", (void **)&d->FuncSetAttribute},
+        {"cuFuncGetAttribute", (void **)&d->FuncGetAttribute},
+        {"cuTensorMapEncodeTiled", (void **)&d->TensorMapEncodeTiled},
+    };
+    for (auto &s : syms) {
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion(s.name, s.slot, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !*s.slot)
+            return fail(KL_ERR_CUDA, std::string("driver entry point not found: ") + s.name);
+    }
+    return KL_OK;
+}
+
+// ------------------------------------------------------------- NVRTC
+
+kl_status nvrtc_compile(const std::string &defines, bool verbose, Compiled *out)
+{
+    nvrtcProgram prog;
+    nvrtcResult r = nvrtcCreateProgram(&prog, kSource, "kl_stencil.cu", 0, nullptr, nullptr);
+    if (r != NVRTC_SUCCESS) return fail(KL_ERR_NVRTC, nvrtcGetErrorString(r));
+    std::vector<std::string> opts = {"-arch=sm_103a", "-std=c++17", "-lineinfo"};
+    if (verbose) opts.push_back("--ptxas-options=-v");
+    std::stringstream ss(defines);
+    std::string tok;
+    while (ss >> tok) opts.push_back(tok);
+    std::vector<const char *> cops;
+    for (auto &o : opts) cops.push_back(o.c_str());
+    r = nvrtcCompileProgram(prog, (int)cops.size(), cops.data());
+    size_t logn = 0;
+    nvrtcGetProgramLogSize(prog, &logn);
+    out->log.assign(logn, '\0');
+    if (logn) nvrtcGetProgramLog(prog, &out->log[0]);
+    while (!out->log.empty() && out->log.back() == '\0') out->log.pop_back();
+    if (r != NVRTC_SUCCESS) {
+        nvrtcDestroyProgram(&prog);
+        return fail(KL_ERR_NVRTC, std::string("NVRTC: ") + nvrtcGetErrorString(r) + "\n" +
+                                      defines + "\n" + out->log);
+    }
+    size_t n = 0;
+    nvrtcGetCUBINSize(prog, &n);
+    out->cubin.resize(n);
+    nvrtcGetCUBIN(prog, out->cubin.data());
+    nvrtcDestroyProgram(&prog);
+    return KL_OK;
+}
+
+// ------------------------------------------------------ kernel cache
+
+kl_status get_kernel(kl_ctx *ctx, const kl_op &op, const Config &cfg, int zbc, int zuni,
+                     Kernel **out)
+{
+    std::string key = compile_defines(op, cfg, zbc, zuni);
+    auto it = ctx->kernels.find(key);
+    if (it != ctx->kernels.end()) {
+        *out = &it->second;
+        return KL_OK;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    Compiled c;
+    kl_status st = nvrtc_compile(key, false, &c);
+    if (st) return st;
+    ctx->t_nvrtc_ms += ms_since(t0);
+    auto t1 = std::chrono::steady_clock::now();
+    Kernel k;
+    k.cfg = cfg;
+    CUresult r = ctx->drv.ModuleLoadData(&k.mod, c.cubin.data());
+    if (r != CUDA_SUCCESS) return cu_fail(r, "cuModuleLoadData");
+    r = ctx->drv.ModuleGetFunction(&k.fn, k.mod, "kl_tendency");
+    if (r != CUDA_SUCCESS) {
+        ctx->drv.ModuleUnload(k.mod);
+        return cu_fail(r, "cuModuleGetFunction");
+    }
+    ctx->drv.FuncGetAttribute(&k.nregs, CU_FUNC_ATTRIBUTE_NUM_REGS, k.fn);
+    ctx->drv.FuncGetAttribute(&k.local_bytes, CU_FUNC_ATTRIBUTE_LOCAL_SIZE_BYTES, k.fn);
+    if (cfg.family == 1) {
+        k.smem = zmarch_smem_bytes(op, cfg);
+        r = ctx->drv.FuncSetAttribute(k.fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES,
+                                      (int)k.smem);
+        if (r != CUDA_SUCCESS) {
+            ctx->drv.ModuleUnload(k.mod);
+            return cu_fail(r, "cuFuncSetAttribute(max dynamic smem)");
+        }
+    }
+    ctx->t_load_ms += ms_since(t1);
+    ctx->cache_misses++;
+    auto ins = ctx->kernels.emplace(key, k);
+    *out = &ins.first->second;
+    return KL_OK;
+}
+
+// ----------------------------------------------------- z profiles
+
+kl_status get_profile(kl_ctx *ctx, const kl_grid &g, Profile **out)
+{
+    // key: z grid description (content hash of zh, FNV-1a)
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void *p, size_t n) {
+        const unsigned char *b = (const unsigned char *)p;
+        for (size_t q = 0; q < n; ++q) h = (h ^ b[q]) * 1099511628211ull;
+    };
+    mix(&g.nz, sizeof g.nz);
+    mix(&g.g, sizeof g.g);
+    mix(&g.zbc, sizeof g.zbc);
+    if (g.zh) mix(g.zh, sizeof(double) * (size_t)(g.nz + 1));
+    else mix(&g.dz, sizeof g.dz);
+    std::string key = std::to_string(h) + (g.zh ? "s" : "u");
+    auto it = ctx->profiles.find(key);
+    if (it != ctx->profiles.end()) {
+        *out = &it->second;
+        return KL_OK;
+    }
+    std::vector<double> dzi, dzhi;
+    zprofile_host(g.nz, g.g, g.zbc, g.zh, g.dz, &dzi, &dzhi);
+    int n = g.nz + 2 * g.g;
+    // d64: dzi | dzhi | dz | dzh ; d32: dzi | dzhi
+    std::vector<double> h64(4 * (size_t)n);
+    std::vector<float> h32(2 * (size_t)n);
+    for (int q = 0; q < n; ++q) {
+        h64[q] = dzi[q];
+        h64[n + q] = dzhi[q];
+        h64[2 * n + q] = 1.0 / dzi[q];
+        h64[3 * n + q] = 1.0 / dzhi[q];
+        h32[q] = (float)dzi[q];
+        h32[n + q] = (float)dzhi[q];
+    }
+    Profile p;
+    p.n = n;
+    cudaError_t e = cudaMalloc(&p.d64, sizeof(double) * h64.size());
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(profile)");
+    e = cudaMalloc(&p.d32, sizeof(float) * h32.size());
+    if (e != cudaSuccess) {
+        cudaFree(p.d64);
+        return cuda_fail(e, "cudaMalloc(profile)");
+    }
+    e = cudaMemcpy(p.d64, h64.data(), sizeof(double) * h64.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p.d32, h32.data(), sizeof(float) * h32.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(p.d64);
+        cudaFree(p.d32);
+        return cuda_fail(e, "cudaMemcpy(profile)");
+    }
+    auto ins = ctx->profiles.emplace(key, p);
+    *out = &ins.first->second;
+    return KL_OK;
+}
+
+// ------------------------------------------------------------ launch
+
+static kl_status check_op(const kl_op *op)
+{
+    if (!op) return fail(KL_ERR_INVALID_ARG, "op is NULL");
+    if (op->adv != 0 && op->adv != 2 && op->adv != 5)
+        return fail(KL_ERR_INVALID_ARG, "adv must be 0, 2 or 5");
+    if (op->diff < 0 || op->diff > 2) return fail(KL_ERR_INVALID_ARG, "diff must be 0, 1 or 2");
+    if (op->dtype < KL_F64 || op->dtype > KL_F16)
+        return fail(KL_ERR_INVALID_ARG, "dtype must be 0..3");
+    if (op->accumulate != 0 && op->accumulate != 1)
+        return fail(KL_ERR_INVALID_ARG, "accumulate must be 0 or 1");
+    return KL_OK;
+}
+
+static kl_status check_fields(const kl_op &op, const kl_fields *f)
+{
+    if (!f) return fail(KL_ERR_INVALID_ARG, "fields is NULL");
+    if (!f->u || !f->v || !f->w || !f->ut || !f->vt || !f->wt)
+        return fail(KL_ERR_INVALID_ARG, "a field pointer is NULL");
+    if (op.diff == 2 && !f->nu) return fail(KL_ERR_INVALID_ARG, "diff = 2 needs the nu field");
+    int es = esize_of(op.dtype);
+    const void *ps[] = {f->u, f->v, f->w, f->ut, f->vt, f->wt, op.diff == 2 ? f->nu : f->u};
+    for (const void *p : ps)
+        if ((uintptr_t)p % (uintptr_t)es) return fail(KL_ERR_INVALID_ARG, "misaligned field pointer");
+    return KL_OK;
+}
+
+static void fill_coefs(KArgs &a, const kl_grid &g)
+{
+    double dzi = g.zh ? 0.0 : 1.0 / g.dz;
+    double c[8] = {1.0 / g.dx, 1.0 / g.dy, dzi, dzi, g.nu, g.nu / (g.dx * g.dx),
+                   g.nu / (g.dy * g.dy), 0.0};
+    for (int q = 0; q < 8; ++q) {
+        a.cd[q] = c[q];
+        a.cf[q] = (float)c[q];
+    }
+}
+
+kl_status launch_config(kl_ctx *ctx, const kl_op &op, const Config &cfg, const kl_grid &g,
+                        const kl_fields &f, cudaStream_t s)
+{
+    std::string err;
+    if (!config_check(op, cfg, &err)) return fail(KL_ERR_INVALID_ARG, "configuration: " + err);
+    Geom geo;
+    kl_status st = check_grid(&g, halo_of(op), &geo);
+    if (st) return st;
+    int zuni = g.zh ? 0 : 1;
+    Profile *prof = nullptr;
+    if (!zuni) {
+        st = get_profile(ctx, g, &prof);
+        if (st) return st;
+    }
+    Kernel *k = nullptr;
+    auto t0 = std::chrono::steady_clock::now();
+    bool miss = ctx->kernels.find(compile_defines(op, cfg, g.zbc, zuni)) == ctx->kernels.end();
+    st = get_kernel(ctx, op, cfg, g.zbc, zuni, &k);
+    if (st) return st;
+    if (!miss) ctx->cache_hits++;
+
+    int es = esize_of(op.dtype);
+    KArgs a;
+    memset(&a, 0, sizeof a);
+    const char *base[7] = {(const char *)f.u, (const char *)f.v, (const char *)f.w,
+                           (const char *)f.nu, (const char *)f.ut, (const char *)f.vt,
+                           (const char *)f.wt};
+    size_t off = (size_t)g.origin * es;
+    a.u = base[0] + off;
+    a.v = base[1] + off;
+    a.w = base[2] + off;
+    a.nu = f.nu ? base[3] + off : nullptr;
+    a.ut = (void *)(base[4] + off);
+    a.vt = (void *)(base[5] + off);
+    a.wt = (void *)(base[6] + off);
+    if (prof) {
+        if (op.dtype == KL_F64) {
+            a.dzi = prof->d64 + g.g;
+            a.dzhi = prof->d64 + prof->n + g.g;
+        } else {
+            a.dzi = prof->d32 + g.g;
+            a.dzhi = prof->d32 + prof->n + g.g;
+        }
+    }
+    a.err = ctx->d_err;
+    a.sj = g.sj;
+    a.sk = g.sk;
+    a.nx = g.nx;
+    a.ny = g.ny;
+    a.nz = g.nz;
+    a.tile_x0 = geo.x0;
+    a.tile_y0 = geo.y0;
+    a.tile_z0 = geo.z0;
+    fill_coefs(a, g);
+
+    CUresult r;
+    if (cfg.family == 0) {
+        a.nbx = (g.nx + cfg.bx * cfg.tx - 1) / (cfg.bx * cfg.tx);
+        a.nby = (g.ny + cfg.by * cfg.ty - 1) / (cfg.by * cfg.ty);
+        a.nbz = (g.nz + cfg.bz * cfg.tz - 1) / (cfg.bz * cfg.tz);
+        long long nb = a.nbx * a.nby * a.nbz;
+        if (nb > 0x7fffffffLL) return fail(KL_ERR_UNSUPPORTED, "grid too large");
+        void *params[] = {&a};
+        r = ctx->drv.LaunchKernel(k->fn, (unsigned)nb, 1, 1, cfg.bx, cfg.by, cfg.bz, 0,
+                                  (CUstream)s, params, nullptr);
+    } else {
+        return fail(KL_ERR_UNSUPPORTED, "zmarch family not available in this build");
+    }
+    if (r != CUDA_SUCCESS) return cu_fail(r, "cuLaunchKernel");
+    if (miss) {
+        ctx->t_launch_ms += ms_since(t0);
+    }
+    ctx->launches++;
+    ctx->last_config = config_string(cfg);
+    return KL_OK;
+}
+
+}  // namespace kl
+
+using namespace kl;
+
+// ================================================================= C ABI
+
+extern "C" {
+
+const char *kl_last_error(void) { return g_last_error.c_str(); }
+
+const char *kl_version(void) { return "libkl 0.1 (sm_103a, NVRTC)"; }
+
+kl_status kl_create(kl_ctx **out, int device, const char *wisdom_dir)
+{
+    if (!out) return fail(KL_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(KL_ERR_INVALID_ARG, "no such device");
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    e = cudaFree(nullptr);  // make the primary context current on this thread
+    if (e != cudaSuccess) return cuda_fail(e, "context init");
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+    kl_ctx *c = new kl_ctx();
+    c->device = device;
+    c->cc_major = prop.major;
+    c->cc_minor = prop.minor;
+    c->nsm = prop.multiProcessorCount;
+    c->name = prop.name;
+    if (wisdom_dir) c->wisdom_dir = wisdom_dir;
+    else if (const char *w = getenv("KL_WISDOM_DIR")) c->wisdom_dir = w;
+    kl_status st = driver_load(&c->drv);
+    if (st) {
+        delete c;
+        return st;
+    }
+    e = cudaMalloc(&c->d_err, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_out, sizeof(double) * 8);
+    if (e != cudaSuccess) {
+        kl_destroy(c);
+        return cuda_fail(e, "context buffers");
+    }
+    *out = c;
+    return KL_OK;
+}
+
+void kl_destroy(kl_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (auto &p : c->kernels)
+        if (p.second.mod) c->drv.ModuleUnload(p.second.mod);
+    for (auto &p : c->profiles) {
+        cudaFree(p.second.d64);
+        cudaFree(p.second.d32);
+    }
+    for (auto &p : c->tables) cudaFree(p.second.first);
+    cudaFree(c->d_err);
+    cudaFree(c->d_scratch);
+    if (c->h_out) cudaFreeHost(c->h_out);
+    delete c;
+}
+
+kl_status kl_layout(int32_t nx, int32_t ny, int32_t nz, int32_t g, int32_t dtype, int64_t *sj,
+                    int64_t *sk, int64_t *origin, int64_t *extent)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || g < 0 || dtype < 0 || dtype > 3 || !sj || !sk || !origin ||
+        !extent)
+        return fail(KL_ERR_INVALID_ARG, "kl_layout: bad argument");
+    int64_t al = 128 / esize_of(dtype);                 // elements per 128 bytes
+    int64_t x0 = (g + al - 1) / al * al;                // interior x start, aligned
+    int64_t row = (x0 + nx + g + al - 1) / al * al;     // row pitch, aligned
+    *sj = row;
+    *sk = row * (ny + 2 * (int64_t)g);
+    *origin = x0 + (int64_t)g * *sj + (int64_t)g * *sk;
+    *extent = *sk * (nz + 2 * (int64_t)g);
+    if (*extent >= (int64_t(1) << 31)) return fail(KL_ERR_BOUNDS, "field larger than 2^31 elements");
+    return KL_OK;
+}
+
+kl_status kl_fill_ghosts(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, void *u, void *v,
+                         void *w, void *nu, void *stream)
+{
+    if (!ctx) return fail(KL_ERR_INVALID_ARG, "ctx is NULL");
+    if (dtype < 0 || dtype > 3) return fail(KL_ERR_INVALID_ARG, "dtype must be 0..3");
+    kl_status st = check_grid(grid, 1, nullptr);
+    if (st) return st;
+    if (!u || !v || !w) return fail(KL_ERR_INVALID_ARG, "u, v, w must not be NULL");
+    cudaError_t e = fill_ghosts_launch(esize_of(dtype), *grid, u, v, w, nu, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fill ghosts launch");
+    ctx->launches++;
+    return KL_OK;
+}
+
+static kl_status select_config(kl_ctx *ctx, const kl_op &op, const kl_grid &g, Config *cfg)
+{
+    char key[160];
+    snprintf(key, sizeof key, "%d/%d/%d/%d/%d/%d/%d/%d", op.adv, op.diff, op.dtype,
+             op.accumulate, g.zbc, g.nx, g.ny, g.nz);
+    auto it = ctx->selection.find(key);
+    std::string text;
+    if (it != ctx->selection.end()) {
+        text = it->second;
+    } else {
+        auto t0 = std::chrono::steady_clock::now();
+        std::vector<WisdomRecord> recs;
+        std::string err;
+        int rule = 5;
+        text = "default";
+        if (!ctx->wisdom_dir.empty()) {
+            std::string path = ctx->wisdom_dir + "/" + wisdom_file_name(op);
+            if (wisdom_read(path, &recs, &err))
+                rule = wisdom_select(recs, ctx->name, ctx->cc_major, ctx->cc_minor, g.zbc, g.nx,
+                                     g.ny, g.nz, &text);
+            else
+                ctx->last_rule_text = err;
+        }
+        // a record whose configuration is invalid here falls back to the default
+        Config c;
+        if (!config_parse(text, &c, &err) || !config_check(op, c, &err)) {
+            ctx->last_rule_text = "wisdom config rejected (" + err + "); default used";
+            text = "default";
+            rule = 5;
+        }
+        ctx->selection[key] = text;
+        ctx->selection_rule[key] = rule;
+        ctx->t_wisdom_ms += ms_since(t0);
+    }
+    std::string err;
+    if (!config_parse(text, cfg, &err)) return fail(KL_ERR_WISDOM_PARSE, err);
+    return KL_OK;
+}
+
+kl_status kl_capture_if_requested(kl_ctx *ctx, const kl_op *op, const kl_grid *grid,
+                                  const kl_fields *fields, void *stream);
+
+kl_status kl_launch(kl_ctx *ctx, const kl_op *op, const kl_grid *grid, const kl_fields *fields,
+                    void *stream)
+{
+    if (!ctx) return fail(KL_ERR_INVALID_ARG, "ctx is NULL");
+    kl_status st = check_op(op);
+    if (st) return st;
+    st = check_fields(*op, fields);
+    if (st) return st;
+    st = check_grid(grid, halo_of(*op), nullptr);
+    if (st) return st;
+    if (env_lists("KERNEL_LAUNCHER_CAPTURE", "tendency")) {
+        st = kl_capture_if_requested(ctx, op, grid, fields, stream);
+        if (st) return st;
+    }
+    Config cfg;
+    st = select_config(ctx, *op, *grid, &cfg);
+    if (st) return st;
+    return launch_config(ctx, *op, cfg, *grid, *fields, (cudaStream_t)stream);
+}
+
+kl_status kl_launch_with_config(kl_ctx *ctx, const kl_op *op, const char *config,
+                                const kl_grid *grid, const kl_fields *fields, void *stream)
+{
+    if (!ctx || !config) return fail(KL_ERR_INVALID_ARG, "ctx or config is NULL");
+    kl_status st = check_op(op);
+    if (st) return st;
+    st = check_fields(*op, fields);
+    if (st) return st;
+    Config cfg;
+    std::string err;
+    if (!config_parse(config, &cfg, &err)) return fail(KL_ERR_INVALID_ARG, err);
+    return launch_config(ctx, *op, cfg, *grid, *fields, (cudaStream_t)stream);
+}
+
+kl_status kl_diag(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, int32_t level, const void *t,
+                  const double *ref, double out[6], void *stream)
+{
+    if (!ctx || !t || !out) return fail(KL_ERR_INVALID_ARG, "ctx, t and out must not be NULL");
+    if (dtype < 0 || dtype > 3 || (level != 0 && level != 1))
+        return fail(KL_ERR_INVALID_ARG, "bad dtype or level");
+    kl_status st = check_grid(grid, 1, nullptr);
+    if (st) return st;
+    Profile *prof = nullptr;
+    st = get_profile(ctx, *grid, &prof);
+    if (st) return st;
+    int nb = diag_blocks(ctx->nsm);
+    size_t need = (size_t)nb * 6 + 8;
+    if (ctx->scratch_doubles < need) {
+        cudaFree(ctx->d_scratch);
+        ctx->d_scratch = nullptr;
+        ctx->scratch_doubles = 0;
+        cudaError_t e = cudaMalloc(&ctx->d_scratch, need * sizeof(double));
+        if (e != cudaSuccess) return fail(KL_ERR_OOM, "cudaMalloc(diag scratch) failed");
+        ctx->scratch_doubles = need;
+    }
+    const double *wz = prof->d64 + (level == 0 ? 2 : 3) * prof->n + grid->g;
+    double *dout = ctx->d_scratch + (size_t)nb * 6;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = diag_launch(dtype, *grid, level, t, ref, wz, ctx->d_scratch, nb, dout, s);
+    if (e != cudaSuccess) return cuda_fail(e, "diag launch");
+    e = cudaMemcpyAsync(ctx->h_out, dout, 6 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "diag readback");
+    memcpy(out, ctx->h_out, 6 * sizeof(double));
+    ctx->launches += 2;
+    return KL_OK;
+}
+
+kl_status kl_stats(kl_ctx *ctx, char *buf, size_t n)
+{
+    if (!ctx || !buf || !n) return fail(KL_ERR_INVALID_ARG, "bad arguments");
+    std::string rules;
+    for (auto &p : ctx->selection_rule)
+        rules += (rules.empty() ? "" : ",") + std::string("\"") + p.first + "\":" +
+                 std::to_string(p.second);
+    int m = snprintf(buf, n,
+                     "{\"device\":\"%s\",\"cc\":\"%d.%d\",\"sms\":%d,\"launches\":%lld,"
+                     "\"cache_hits\":%lld,\"cache_misses\":%lld,\"modules\":%zu,"
+                     "\"stage_ms\":{\"wisdom\":%.3f,\"nvrtc\":%.3f,\"module_load\":%.3f,"
+                     "\"launch\":%.3f},\"last_config\":\"%s\",\"rules\":{%s},\"note\":\"%s\"}",
+                     ctx->name.c_str(), ctx->cc_major, ctx->cc_minor, ctx->nsm, ctx->launches,
+                     ctx->cache_hits, ctx->cache_misses, ctx->kernels.size(), ctx->t_wisdom_ms,
+                     ctx->t_nvrtc_ms, ctx->t_load_ms, ctx->t_launch_ms, ctx->last_config.c_str(),
+                     rules.c_str(), ctx->last_rule_text.c_str());
+    if (m < 0 || (size_t)m >= n) return fail(KL_ERR_INVALID_ARG, "stats buffer too small");
+    return KL_OK;
+}
+
+// ---- host-only helpers
+
+kl_status kl_config_normalize(const kl_op *op, const char *config, char *buf, size_t n)
+{
+    kl_status st = check_op(op);
+    if (st) return st;
+    if (!config || !buf) return fail(KL_ERR_INVALID_ARG, "NULL argument");
+    Config c;
+    std::string err;
+    if (!config_parse(config, &c, &err) || !config_check(*op, c, &err))
+        return fail(KL_ERR_INVALID_ARG, err);
+    std::string s = config_string(c);
+    if (s.size() + 1 > n) return fail(KL_ERR_INVALID_ARG, "buffer too small");
+    memcpy(buf, s.c_str(), s.size() + 1);
+    return KL_OK;
+}
+
+kl_status kl_space_size(const kl_op *op, int32_t family, int64_t *count)
+{
+    kl_status st = check_op(op);
+    if (st) return st;
+    if (!count || (family != 0 && family != 1)) return fail(KL_ERR_INVALID_ARG, "bad family");
+    *count = space_size(family);
+    return KL_OK;
+}
+
+kl_status kl_space_config(const kl_op *op, int32_t family, int64_t idx, char *buf, size_t n)
+{
+    kl_status st = check_op(op);
+    if (st) return st;
+    Config c;
+    if (!buf || !space_config(family, idx, &c)) return fail(KL_ERR_INVALID_ARG, "bad index");
+    std::string s = config_string(c);
+    if (s.size() + 1 > n) return fail(KL_ERR_INVALID_ARG, "buffer too small");
+    memcpy(buf, s.c_str(), s.size() + 1);
+    std::string err;
+    if (!config_check(*op, c, &err)) return fail(KL_ERR_INVALID_ARG, err);
+    return KL_OK;
+}
+
+kl_status kl_compile_only(const kl_op *op, const char *config, int32_t zbc, int32_t zuni,
+                          char *log, size_t n)
+{
+    kl_status st = check_op(op);
+    if (st) return st;
+    Config c;
+    std::string err;
+    if (!config || !config_parse(config, &c, &err) || !config_check(*op, c, &err))
+        return fail(KL_ERR_INVALID_ARG, "configuration: " + err);
+    Compiled out;
+    st = nvrtc_compile(compile_defines(*op, c, zbc, zuni), true, &out);
+    if (log && n) {
+        std::string s = st ? g_last_error : out.log;
+        size_t m = std::min(n - 1, s.size());
+        memcpy(log, s.data(), m);
+        log[m] = '\0';
+    }
+    return st;
+}
+
+kl_status kl_wisdom_select(const char *path, const char *device, int32_t cc_major,
+                           int32_t cc_minor, int32_t zbc, int32_t nx, int32_t ny, int32_t nz,
+                           char *cfg, size_t n, int32_t *rule)
+{
+    if (!path || !device || !cfg || !n || !rule) return fail(KL_ERR_INVALID_ARG, "NULL argument");
+    std::vector<WisdomRecord> recs;
+    std::string err, text = "default";
+    int r = 5;
+    kl_status st = KL_OK;
+    if (wisdom_read(path, &recs, &err)) {
+        r = wisdom_select(recs, device, cc_major, cc_minor, zbc, nx, ny, nz, &text);
+    } else {
+        // missing or unreadable file: the default (rule 5); report why
+        set_error(err);
+        st = KL_OK;
+    }
+    if (text.size() + 1 > n) return fail(KL_ERR_INVALID_ARG, "buffer too small");
+    memcpy(cfg, text.c_str(), text.size() + 1);
+    *rule = r;
+    return st;
+}
+
+kl_status kl_wisdom_append(const char *path, const char *device, int32_t cc_major,
+                           int32_t cc_minor, int32_t zbc, int32_t nx, int32_t ny, int32_t nz,
+                           const char *config, double time_us, const char *extra)
+{
+    if (!path || !device || !config) return fail(KL_ERR_INVALID_ARG, "NULL argument");
+    WisdomRecord r;
+    r.device = device;
+    r.cc_major = cc_major;
+    r.cc_minor = cc_minor;
+    r.zbc = zbc;
+    r.nx = nx;
+    r.ny = ny;
+    r.nz = nz;
+    r.config = config;
+    r.time_us = time_us;
+    if (extra && *extra) {
+        std::stringstream ss(extra);
+        std::string tok;
+        while (ss >> tok) {
+            size_t eq = tok.find('=');
+            if (eq == std::string::npos) return fail(KL_ERR_INVALID_ARG, "extra needs key=value");
+            r.extra[tok.substr(0, eq)] = tok.substr(eq + 1);
+        }
+    }
+    std::string err;
+    if (!wisdom_append(path, r, &err)) return fail(KL_ERR_IO, err);
+    return KL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,240 @@
+// kl_device.cu -- ghost fill and FP64 diagnostic reductions (nvcc, sm_103a).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "kl_internal.h"
+
+namespace {
+
+// ------------------------------------------------------------ ghost fill
+//
+// Ghost points are enumerated in three disjoint groups: the 2g full z planes
+// (with x and y ghosts), the 2g y rows of every interior level (with x
+// ghosts), and the 2g x points of every interior row.  Each maps straight to
+// an interior source point, axis by axis, so one launch fills faces, edges
+// and corners with no ordering between them.  The copy moves raw bits; the
+// odd (w) mirror flips the sign bit, which negates exactly in every format.
+
+struct FillArgs {
+    char *f[4];              // u, v, w, nu at interior (0,0,0); nu may be NULL
+    long long sj, sk;
+    int nx, ny, nz, g, zbc;
+    long long px, py;        // padded row length / rows per plane
+    long long n_zp, n_yr, n_xp, total;
+};
+
+__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+template <typename B>
+__global__ void __launch_bounds__(256) fill_kernel(FillArgs a)
+{
+    const B sign_bit = (B)1 << (sizeof(B) * 8 - 1);
+    const int g = a.g, g2 = 2 * a.g;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < a.total;
+         t += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        if (t < a.n_zp) {
+            long long plane = a.px * a.py;
+            int p = (int)(t / plane);
+            long long r = t % plane;
+            j = (int)(r / a.px) - g;
+            i = (int)(r % a.px) - g;
+            k = p < g ? p - g : a.nz + (p - g);
+        } else if (t < a.n_zp + a.n_yr) {
+            long long t2 = t - a.n_zp;
+            long long row = t2 / a.px;
+            i = (int)(t2 % a.px) - g;
+            k = (int)(row / g2);
+            int q = (int)(row % g2);
+            j = q < g ? q - g : a.ny + (q - g);
+        } else {
+            long long t3 = t - a.n_zp - a.n_yr;
+            int q = (int)(t3 % g2);
+            long long rest = t3 / g2;
+            j = (int)(rest % a.ny);
+            k = (int)(rest / a.ny);
+            i = q < g ? q - g : a.nx + (q - g);
+        }
+        int si = wrapi(i, a.nx), sj = wrapi(j, a.ny);
+        long long dst = i + j * a.sj + k * a.sk;
+        // even fields (u, v, nu)
+        int ske;
+        if (a.zbc == 0) ske = wrapi(k, a.nz);
+        else ske = k < 0 ? -1 - k : (k >= a.nz ? 2 * a.nz - 1 - k : k);
+        long long srce = si + sj * a.sj + (long long)ske * a.sk;
+        for (int f = 0; f < 4; ++f) {
+            if (f == 2 || !a.f[f]) continue;
+            B *p = (B *)a.f[f];
+            p[dst] = p[srce];
+        }
+        // w: odd about the walls, w(nz) = 0
+        B *pw = (B *)a.f[2];
+        if (a.zbc == 0) {
+            pw[dst] = pw[srce];
+        } else if (k == a.nz) {
+            pw[dst] = (B)0;
+        } else {
+            int sko = k < 0 ? -k : (k > a.nz ? 2 * a.nz - k : k);
+            B v = pw[si + sj * a.sj + (long long)sko * a.sk];
+            pw[dst] = (k < 0 || k > a.nz) ? (B)(v ^ sign_bit) : v;
+        }
+    }
+}
+
+// ---------------------------------------------------------- diagnostics
+
+struct DiagArgs {
+    const void *t;
+    const double *ref;
+    const double *wz;        // weight per level k (dz_k or dzh_k)
+    long long sj, sk;
+    int nx, ny, nz;
+    long long n;
+    double *partial;         // nblocks x 6
+};
+
+template <typename T> __device__ __forceinline__ double to_d(T x) { return (double)x; }
+template <> __device__ __forceinline__ double to_d<__nv_bfloat16>(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+template <> __device__ __forceinline__ double to_d<__half>(__half x) { return (double)__half2float(x); }
+
+__device__ __forceinline__ void reduce6(double v[6], double *out)
+{
+    // 0, 2: max; others: sum
+    for (int o = 16; o > 0; o >>= 1)
+        for (int c = 0; c < 6; ++c) {
+            double x = __shfl_xor_sync(0xffffffffu, v[c], o);
+            v[c] = (c == 0 || c == 2) ? fmax(v[c], x) : v[c] + x;
+        }
+    __shared__ double sh[32][6];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0)
+        for (int c = 0; c < 6; ++c) sh[warp][c] = v[c];
+    __syncthreads();
+    if (warp == 0) {
+        for (int c = 0; c < 6; ++c) v[c] = lane < nw ? sh[lane][c] : ((c == 0 || c == 2) ? 0.0 : 0.0);
+        for (int o = 16; o > 0; o >>= 1)
+            for (int c = 0; c < 6; ++c) {
+                double x = __shfl_xor_sync(0xffffffffu, v[c], o);
+                v[c] = (c == 0 || c == 2) ? fmax(v[c], x) : v[c] + x;
+            }
+        if (lane == 0)
+            for (int c = 0; c < 6; ++c) out[c] = v[c];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) diag_kernel(DiagArgs a)
+{
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    const T *t = (const T *)a.t;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < a.n;
+         q += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(q % a.nx);
+        long long r = q / a.nx;
+        int j = (int)(r % a.ny);
+        int k = (int)(r / a.ny);
+        long long o = i + j * a.sj + k * a.sk;
+        double tv = to_d(t[o]);
+        double rv = a.ref ? a.ref[o] : 0.0;
+        double e = tv - rv;
+        v[0] = fmax(v[0], fabs(e));
+        v[1] += e * e;
+        v[2] = fmax(v[2], fabs(rv));
+        v[3] += rv * rv;
+        v[4] += tv;
+        v[5] += tv * a.wz[k];
+    }
+    reduce6(v, a.partial + 6 * (size_t)blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256) diag_final(const double *partial, int nb, long long n, double *out)
+{
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        const double *p = partial + 6 * (size_t)b;
+        v[0] = fmax(v[0], p[0]);
+        v[1] += p[1];
+        v[2] = fmax(v[2], p[2]);
+        v[3] += p[3];
+        v[4] += p[4];
+        v[5] += p[5];
+    }
+    __shared__ double res[6];
+    reduce6(v, res);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        out[0] = res[0];
+        out[1] = n ? sqrt(res[1] / (double)n) : 0.0;
+        out[2] = res[2];
+        out[3] = n ? sqrt(res[3] / (double)n) : 0.0;
+        out[4] = res[4];
+        out[5] = res[5];
+    }
+}
+
+}  // namespace
+
+namespace kl {
+
+cudaError_t fill_ghosts_launch(int esize, const kl_grid &g, void *u, void *v, void *w, void *nu,
+                               cudaStream_t s)
+{
+    FillArgs a;
+    size_t off = (size_t)g.origin * esize;
+    a.f[0] = (char *)u + off;
+    a.f[1] = (char *)v + off;
+    a.f[2] = (char *)w + off;
+    a.f[3] = nu ? (char *)nu + off : nullptr;
+    a.sj = g.sj;
+    a.sk = g.sk;
+    a.nx = g.nx;
+    a.ny = g.ny;
+    a.nz = g.nz;
+    a.g = g.g;
+    a.zbc = g.zbc;
+    a.px = g.nx + 2LL * g.g;
+    a.py = g.ny + 2LL * g.g;
+    a.n_zp = 2LL * g.g * a.px * a.py;
+    a.n_yr = (long long)g.nz * 2 * g.g * a.px;
+    a.n_xp = (long long)g.nz * g.ny * 2 * g.g;
+    a.total = a.n_zp + a.n_yr + a.n_xp;
+    long long blocks = (a.total + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (esize == 8) fill_kernel<unsigned long long><<<(unsigned)blocks, 256, 0, s>>>(a);
+    else if (esize == 4) fill_kernel<unsigned int><<<(unsigned)blocks, 256, 0, s>>>(a);
+    else fill_kernel<unsigned short><<<(unsigned)blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int diag_blocks(int nsm) { return nsm * 4; }
+
+cudaError_t diag_launch(int dtype, const kl_grid &g, int level, const void *t, const double *ref,
+                        const double *wz, double *scratch, int nblocks, double *dout,
+                        cudaStream_t s)
+{
+    (void)level;
+    int es = esize_of(dtype);
+    DiagArgs a;
+    a.t = (const char *)t + (size_t)g.origin * es;
+    a.ref = ref ? ref + g.origin : nullptr;
+    a.wz = wz;
+    a.sj = g.sj;
+    a.sk = g.sk;
+    a.nx = g.nx;
+    a.ny = g.ny;
+    a.nz = g.nz;
+    a.n = (long long)g.nx * g.ny * g.nz;
+    a.partial = scratch;
+    switch (dtype) {
+    case KL_F64: diag_kernel<double><<<nblocks, 256, 0, s>>>(a); break;
+    case KL_F32: diag_kernel<float><<<nblocks, 256, 0, s>>>(a); break;
+    case KL_BF16: diag_kernel<__nv_bfloat16><<<nblocks, 256, 0, s>>>(a); break;
+    default: diag_kernel<__half><<<nblocks, 256, 0, s>>>(a); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    diag_final<<<1, 256, 0, s>>>(scratch, nblocks, a.n, dout);
+    return cudaGetLastError();
+}
+
+}  // namespace kl

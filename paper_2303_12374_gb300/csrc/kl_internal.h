@@ -1,0 +1,177 @@
+// kl_internal.h -- declarations shared by the translation units of libkl.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "kl.h"
+
+namespace kl {
+
+// ------------------------------------------------------------ status
+kl_status fail(kl_status code, const std::string &msg);   // records message, returns code
+kl_status cuda_fail(cudaError_t e, const char *what);
+kl_status cu_fail(CUresult r, const char *what);
+void set_error(const std::string &msg);
+
+// -------------------------------------------------------- configuration
+// One point of the tuning space.  family 0 "direct": the parameters of
+// Table 2.  family 1 "zmarch": z-marching CTAs with TMA-staged planes.
+struct Config {
+    int family = 0;
+    // direct (Table 2 defaults)
+    int bx = 256, by = 1, bz = 1;
+    int tx = 1, ty = 1, tz = 1;
+    int ux = 0, uy = 0, uz = 0;
+    int cx = 0, cy = 0, cz = 0;
+    int perm = 0;
+    int minb = 1;
+    // zmarch
+    int mbx = 32, mby = 4;     // threads along x, y
+    int mpx = 2, mpy = 1;      // points per thread along x (consecutive), y (block-strided)
+    int kc = 32;               // z levels per CTA
+    int ns = 8;                // plane ring slots (>= 7 + prefetch)
+    int mminb = 1;             // min blocks per SM
+};
+
+std::string config_string(const Config &c);
+bool config_parse(const std::string &s, Config *c, std::string *err);
+// constraints of the space for an op (threads per block, shared memory,
+// ghost width, ...).  smem_limit 0 = use the sm_103a per-block maximum.
+bool config_check(const kl_op &op, const Config &c, std::string *err);
+int64_t space_size(int family);
+bool space_config(int family, int64_t idx, Config *c);
+
+// dynamic shared memory of a zmarch configuration, bytes
+size_t zmarch_smem_bytes(const kl_op &op, const Config &c);
+int halo_of(const kl_op &op);           // in-plane stencil reach (3 for adv5, else 1)
+int esize_of(int dtype);
+
+// ------------------------------------------------------------- wisdom
+struct WisdomRecord {
+    std::string device;
+    int cc_major = 0, cc_minor = 0;
+    int zbc = 0;
+    int nx = 0, ny = 0, nz = 0;
+    std::string config;
+    double time_us = 0;
+    std::map<std::string, std::string> extra;
+};
+bool wisdom_read(const std::string &path, std::vector<WisdomRecord> *out, std::string *err);
+// returns rule 1..5 and the chosen configuration string
+int wisdom_select(const std::vector<WisdomRecord> &recs, const std::string &device, int ccM,
+                  int ccm, int zbc, int nx, int ny, int nz, std::string *config);
+std::string wisdom_file_name(const kl_op &op);
+bool wisdom_append(const std::string &path, const WisdomRecord &r, std::string *err);
+
+// ------------------------------------------------------------ compile
+struct Compiled {
+    std::vector<char> cubin;
+    std::string log;
+};
+std::string compile_defines(const kl_op &op, const Config &c, int zbc, int zuni);
+kl_status nvrtc_compile(const std::string &defines, bool verbose, Compiled *out);
+
+// ------------------------------------------------------------ driver API
+struct Driver {
+    CUresult (*ModuleLoadData)(CUmodule *, const void *) = nullptr;
+    CUresult (*ModuleUnload)(CUmodule) = nullptr;
+    CUresult (*ModuleGetFunction)(CUfunction *, CUmodule, const char *) = nullptr;
+    CUresult (*LaunchKernel)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned,
+                             unsigned, unsigned, CUstream, void **, void **) = nullptr;
+    CUresult (*FuncSetAttribute)(CUfunction, CUfunction_attribute, int) = nullptr;
+    CUresult (*FuncGetAttribute)(int *, CUfunction_attribute, CUfunction) = nullptr;
+    CUresult (*TensorMapEncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                     const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                     const cuuint32_t *, CUtensorMapInterleave,
+                                     CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                     CUtensorMapFloatOOBfill) = nullptr;
+};
+kl_status driver_load(Driver *d);
+
+// -------------------------------------------------------- kernel args
+// Mirror of struct kl_args in kl_stencil.cuh (all members 8-byte aligned).
+struct KArgs {
+    const void *u, *v, *w, *nu;
+    void *ut, *vt, *wt;
+    const void *dzi, *dzhi;
+    int *err;
+    long long sj, sk;
+    long long nx, ny, nz;
+    long long nbx, nby, nbz;
+    long long kchunk;
+    long long tile_x0, tile_y0, tile_z0;
+    double cd[8];
+    float cf[8];
+};
+
+struct Kernel {
+    CUmodule mod = nullptr;
+    CUfunction fn = nullptr;
+    Config cfg;
+    size_t smem = 0;
+    int nregs = 0;
+    int local_bytes = 0;
+};
+
+struct Profile {
+    double *d64 = nullptr;   // dzi | dzhi, each nz + 2g, f64
+    float *d32 = nullptr;    // same in f32
+    int n = 0;
+};
+
+// validated geometry of one launch
+struct Geom {
+    int64_t x0, y0, z0;      // tensor coordinates of interior (0,0,0)
+};
+kl_status check_grid(const kl_grid *g, int need_g, Geom *geo);
+void zprofile_host(int nz, int g, int zbc, const double *zh, double dz_uniform,
+                   std::vector<double> *dzi, std::vector<double> *dzhi);
+
+}  // namespace kl
+
+struct kl_ctx {
+    int device = 0;
+    int cc_major = 0, cc_minor = 0;
+    int nsm = 0;
+    std::string name;
+    std::string wisdom_dir;
+    kl::Driver drv;
+    std::map<std::string, kl::Kernel> kernels;        // compile key -> module
+    std::map<std::string, std::string> selection;     // problem key -> config
+    std::map<std::string, int> selection_rule;
+    std::map<std::string, kl::Profile> profiles;      // z-grid key -> device profiles
+    int *d_err = nullptr;
+    double *d_scratch = nullptr;
+    size_t scratch_doubles = 0;
+    double *h_out = nullptr;                          // pinned, diag results
+    // tile tables of batched launches, keyed by the batch signature
+    std::map<std::string, std::pair<void *, size_t>> tables;
+    // statistics
+    long long launches = 0, cache_hits = 0, cache_misses = 0;
+    double t_wisdom_ms = 0, t_nvrtc_ms = 0, t_load_ms = 0, t_launch_ms = 0;
+    double last_first_launch_ms = 0;
+    std::string last_config, last_rule_text;
+};
+
+namespace kl {
+// launch one tendency kernel with a resolved configuration (shared by
+// kl_launch, kl_launch_with_config and the tuner)
+kl_status launch_config(kl_ctx *ctx, const kl_op &op, const Config &cfg, const kl_grid &g,
+                        const kl_fields &f, cudaStream_t s);
+kl_status get_kernel(kl_ctx *ctx, const kl_op &op, const Config &cfg, int zbc, int zuni,
+                     Kernel **out);
+kl_status get_profile(kl_ctx *ctx, const kl_grid &g, Profile **out);
+// device kernels of kl_device.cu
+cudaError_t fill_ghosts_launch(int esize, const kl_grid &g, void *u, void *v, void *w,
+                               void *nu, cudaStream_t s);
+cudaError_t diag_launch(int dtype, const kl_grid &g, int level, const void *t,
+                        const double *ref, const double *wz, double *scratch, int nblocks,
+                        double *dout, cudaStream_t s);
+int diag_blocks(int nsm);
+}  // namespace kl

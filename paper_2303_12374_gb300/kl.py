@@ -1,0 +1,223 @@
+"""ctypes binding of libkl (include/kl.h): the same entry points, argument
+marshalling only.  Every step of the stencil path runs in the library's CUDA
+kernels; nothing here computes a tendency, and there is no CPU fallback: if
+the shared library is missing or fails to load, every call raises.
+
+PyTorch is used only for device memory and streams (`torch.Tensor.data_ptr()`,
+`torch.cuda.current_stream().cuda_stream`).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+KL_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "NVRTC", -4: "IO", -5: "WISDOM_PARSE",
+          -6: "UNSUPPORTED", -7: "BOUNDS", -8: "TIMEOUT", -9: "OOM"}
+DTYPES = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
+
+
+class KLError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"kl status {status} ({ERRORS.get(status, '?')}): {msg}")
+        self.status = status
+
+
+class Op(ctypes.Structure):
+    _fields_ = [("adv", ctypes.c_int32), ("diff", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("accumulate", ctypes.c_int32)]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("g", ctypes.c_int32), ("sj", ctypes.c_int64), ("sk", ctypes.c_int64),
+                ("origin", ctypes.c_int64), ("extent", ctypes.c_int64),
+                ("zbc", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("nu", ctypes.c_double), ("zh", ctypes.POINTER(ctypes.c_double))]
+
+
+class Fields(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_void_p), ("v", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("nu", ctypes.c_void_p), ("ut", ctypes.c_void_p), ("vt", ctypes.c_void_p),
+                ("wt", ctypes.c_void_p)]
+
+
+# every symbol include/kl.h declares, with ctypes signatures
+_P = ctypes.c_void_p
+_I32, _I64, _D = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+_S = ctypes.c_char_p
+SIGNATURES = {
+    "kl_create": ([ctypes.POINTER(_P), ctypes.c_int, _S], ctypes.c_int),
+    "kl_destroy": ([_P], None),
+    "kl_last_error": ([], _S),
+    "kl_layout": ([_I32, _I32, _I32, _I32, _I32] + [ctypes.POINTER(_I64)] * 4, ctypes.c_int),
+    "kl_fill_ghosts": ([_P, _I32, ctypes.POINTER(Grid), _P, _P, _P, _P, _P], ctypes.c_int),
+    "kl_launch": ([_P, ctypes.POINTER(Op), ctypes.POINTER(Grid), ctypes.POINTER(Fields), _P],
+                  ctypes.c_int),
+    "kl_launch_with_config": ([_P, ctypes.POINTER(Op), _S, ctypes.POINTER(Grid),
+                               ctypes.POINTER(Fields), _P], ctypes.c_int),
+    "kl_launch_batched": ([_P, ctypes.POINTER(Op), _I32, ctypes.POINTER(Grid),
+                           ctypes.POINTER(Fields), _P], ctypes.c_int),
+    "kl_capture": ([_P, ctypes.POINTER(Op), ctypes.POINTER(Grid), ctypes.POINTER(Fields), _S, _P],
+                   ctypes.c_int),
+    "kl_tune": ([_P, _S, _S, _S], ctypes.c_int),
+    "kl_diag": ([_P, _I32, ctypes.POINTER(Grid), _I32, _P, _P, ctypes.POINTER(_D), _P],
+                ctypes.c_int),
+    "kl_stats": ([_P, ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
+    "kl_config_normalize": ([ctypes.POINTER(Op), _S, ctypes.c_char_p, ctypes.c_size_t],
+                            ctypes.c_int),
+    "kl_space_size": ([ctypes.POINTER(Op), _I32, ctypes.POINTER(_I64)], ctypes.c_int),
+    "kl_space_config": ([ctypes.POINTER(Op), _I32, _I64, ctypes.c_char_p, ctypes.c_size_t],
+                        ctypes.c_int),
+    "kl_compile_only": ([ctypes.POINTER(Op), _S, _I32, _I32, ctypes.c_char_p, ctypes.c_size_t],
+                        ctypes.c_int),
+    "kl_wisdom_select": ([_S, _S, _I32, _I32, _I32, _I32, _I32, _I32, ctypes.c_char_p,
+                          ctypes.c_size_t, ctypes.POINTER(_I32)], ctypes.c_int),
+    "kl_wisdom_append": ([_S, _S, _I32, _I32, _I32, _I32, _I32, _I32, _S, _D, _S], ctypes.c_int),
+    "kl_version": ([], _S),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libkl.so (building it first if needed); raises if that fails."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libkl.so not found at {path}; run build() first")
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().kl_last_error().decode()
+
+
+def check(status: int) -> None:
+    if status != KL_OK:
+        raise KLError(status, last_error())
+
+
+def _b(s):
+    return None if s is None else (s.encode() if isinstance(s, str) else s)
+
+
+# ----------------------------------------------------------- entry points
+
+def kl_create(device: int = 0, wisdom_dir: str | None = None) -> int:
+    ctx = ctypes.c_void_p()
+    check(load().kl_create(ctypes.byref(ctx), device, _b(wisdom_dir)))
+    return ctx.value
+
+
+def kl_destroy(ctx: int) -> None:
+    load().kl_destroy(ctx)
+
+
+def kl_layout(nx, ny, nz, g, dtype):
+    out = [ctypes.c_int64() for _ in range(4)]
+    check(load().kl_layout(nx, ny, nz, g, dtype, *[ctypes.byref(o) for o in out]))
+    return tuple(o.value for o in out)   # sj, sk, origin, extent
+
+
+def kl_fill_ghosts(ctx, dtype, grid: Grid, u, v, w, nu=None, stream=None) -> None:
+    check(load().kl_fill_ghosts(ctx, dtype, ctypes.byref(grid), u, v, w, nu, stream))
+
+
+def kl_launch(ctx, op: Op, grid: Grid, fields: Fields, stream=None) -> None:
+    check(load().kl_launch(ctx, ctypes.byref(op), ctypes.byref(grid), ctypes.byref(fields), stream))
+
+
+def kl_launch_with_config(ctx, op: Op, config: str, grid: Grid, fields: Fields,
+                          stream=None) -> None:
+    check(load().kl_launch_with_config(ctx, ctypes.byref(op), _b(config), ctypes.byref(grid),
+                                       ctypes.byref(fields), stream))
+
+
+def kl_launch_batched(ctx, op: Op, grids, fields, stream=None) -> None:
+    n = len(grids)
+    ga = (Grid * n)(*grids)
+    fa = (Fields * n)(*fields)
+    check(load().kl_launch_batched(ctx, ctypes.byref(op), n, ga, fa, stream))
+
+
+def kl_capture(ctx, op: Op, grid: Grid, fields: Fields, path: str, stream=None) -> None:
+    check(load().kl_capture(ctx, ctypes.byref(op), ctypes.byref(grid), ctypes.byref(fields),
+                            _b(path), stream))
+
+
+def kl_tune(ctx, capture_path: str, opts: str, wisdom_path: str) -> None:
+    check(load().kl_tune(ctx, _b(capture_path), _b(opts), _b(wisdom_path)))
+
+
+def kl_diag(ctx, dtype, grid: Grid, level, t, ref=None, stream=None):
+    out = (ctypes.c_double * 6)()
+    check(load().kl_diag(ctx, dtype, ctypes.byref(grid), level, t, ref, out, stream))
+    return list(out)
+
+
+def kl_stats(ctx) -> str:
+    buf = ctypes.create_string_buffer(8192)
+    check(load().kl_stats(ctx, buf, len(buf)))
+    return buf.value.decode()
+
+
+def kl_config_normalize(op: Op, config: str) -> str:
+    buf = ctypes.create_string_buffer(1024)
+    check(load().kl_config_normalize(ctypes.byref(op), _b(config), buf, len(buf)))
+    return buf.value.decode()
+
+
+def kl_space_size(op: Op, family: int) -> int:
+    n = ctypes.c_int64()
+    check(load().kl_space_size(ctypes.byref(op), family, ctypes.byref(n)))
+    return n.value
+
+
+def kl_space_config(op: Op, family: int, idx: int):
+    """(config text, valid?) of the idx-th point of the raw space."""
+    buf = ctypes.create_string_buffer(1024)
+    st = load().kl_space_config(ctypes.byref(op), family, idx, buf, len(buf))
+    if st not in (KL_OK, -1) or not buf.value:
+        check(st)
+    return buf.value.decode(), st == KL_OK
+
+
+def kl_compile_only(op: Op, config: str, zbc: int = 0, zuni: int = 1) -> str:
+    buf = ctypes.create_string_buffer(65536)
+    check(load().kl_compile_only(ctypes.byref(op), _b(config), zbc, zuni, buf, len(buf)))
+    return buf.value.decode()
+
+
+def kl_wisdom_select(path, device, cc_major, cc_minor, zbc, nx, ny, nz):
+    buf = ctypes.create_string_buffer(1024)
+    rule = ctypes.c_int32()
+    check(load().kl_wisdom_select(_b(path), _b(device), cc_major, cc_minor, zbc, nx, ny, nz, buf,
+                                  len(buf), ctypes.byref(rule)))
+    return buf.value.decode(), rule.value
+
+
+def kl_wisdom_append(path, device, cc_major, cc_minor, zbc, nx, ny, nz, config, time_us,
+                     extra: str = "") -> None:
+    check(load().kl_wisdom_append(_b(path), _b(device), cc_major, cc_minor, zbc, nx, ny, nz,
+                                  _b(config), time_us, _b(extra)))
+
+
+def kl_version() -> str:
+    return load().kl_version().decode()

@@ -1,0 +1,157 @@
+"""GPU parity through the C ABI against the FP64 oracle, element by element.
+
+Sizes span several tiles and ragged tails (odd extents); every op, storage
+type and boundary condition; the default and several tuned configurations;
+the ghost fill bit-exact; accumulate mode; full-size grids on sampled levels.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from gpu_cases import TOL, make_inputs, oracle_ref, rel_err, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+CONFIGS_DIRECT = [
+    "default",
+    "direct:bx=32,by=4,bz=2,tx=2,ty=1,tz=2,ux=1,uz=1,cx=1,cz=1,perm=ZXY,minb=2",
+    "direct:bx=64,by=2,bz=1,tx=4,ty=2,tz=1,ux=1,uy=1,cx=1,cy=0,perm=YZX,minb=1",
+    "direct:bx=16,by=8,bz=4,tx=1,ty=4,tz=4,uy=1,uz=0,cy=1,cz=0,perm=ZYX,minb=3",
+]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_2303_12374_gb300 import kl
+    assert torch.cuda.is_available()
+    c = kl.kl_create(0, None)
+    yield c
+    kl.kl_destroy(c)
+
+
+@pytest.mark.parametrize("dtype", [0, 1, 2, 3])
+@pytest.mark.parametrize("walls,g", [(False, 1), (True, 3), (False, 3)])
+def test_ghost_fill_bit_exact(ctx, oracle_mod, dtype, walls, g):
+    nx, ny, nz = 13, 9, 7
+    f = make_inputs(nx, ny, nz, seed=21, walls=walls, var_nu=True)
+    p, bufs, _, rin = run_gpu(ctx, f, adv=2 if g == 1 else 5, diff=2, dtype=dtype, walls=walls,
+                              g=g)
+    for name, odd in (("u", False), ("v", False), ("w", True), ("nu", False)):
+        got = p.padded_view(bufs[name]).double().cpu().numpy()
+        ref = oracle_mod.pad(rin[name], g, walls, odd)
+        assert np.array_equal(got, ref), name
+
+
+CASES = [
+    # nx, ny, nz, g, walls, stretch, adv, diff
+    (13, 11, 9, 3, True, 0.0, 5, 1),
+    (37, 21, 17, 3, True, 2.0, 5, 2),
+    (33, 19, 12, 1, False, 0.0, 2, 1),
+    (40, 24, 10, 3, False, 0.0, 5, 0),
+    (29, 30, 14, 1, True, 2.0, 0, 2),
+    (21, 17, 11, 1, True, 0.0, 2, 2),
+]
+
+
+@pytest.mark.parametrize("dtype", [0, 1, 2, 3])
+@pytest.mark.parametrize("case", CASES)
+def test_tendency_parity_default(ctx, oracle_mod, dtype, case):
+    nx, ny, nz, g, walls, stretch, adv, diff = case
+    f = make_inputs(nx, ny, nz, seed=100 + nx, walls=walls, stretch=stretch, var_nu=diff == 2)
+    p, _, outs, rin = run_gpu(ctx, f, adv=adv, diff=diff, dtype=dtype, walls=walls, g=g,
+                              stretched=stretch > 0)
+    ref = oracle_ref(oracle_mod, rin, f["zh"], adv=adv, diff=diff, walls=walls, g=g)
+    for name, r in zip(("ut", "vt", "wt"), ref):
+        e = rel_err(p.download(outs[name]), r)
+        assert e <= TOL[dtype], (name, e)
+
+
+@pytest.mark.parametrize("config", CONFIGS_DIRECT)
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_tendency_parity_configs(ctx, oracle_mod, config, dtype):
+    nx, ny, nz = 70, 45, 23
+    f = make_inputs(nx, ny, nz, seed=7, walls=True, stretch=2.0, var_nu=True)
+    for adv, diff in ((5, 1), (5, 2), (2, 1)):
+        p, _, outs, rin = run_gpu(ctx, f, adv=adv, diff=diff, dtype=dtype, walls=True, g=3,
+                                  stretched=True, config=config)
+        ref = oracle_ref(oracle_mod, rin, f["zh"], adv=adv, diff=diff, walls=True, g=3)
+        for name, r in zip(("ut", "vt", "wt"), ref):
+            e = rel_err(p.download(outs[name]), r)
+            assert e <= TOL[dtype], (config, adv, diff, name, e)
+
+
+def test_accumulate(ctx, oracle_mod):
+    nx, ny, nz = 30, 20, 12
+    f = make_inputs(nx, ny, nz, seed=3, walls=True)
+    rng = np.random.default_rng(0)
+    t0 = {k: rng.standard_normal((nz, ny, nx)) for k in ("ut", "vt", "wt")}
+    p, _, outs, rin = run_gpu(ctx, f, adv=5, diff=1, dtype=0, walls=True, g=3, accumulate=True,
+                              t0=t0)
+    ref = oracle_ref(oracle_mod, rin, f["zh"], adv=5, diff=1, walls=True, g=3)
+    for name, r in zip(("ut", "vt", "wt"), ref):
+        got = p.download(outs[name])
+        assert rel_err(got, r + t0[name]) <= 1e-12
+
+
+def test_wall_face_w_tendency_is_zero(ctx):
+    f = make_inputs(24, 16, 10, seed=4, walls=True)
+    p, _, outs, _ = run_gpu(ctx, f, adv=5, diff=1, dtype=1, walls=True, g=3)
+    assert np.all(p.download(outs["wt"])[0] == 0.0)
+
+
+def test_constant_fields_zero_to_rounding_on_gpu(ctx):
+    """Constant fields: zero tendency up to the rounding of one flux product.
+
+    The GPU kernels contract products into fused multiply-adds, so equal fluxes
+    can differ by the rounding error of one product; the bound is the kernel's
+    tolerance times the size of one flux term |u|^2 / dx.  (The oracle, built
+    without contraction, gives exact zeros; that is pinned separately.)"""
+    nx, ny, nz = 40, 24, 12
+    f = {"u": np.full((nz, ny, nx), 0.7), "v": np.full((nz, ny, nx), -1.3),
+         "w": np.zeros((nz, ny, nx)), "nu": np.full((nz, ny, nx), 2e-3)}
+    from paper_2303_12374_gb300 import synth
+    f["zh"] = synth.zfaces(nz, 1.0, 2.0)
+    for dtype in (0, 1):
+        for adv, diff in ((5, 2), (2, 1)):
+            p, _, outs, _ = run_gpu(ctx, f, adv=adv, diff=diff, dtype=dtype, walls=True, g=3,
+                                    stretched=True)
+            flux_scale = 1.3 ** 2 * max(nx, ny, 1.0 / np.diff(f["zh"]).min())
+            for k in ("ut", "vt", "wt"):
+                assert np.abs(p.download(outs[k])).max() <= TOL[dtype] * flux_scale, (dtype, k)
+
+
+def test_diag_matches_oracle(ctx, oracle_mod):
+    import torch
+    from paper_2303_12374_gb300 import kl
+    nx, ny, nz = 50, 30, 20
+    f = make_inputs(nx, ny, nz, seed=9, walls=True, stretch=2.0)
+    p, _, outs, rin = run_gpu(ctx, f, adv=5, diff=1, dtype=1, walls=True, g=3, stretched=True)
+    ref = oracle_ref(oracle_mod, rin, f["zh"], adv=5, diff=1, walls=True, g=3)
+    dz, dzh = oracle_mod.zprofile(nz, 3, True, f["zh"])
+    for level, name, r in ((0, "ut", ref[0]), (0, "vt", ref[1]), (1, "wt", ref[2])):
+        ref_buf = p.upload(r, dtype=torch.float64)
+        got = kl.kl_diag(ctx, p.dtype, p.grid, level, outs[name].data_ptr(), ref_buf.data_ptr())
+        t = p.download(outs[name])
+        wgt = np.broadcast_to((dz if level == 0 else dzh)[3:3 + nz][:, None, None], t.shape)
+        want = oracle_mod.diag(t, r, wgt)
+        assert got[0] == pytest.approx(want[0], rel=1e-12, abs=1e-300)
+        assert got[2] == want[2]
+        for c in (1, 3):
+            assert got[c] == pytest.approx(want[c], rel=1e-12)
+        for c in (4, 5):
+            assert got[c] == pytest.approx(want[c], rel=1e-9, abs=1e-9 * np.abs(t).sum())
+
+
+def test_second_launch_is_cached(ctx):
+    import json
+    from paper_2303_12374_gb300 import kl
+    f = make_inputs(20, 20, 10, seed=5, walls=True)
+    run_gpu(ctx, f, adv=5, diff=1, dtype=1, walls=True, g=3, config="direct:bx=128,minb=2")
+    s1 = json.loads(kl.kl_stats(ctx))
+    run_gpu(ctx, f, adv=5, diff=1, dtype=1, walls=True, g=3, config="direct:bx=128,minb=2")
+    s2 = json.loads(kl.kl_stats(ctx))
+    assert s2["cache_misses"] == s1["cache_misses"]
+    assert s2["cache_hits"] == s1["cache_hits"] + 1

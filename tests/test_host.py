@@ -1,0 +1,188 @@
+"""Host-side logic of libkl, no GPU needed: the library loads and exports
+every symbol of include/kl.h, the configuration space of Table 2, config
+parsing and constraints, run-time compilation with NVRTC for sm_103a, the
+wisdom-selection heuristic of Sec. 4.5, and the recommended layout."""
+
+from __future__ import annotations
+
+import os
+import re
+
+import pytest
+
+from paper_2303_12374_gb300 import kl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_symbols():
+    text = open(os.path.join(ROOT, "include", "kl.h")).read()
+    return sorted(set(re.findall(r"\b(kl_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = kl.load()
+    names = header_symbols()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(kl.SIGNATURES), set(names) ^ set(kl.SIGNATURES)
+    assert "sm_103a" in kl.kl_version()
+
+
+def _golden_space():
+    vals = {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "table2_space.txt")):
+        line = line.strip()
+        if not line or line.startswith("#") or line.startswith("default"):
+            continue
+        name, *rest = line.split()
+        vals[name] = rest
+    return vals
+
+
+def test_space_is_table2():
+    vals = _golden_space()
+    count = 1
+    for name, v in vals.items():
+        if name != "more_than":
+            count *= len(v)
+    op = kl.Op(5, 1, 1, 0)
+    assert kl.kl_space_size(op, 0) == count
+    assert count > int(vals["more_than"][0])
+    # every raw index decodes to values of the table
+    seen = {k: set() for k in ("bx", "by", "bz", "tx", "perm", "minb")}
+    for idx in range(0, count, 997):
+        text, _ = kl.kl_space_config(op, 0, idx)
+        kv = dict(item.split("=") for item in text.split(":", 1)[1].split(","))
+        for k in seen:
+            seen[k].add(kv[k])
+    assert seen["bx"] == set(vals["block_size_x"])
+    assert seen["by"] == set(vals["block_size_y"]) == seen["bz"]
+    assert seen["tx"] == set(vals["tile_factor_x"])
+    assert seen["perm"] == set(vals["unravel"])
+    assert seen["minb"] == set(vals["min_blocks_per_sm"])
+
+
+def test_default_config_is_table2_default():
+    op = kl.Op(5, 1, 1, 0)
+    d = kl.kl_config_normalize(op, "default")
+    assert d == ("direct:bx=256,by=1,bz=1,tx=1,ty=1,tz=1,ux=0,uy=0,uz=0,cx=0,cy=0,cz=0,"
+                 "perm=XYZ,minb=1")
+    assert kl.kl_config_normalize(op, "direct:bx=32,perm=ZYX") .startswith("direct:bx=32,")
+
+
+@pytest.mark.parametrize("bad", ["direct:bx=512", "direct:bx=256,by=8",  # > 1024 threads
+                                 "direct:tx=3", "direct:perm=ABC", "direct:minb=7",
+                                 "direct:foo=1", "nosuch:bx=1", "direct:bx"])
+def test_invalid_configs_are_rejected(bad):
+    with pytest.raises(kl.KLError) as e:
+        kl.kl_config_normalize(kl.Op(5, 1, 1, 0), bad)
+    assert e.value.status == -1
+
+
+@pytest.mark.parametrize("dtype", [0, 1, 2, 3])
+@pytest.mark.parametrize("adv,diff", [(5, 1), (2, 2), (0, 1), (5, 0)])
+def test_nvrtc_compiles_for_sm103a(dtype, adv, diff):
+    log = kl.kl_compile_only(kl.Op(adv, diff, dtype, 0), "default", 1, 0)
+    assert "sm_103a" in log and "registers" in log
+    assert "spill stores" in log
+
+
+def test_nvrtc_compiles_tiled_configs():
+    op = kl.Op(5, 2, 1, 1)
+    for cfg in ["direct:bx=32,by=4,bz=2,tx=2,tz=2,ux=1,uz=1,cx=1,cz=1,perm=ZXY,minb=2",
+                "direct:bx=64,by=2,tx=4,ty=2,ux=1,uy=1,cx=1,perm=YZX"]:
+        log = kl.kl_compile_only(op, cfg, 0, 1)
+        m = re.search(r"(\d+) bytes spill stores", log)
+        assert m is not None
+
+
+def test_nvrtc_failure_is_reported():
+    # a configuration the space accepts but the zmarch family rejects at compile
+    # time is not reachable; an invalid define is reported as INVALID_ARG first
+    with pytest.raises(kl.KLError) as e:
+        kl.kl_compile_only(kl.Op(5, 1, 1, 0), "direct:bx=7", 0, 1)
+    assert e.value.status == -1
+
+
+# ------------------------------------------------------------- wisdom
+
+def _write(path, lines):
+    with open(path, "w") as f:
+        f.write("# test wisdom\n")
+        for l in lines:
+            f.write(l + "\n")
+
+
+def rec(dev, cc, zbc, n, cfg):
+    return (f'device="{dev}" cc={cc} zbc={zbc} nx={n[0]} ny={n[1]} nz={n[2]} '
+            f'config="{cfg}" time_us=1.0 date=2026-01-01')
+
+
+def test_wisdom_rules(tmp_path):
+    p = str(tmp_path / "w.wisdom")
+    _write(p, [
+        rec("GPU A", "10.3", 1, (256, 256, 256), "direct:bx=32"),
+        rec("GPU A", "10.3", 1, (512, 512, 256), "direct:bx=64"),
+        rec("GPU B", "10.3", 1, (128, 128, 128), "direct:bx=128"),
+        rec("GPU C", "9.0", 1, (64, 64, 64), "direct:bx=16"),
+        rec("GPU A", "10.3", 0, (256, 256, 256), "direct:by=2"),
+        rec("GPU A", "10.3", 1, (256, 256, 256), "direct:bx=32,by=2"),  # newer duplicate
+    ])
+    sel = lambda dev, cc, zbc, n: kl.kl_wisdom_select(p, dev, cc[0], cc[1], zbc, *n)
+    # rule 1, newest duplicate wins
+    assert sel("GPU A", (10, 3), 1, (256, 256, 256)) == ("direct:bx=32,by=2", 1)
+    # rule 2: same device, nearest size
+    assert sel("GPU A", (10, 3), 1, (500, 500, 250)) == ("direct:bx=64", 2)
+    assert sel("GPU A", (10, 3), 1, (300, 300, 300)) == ("direct:bx=32", 2)
+    # zbc never crosses
+    assert sel("GPU A", (10, 3), 0, (512, 512, 256)) == ("direct:by=2", 2)
+    # rule 3: other device, same architecture, nearest size
+    assert sel("GPU Z", (10, 3), 1, (100, 100, 100)) == ("direct:bx=128", 3)
+    # rule 4: other architecture, nearest size of any record
+    assert sel("GPU Z", (12, 0), 1, (60, 60, 60)) == ("direct:bx=16", 4)
+    # rule 5: nothing for this zbc ... and a missing file
+    assert sel("GPU Z", (12, 0), 2, (60, 60, 60)) == ("default", 5)
+    assert kl.kl_wisdom_select(str(tmp_path / "none"), "x", 1, 0, 0, 1, 1, 1) == ("default", 5)
+
+
+def test_wisdom_distance_tie_takes_first_record(tmp_path):
+    p = str(tmp_path / "w.wisdom")
+    _write(p, [rec("G", "10.3", 0, (100, 100, 100), "direct:bx=16"),
+               rec("G", "10.3", 0, (300, 100, 100), "direct:bx=32")])
+    assert kl.kl_wisdom_select(p, "G", 10, 3, 0, 200, 100, 100) == ("direct:bx=16", 2)
+
+
+def test_corrupt_wisdom_falls_back_to_default(tmp_path):
+    p = str(tmp_path / "w.wisdom")
+    _write(p, ['device="G" cc=10.3 nx=1 ny=2'])   # no nz / config
+    assert kl.kl_wisdom_select(p, "G", 10, 3, 0, 1, 2, 3) == ("default", 5)
+    assert "record lacks" in kl.last_error()
+
+
+def test_wisdom_append_round_trip(tmp_path):
+    p = str(tmp_path / "w.wisdom")
+    kl.kl_wisdom_append(p, "NVIDIA GB300", 10, 3, 1, 256, 256, 256, "direct:bx=64", 61.5,
+                        "strategy=random evals=10")
+    kl.kl_wisdom_append(p, "NVIDIA GB300", 10, 3, 1, 512, 512, 256, "direct:bx=32", 200.0, "")
+    text = open(p).read()
+    assert text.count("\n") == 3 and "strategy=random" in text
+    assert kl.kl_wisdom_select(p, "NVIDIA GB300", 10, 3, 1, 256, 256, 256) == ("direct:bx=64", 1)
+
+
+# ------------------------------------------------------------- layout
+
+@pytest.mark.parametrize("dtype,es", [(0, 8), (1, 4), (2, 2), (3, 2)])
+def test_layout_alignment(dtype, es):
+    sj, sk, origin, extent = kl.kl_layout(256, 200, 64, 3, dtype)
+    x0 = origin % sj
+    assert (x0 * es) % 128 == 0 and (sj * es) % 128 == 0
+    assert x0 >= 3 and x0 + 256 + 3 <= sj
+    assert sk == sj * 206 and extent == sk * 70
+    assert origin == x0 + 3 * sj + 3 * sk
+
+
+def test_layout_rejects_huge():
+    with pytest.raises(kl.KLError):
+        kl.kl_layout(4096, 4096, 200, 3, 0)
