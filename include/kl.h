@@ -184,6 +184,26 @@ kl_status kl_tune(kl_ctx *ctx, const char *capture_path, const char *opts,
 kl_status kl_diag(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, int32_t level,
                   const void *t, const double *ref, double out[6], void *stream);
 
+/*
+ * kl_diag_noalloc: the diagnostics of kl_diag, for callers that may not
+ * allocate GPU memory while they run (an application that reserves its whole
+ * device-memory budget at start-up and owns the allocator, or a time loop
+ * that cannot take cudaMalloc's implicit synchronisation or failure between
+ * steps).  The paper has no counterpart; this is a library convenience.
+ * It needs no context and calls no allocating routine: its scratch is a
+ * static device array of 8192 x 6 + 8 doubles (~384 KB) that every GPU which
+ * loads libkl keeps until the process exits, so grids of at most 2^26
+ * interior points are accepted (larger ones: KL_ERR_INVALID_ARG, use kl_diag).
+ * t, ref, grid, out[6] as for kl_diag; wz (device, nz doubles, may be NULL
+ * for weights 1) gives the per-level weight of out[5] = sum t*wz[k].
+ * The first call on a device looks up the array's device address (a runtime
+ * call), so make it before any stream capture.  Every call reuses the same
+ * array: calls that overlap on the GPU race and must be serialised.
+ * Synchronises `stream`.
+ */
+kl_status kl_diag_noalloc(int32_t dtype, const kl_grid *grid, const void *t, const double *ref,
+                          const double *wz, double out[6], void *stream);
+
 /* Context statistics as JSON into buf (host, n bytes): cache hits/misses,
  * the four first-launch stage times of Sec. 5.6 (wisdom read, NVRTC,
  * module load, launch), launches, and the last selected record. */

@@ -2,6 +2,9 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <mutex>
+#include <string>
+
 #include "kl_internal.h"
 
 namespace {
@@ -238,3 +241,122 @@ cudaError_t diag_launch(int dtype, const kl_grid &g, int level, const void *t, c
 }
 
 }  // namespace kl
+
+// ==================================================== allocation-free diag
+//
+// kl_diag_noalloc is for callers that may not allocate GPU memory while they
+// run: applications that reserve their whole device-memory budget up front
+// and own the allocator, or time loops that cannot afford the implicit device
+// synchronisation and possible failure of cudaMalloc between steps.  Its
+// scratch (one partial record of 6 doubles per block of KL_NOALLOC_PTS
+// points, plus the 6 results) is this file-scope array, which every GPU that
+// loads the library keeps until the process exits.  Every call overwrites the
+// records it uses before reading them, so nothing has to start at zero; the
+// array is shared by all calls, so calls that overlap on the GPU (different
+// streams, or host threads) race and must be serialised by the caller.
+
+#define KL_NOALLOC_PTS 8192                    // interior points per block
+#define KL_NOALLOC_MAX_BLOCKS 8192             // => at most 2^26 interior points
+static __device__ __align__(256) double kl_noalloc_scratch[KL_NOALLOC_MAX_BLOCKS * 6 + 8];
+
+namespace {
+
+// As diag_kernel, but block b reduces the fixed point range
+// [b * KL_NOALLOC_PTS, (b + 1) * KL_NOALLOC_PTS), so the number of partial
+// records depends on the grid only.  wz may be NULL (weights 1).
+template <typename T>
+__global__ void __launch_bounds__(256) diag_kernel_fixed(DiagArgs a)
+{
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    const T *t = (const T *)a.t;
+    long long q0 = (long long)blockIdx.x * KL_NOALLOC_PTS;
+    long long q1 = q0 + KL_NOALLOC_PTS < a.n ? q0 + KL_NOALLOC_PTS : a.n;
+    for (long long q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+        int i = (int)(q % a.nx);
+        long long r = q / a.nx;
+        int j = (int)(r % a.ny);
+        int k = (int)(r / a.ny);
+        long long o = i + j * a.sj + k * a.sk;
+        double tv = to_d(t[o]);
+        double rv = a.ref ? a.ref[o] : 0.0;
+        double e = tv - rv;
+        v[0] = fmax(v[0], fabs(e));
+        v[1] += e * e;
+        v[2] = fmax(v[2], fabs(rv));
+        v[3] += rv * rv;
+        v[4] += tv;
+        v[5] += tv * (a.wz ? a.wz[k] : 1.0);
+    }
+    reduce6(v, a.partial + 6 * (size_t)blockIdx.x);
+}
+
+// device address of kl_noalloc_scratch per device, looked up once per device
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[256] = {nullptr};
+
+}  // namespace
+
+extern "C" kl_status kl_diag_noalloc(int32_t dtype, const kl_grid *grid, const void *t,
+                                     const double *ref, const double *wz, double out[6],
+                                     void *stream)
+{
+    using namespace kl;
+    if (!t || !out) return fail(KL_ERR_INVALID_ARG, "kl_diag_noalloc: t and out must not be NULL");
+    if (dtype < 0 || dtype > 3) return fail(KL_ERR_INVALID_ARG, "kl_diag_noalloc: dtype must be 0..3");
+    kl_status st = check_grid(grid, 1, nullptr);
+    if (st) return st;
+    long long n = (long long)grid->nx * grid->ny * grid->nz;
+    long long nb = (n + KL_NOALLOC_PTS - 1) / KL_NOALLOC_PTS;
+    if (nb > KL_NOALLOC_MAX_BLOCKS)
+        return fail(KL_ERR_INVALID_ARG,
+                    "kl_diag_noalloc: grid has " + std::to_string(n) +
+                        " interior points; the static scratch holds at most " +
+                        std::to_string((long long)KL_NOALLOC_MAX_BLOCKS * KL_NOALLOC_PTS) +
+                        " (use kl_diag)");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "kl_diag_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= 256) return fail(KL_ERR_UNSUPPORTED, "kl_diag_noalloc: device index >= 256");
+    double *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            // set-up, once per device, with that device current: the host-side
+            // name of the array is not a device address, so ask the runtime
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, kl_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "kl_diag_noalloc: cudaGetSymbolAddress");
+            g_noalloc_ptr[dev] = (double *)p;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    int es = esize_of(dtype);
+    DiagArgs a;
+    a.t = (const char *)t + (size_t)grid->origin * es;
+    a.ref = ref ? ref + grid->origin : nullptr;
+    a.wz = wz;
+    a.sj = grid->sj;
+    a.sk = grid->sk;
+    a.nx = grid->nx;
+    a.ny = grid->ny;
+    a.nz = grid->nz;
+    a.n = n;
+    a.partial = scratch;
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (dtype) {
+    case KL_F64: diag_kernel_fixed<double><<<(unsigned)nb, 256, 0, s>>>(a); break;
+    case KL_F32: diag_kernel_fixed<float><<<(unsigned)nb, 256, 0, s>>>(a); break;
+    case KL_BF16: diag_kernel_fixed<__nv_bfloat16><<<(unsigned)nb, 256, 0, s>>>(a); break;
+    default: diag_kernel_fixed<__half><<<(unsigned)nb, 256, 0, s>>>(a); break;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kl_diag_noalloc: launch");
+    double *res = scratch + (size_t)KL_NOALLOC_MAX_BLOCKS * 6;
+    diag_final<<<1, 256, 0, s>>>(scratch, (int)nb, n, res);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kl_diag_noalloc: launch");
+    e = cudaMemcpyAsync(out, res, 6 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "kl_diag_noalloc: readback");
+    return KL_OK;
+}

@@ -67,6 +67,8 @@ SIGNATURES = {
     "kl_tune": ([_P, _S, _S, _S], ctypes.c_int),
     "kl_diag": ([_P, _I32, ctypes.POINTER(Grid), _I32, _P, _P, ctypes.POINTER(_D), _P],
                 ctypes.c_int),
+    "kl_diag_noalloc": ([_I32, ctypes.POINTER(Grid), _P, _P, _P, ctypes.POINTER(_D), _P],
+                        ctypes.c_int),
     "kl_stats": ([_P, ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
     "kl_config_normalize": ([ctypes.POINTER(Op), _S, ctypes.c_char_p, ctypes.c_size_t],
                             ctypes.c_int),
@@ -169,6 +171,13 @@ def kl_tune(ctx, capture_path: str, opts: str, wisdom_path: str) -> None:
 def kl_diag(ctx, dtype, grid: Grid, level, t, ref=None, stream=None):
     out = (ctypes.c_double * 6)()
     check(load().kl_diag(ctx, dtype, ctypes.byref(grid), level, t, ref, out, stream))
+    return list(out)
+
+
+def kl_diag_noalloc(dtype, grid: Grid, t, ref=None, wz=None, stream=None):
+    """kl_diag without a context and without any allocation (static scratch)."""
+    out = (ctypes.c_double * 6)()
+    check(load().kl_diag_noalloc(dtype, ctypes.byref(grid), t, ref, wz, out, stream))
     return list(out)
 
 
