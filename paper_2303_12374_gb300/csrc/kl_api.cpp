@@ -120,20 +120,14 @@ kl_status nvrtc_compile(const std::string &defines, bool verbose, Compiled *out)
 
 // ------------------------------------------------------ kernel cache
 
-kl_status get_kernel(kl_ctx *ctx, const kl_op &op, const Config &cfg, int zbc, int zuni,
-                     Kernel **out)
+kl_status load_compiled(kl_ctx *ctx, const kl_op &op, const Config &cfg, const std::string &key,
+                        const Compiled &c, Kernel **out)
 {
-    std::string key = compile_defines(op, cfg, zbc, zuni);
     auto it = ctx->kernels.find(key);
     if (it != ctx->kernels.end()) {
         *out = &it->second;
         return KL_OK;
     }
-    auto t0 = std::chrono::steady_clock::now();
-    Compiled c;
-    kl_status st = nvrtc_compile(key, false, &c);
-    if (st) return st;
-    ctx->t_nvrtc_ms += ms_since(t0);
     auto t1 = std::chrono::steady_clock::now();
     Kernel k;
     k.cfg = cfg;
@@ -160,6 +154,23 @@ kl_status get_kernel(kl_ctx *ctx, const kl_op &op, const Config &cfg, int zbc, i
     auto ins = ctx->kernels.emplace(key, k);
     *out = &ins.first->second;
     return KL_OK;
+}
+
+kl_status get_kernel(kl_ctx *ctx, const kl_op &op, const Config &cfg, int zbc, int zuni,
+                     Kernel **out)
+{
+    std::string key = compile_defines(op, cfg, zbc, zuni);
+    auto it = ctx->kernels.find(key);
+    if (it != ctx->kernels.end()) {
+        *out = &it->second;
+        return KL_OK;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    Compiled c;
+    kl_status st = nvrtc_compile(key, false, &c);
+    if (st) return st;
+    ctx->t_nvrtc_ms += ms_since(t0);
+    return load_compiled(ctx, op, cfg, key, c, out);
 }
 
 // ----------------------------------------------------- z profiles
@@ -258,6 +269,64 @@ static void fill_coefs(KArgs &a, const kl_grid &g)
     }
 }
 
+bool config_fits(const kl_op &op, const Config &cfg, const kl_grid &g, const kl_fields *f,
+                 std::string *why)
+{
+    if (cfg.family == 0) return true;
+    Geom geo;
+    if (check_grid(&g, halo_of(op), &geo) != KL_OK) {
+        *why = "grid invalid";
+        return false;
+    }
+    int es = esize_of(op.dtype);
+    if ((geo.x0 * es) % 16 || (g.sj * es) % 16 || (g.sk * es) % 16) {
+        *why = "zmarch needs the interior x start and the strides 16-byte aligned";
+        return false;
+    }
+    if (f) {
+        const void *ps[4] = {f->u, f->v, f->w, op.diff == 2 ? f->nu : f->u};
+        for (const void *p : ps)
+            if ((uintptr_t)p % 16) {
+                *why = "zmarch needs 16-byte aligned field pointers";
+                return false;
+            }
+    }
+    return true;
+}
+
+// TMA descriptor of one field for the zmarch box; cached by pointer and layout
+static kl_status get_tmap(kl_ctx *ctx, const kl_op &op, const kl_grid &g, const ZGeom &z,
+                          const void *ptr, CUtensorMap *out)
+{
+    char key[256];
+    snprintf(key, sizeof key, "%p/%d/%lld/%lld/%lld/%d/%d", ptr, op.dtype, (long long)g.sj,
+             (long long)g.sk, (long long)g.extent, z.pitch, z.rows);
+    auto it = ctx->tmaps.find(key);
+    if (it != ctx->tmaps.end()) {
+        *out = it->second;
+        return KL_OK;
+    }
+    int es = esize_of(op.dtype);
+    CUtensorMapDataType dt = op.dtype == KL_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                             : op.dtype == KL_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                  : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    cuuint64_t dims[3] = {(cuuint64_t)g.sj, (cuuint64_t)(g.sk / g.sj), (cuuint64_t)(g.extent / g.sk)};
+    cuuint64_t strides[2] = {(cuuint64_t)(g.sj * es), (cuuint64_t)(g.sk * es)};
+    cuuint32_t box[3] = {(cuuint32_t)z.pitch, (cuuint32_t)z.rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUtensorMap m;
+    CUresult r = ctx->drv.TensorMapEncodeTiled(&m, dt, 3, const_cast<void *>(ptr), dims, strides, box,
+                                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                               CU_TENSOR_MAP_SWIZZLE_NONE,
+                                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cu_fail(r, "cuTensorMapEncodeTiled");
+    if (ctx->tmaps.size() > 4096) ctx->tmaps.clear();
+    ctx->tmaps[key] = m;
+    *out = m;
+    return KL_OK;
+}
+
 kl_status launch_config(kl_ctx *ctx, const kl_op &op, const Config &cfg, const kl_grid &g,
                         const kl_fields &f, cudaStream_t s)
 {
@@ -313,6 +382,7 @@ kl_status launch_config(kl_ctx *ctx, const kl_op &op, const Config &cfg, const k
     a.tile_z0 = geo.z0;
     fill_coefs(a, g);
 
+    if (!config_fits(op, cfg, g, &f, &err)) return fail(KL_ERR_INVALID_ARG, "configuration: " + err);
     CUresult r;
     if (cfg.family == 0) {
         a.nbx = (g.nx + cfg.bx * cfg.tx - 1) / (cfg.bx * cfg.tx);
@@ -324,7 +394,21 @@ kl_status launch_config(kl_ctx *ctx, const kl_op &op, const Config &cfg, const k
         r = ctx->drv.LaunchKernel(k->fn, (unsigned)nb, 1, 1, cfg.bx, cfg.by, cfg.bz, 0,
                                   (CUstream)s, params, nullptr);
     } else {
-        return fail(KL_ERR_UNSUPPORTED, "zmarch family not available in this build");
+        ZGeom z = zmarch_geometry(op, cfg);
+        CUtensorMap maps[4];
+        const void *fp[4] = {f.u, f.v, f.w, op.diff == 2 ? f.nu : f.u};
+        for (int q = 0; q < 4; ++q) {
+            st = get_tmap(ctx, op, g, z, fp[q], &maps[q]);
+            if (st) return st;
+        }
+        a.kchunk = cfg.kc;
+        unsigned gxn = (unsigned)((g.nx + z.txs - 1) / z.txs);
+        unsigned gyn = (unsigned)((g.ny + z.tys - 1) / z.tys);
+        unsigned gzn = (unsigned)((g.nz + cfg.kc - 1) / cfg.kc);
+        if (gyn > 65535 || gzn > 65535) return fail(KL_ERR_UNSUPPORTED, "grid too large");
+        void *params[] = {&a, &maps[0], &maps[1], &maps[2], &maps[3]};
+        r = ctx->drv.LaunchKernel(k->fn, gxn, gyn, gzn, cfg.mbx, cfg.mby, 1, (unsigned)k->smem,
+                                  (CUstream)s, params, nullptr);
     }
     if (r != CUDA_SUCCESS) return cu_fail(r, "cuLaunchKernel");
     if (miss) {
@@ -460,7 +544,8 @@ static kl_status select_config(kl_ctx *ctx, const kl_op &op, const kl_grid &g, C
         }
         // a record whose configuration is invalid here falls back to the default
         Config c;
-        if (!config_parse(text, &c, &err) || !config_check(op, c, &err)) {
+        if (!config_parse(text, &c, &err) || !config_check(op, c, &err) ||
+            !config_fits(op, c, g, nullptr, &err)) {
             ctx->last_rule_text = "wisdom config rejected (" + err + "); default used";
             text = "default";
             rule = 5;

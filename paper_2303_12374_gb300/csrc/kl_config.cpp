@@ -113,18 +113,31 @@ int halo_of(const kl_op &op) { return op.adv == 5 ? 3 : 1; }
 
 static int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
-// zmarch shared-memory plane: rows of (L + TXS + R) elements, TYS + 2H rows
+// zmarch shared-memory plane: rows of (L + TXS + R) elements, TYS + 2H rows;
+// identical formulas to the KL_PITCH / KL_ROWS / KL_PLANE_BYTES macros of
+// kl_stencil.cuh
+ZGeom zmarch_geometry(const kl_op &op, const Config &c)
+{
+    ZGeom z;
+    int es = esize_of(op.dtype), h = halo_of(op);
+    z.al = 16 / es;
+    z.txs = c.mbx * c.mpx;
+    z.tys = c.mby * c.mpy;
+    z.lpad = round_up(h, z.al);
+    z.pitch = round_up(z.lpad + z.txs + h, z.al);
+    z.rows = z.tys + 2 * h;
+    z.halo = h;
+    z.box_bytes = (size_t)z.pitch * z.rows * es;
+    z.plane_bytes = (z.box_bytes + 127) / 128 * 128;
+    z.nf = op.diff == 2 ? 4 : 3;
+    return z;
+}
+
 size_t zmarch_smem_bytes(const kl_op &op, const Config &c)
 {
-    int es = esize_of(op.dtype), h = halo_of(op), al = 16 / es;
-    int txs = c.mbx * c.mpx, tys = c.mby * c.mpy;
-    int left = round_up(h, al);
-    int pitch = round_up(left + txs + h, al);
-    int rows = tys + 2 * h;
-    int nf = op.diff == 2 ? 4 : 3;
-    size_t plane = (size_t)pitch * rows * es;
-    plane = (plane + 127) / 128 * 128;
-    return plane * nf * c.ns + 128;   // + mbarriers
+    ZGeom z = zmarch_geometry(op, c);
+    // ring + 128 B of alignment slack + one 8-byte mbarrier per slot
+    return z.plane_bytes * z.nf * c.ns + 256;
 }
 
 static bool in(int v, std::initializer_list<int> set)
@@ -172,8 +185,14 @@ bool config_check(const kl_op &op, const Config &c, std::string *err)
             *err = "more than 1024 threads per block";
             return false;
         }
-        if (c.ns < 7 + 1) {
-            *err = "plane ring needs at least 8 slots";
+        int reach = halo_of(op);
+        if (c.ns < 2 * reach + 2) {
+            *err = "plane ring needs at least 2R+2 slots";
+            return false;
+        }
+        ZGeom z = zmarch_geometry(op, c);
+        if (z.pitch > 256 || z.rows > 256) {
+            *err = "TMA box wider than 256 elements";
             return false;
         }
         size_t smem = zmarch_smem_bytes(op, c);

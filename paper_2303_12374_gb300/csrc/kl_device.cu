@@ -360,3 +360,65 @@ extern "C" kl_status kl_diag_noalloc(int32_t dtype, const kl_grid *grid, const v
     if (e != cudaSuccess) return cuda_fail(e, "kl_diag_noalloc: readback");
     return KL_OK;
 }
+
+// ============================================ output comparison (tuner)
+//
+// max |a - b| and max |b| over the interior of two fields of the same type,
+// accumulated as non-negative doubles by an integer atomicMax on their bits
+// (the order of non-negative IEEE doubles is the order of their bit patterns).
+
+namespace {
+
+template <typename T>
+__global__ void __launch_bounds__(256) compare_kernel(const T *a, const T *b, long long sj,
+                                                      long long sk, int nx, int ny, long long n,
+                                                      unsigned long long *out)
+{
+    double e = 0.0, m = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(q % nx);
+        long long r = q / nx;
+        int j = (int)(r % ny);
+        int k = (int)(r / ny);
+        long long o = i + j * sj + k * sk;
+        double x = to_d(a[o]), y = to_d(b[o]);
+        double d = fabs(x - y);
+        if (!(d <= 1e300)) d = 1e300;   // NaN or inf: worst possible
+        e = fmax(e, d);
+        m = fmax(m, fabs(y));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        e = fmax(e, __shfl_xor_sync(0xffffffffu, e, o));
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&out[0], (unsigned long long)__double_as_longlong(e));
+        atomicMax(&out[1], (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+}  // namespace
+
+namespace kl {
+
+cudaError_t compare_launch(int dtype, const kl_grid &g, const void *a, const void *b,
+                           unsigned long long *dout, int nsm, cudaStream_t s)
+{
+    int es = esize_of(dtype);
+    const char *pa = (const char *)a + (size_t)g.origin * es;
+    const char *pb = (const char *)b + (size_t)g.origin * es;
+    long long n = (long long)g.nx * g.ny * g.nz;
+    cudaError_t e = cudaMemsetAsync(dout, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    int nb = nsm * 4;
+    switch (dtype) {
+    case KL_F64: compare_kernel<double><<<nb, 256, 0, s>>>((const double *)pa, (const double *)pb, g.sj, g.sk, g.nx, g.ny, n, dout); break;
+    case KL_F32: compare_kernel<float><<<nb, 256, 0, s>>>((const float *)pa, (const float *)pb, g.sj, g.sk, g.nx, g.ny, n, dout); break;
+    case KL_BF16: compare_kernel<__nv_bfloat16><<<nb, 256, 0, s>>>((const __nv_bfloat16 *)pa, (const __nv_bfloat16 *)pb, g.sj, g.sk, g.nx, g.ny, n, dout); break;
+    default: compare_kernel<__half><<<nb, 256, 0, s>>>((const __half *)pa, (const __half *)pb, g.sj, g.sk, g.nx, g.ny, n, dout); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace kl

@@ -47,7 +47,13 @@ bool config_check(const kl_op &op, const Config &c, std::string *err);
 int64_t space_size(int family);
 bool space_config(int family, int64_t idx, Config *c);
 
-// dynamic shared memory of a zmarch configuration, bytes
+// tile / plane geometry of a zmarch configuration (mirrors the KL_* macros of
+// the kernel source) and its dynamic shared memory in bytes
+struct ZGeom {
+    int al, txs, tys, lpad, pitch, rows, halo, nf;
+    size_t box_bytes, plane_bytes;
+};
+ZGeom zmarch_geometry(const kl_op &op, const Config &c);
 size_t zmarch_smem_bytes(const kl_op &op, const Config &c);
 int halo_of(const kl_op &op);           // in-plane stencil reach (3 for adv5, else 1)
 int esize_of(int dtype);
@@ -152,6 +158,7 @@ struct kl_ctx {
     double *h_out = nullptr;                          // pinned, diag results
     // tile tables of batched launches, keyed by the batch signature
     std::map<std::string, std::pair<void *, size_t>> tables;
+    std::map<std::string, CUtensorMap> tmaps;         // TMA descriptors per buffer/box
     // statistics
     long long launches = 0, cache_hits = 0, cache_misses = 0;
     double t_wisdom_ms = 0, t_nvrtc_ms = 0, t_load_ms = 0, t_launch_ms = 0;
@@ -167,6 +174,9 @@ kl_status launch_config(kl_ctx *ctx, const kl_op &op, const Config &cfg, const k
 kl_status get_kernel(kl_ctx *ctx, const kl_op &op, const Config &cfg, int zbc, int zuni,
                      Kernel **out);
 kl_status get_profile(kl_ctx *ctx, const kl_grid &g, Profile **out);
+// can configuration cfg run on this grid's memory layout and pointers?
+bool config_fits(const kl_op &op, const Config &cfg, const kl_grid &g, const kl_fields *f,
+                 std::string *why);
 // device kernels of kl_device.cu
 cudaError_t fill_ghosts_launch(int esize, const kl_grid &g, void *u, void *v, void *w,
                                void *nu, cudaStream_t s);
@@ -174,4 +184,9 @@ cudaError_t diag_launch(int dtype, const kl_grid &g, int level, const void *t,
                         const double *ref, const double *wz, double *scratch, int nblocks,
                         double *dout, cudaStream_t s);
 int diag_blocks(int nsm);
+cudaError_t compare_launch(int dtype, const kl_grid &g, const void *a, const void *b,
+                           unsigned long long *dout, int nsm, cudaStream_t s);
+// load a compiled cubin into the context's cache under its compile key
+kl_status load_compiled(kl_ctx *ctx, const kl_op &op, const Config &cfg, const std::string &key,
+                        const Compiled &c, Kernel **out);
 }  // namespace kl

@@ -196,17 +196,43 @@ struct kl_coef {
 };
 
 // Tendencies of u, v, w at one point.  wall_w: w sits on a wall face (wt = 0).
+// Vertical advective fluxes of the point's column: the bottom ones (faces
+// below u, v and the centre below w) and the top ones.  A z-marching kernel
+// carries the top fluxes of level k as the bottom fluxes of level k+1.
 template <class Acc>
-__device__ __forceinline__ void kl_point(const Acc &A, const kl_coef &K, const kl_zmetric &Z,
-                                         bool wall_w, C &tu, C &tv, C &tw)
+__device__ __forceinline__ void kl_zflux_bottom(const Acc &A, C f[3])
+{
+#if KL_ADV
+    f[0] = FUZ(0); f[1] = FVZ(0); f[2] = FWZ(-1);
+#else
+    f[0] = f[1] = f[2] = C(0);
+#endif
+}
+
+template <class Acc>
+__device__ __forceinline__ void kl_zflux_top(const Acc &A, C f[3])
+{
+#if KL_ADV
+    f[0] = FUZ(1); f[1] = FVZ(1); f[2] = FWZ(0);
+#else
+    f[0] = f[1] = f[2] = C(0);
+#endif
+}
+
+// Tendencies of u, v, w at one point given its vertical fluxes (zb bottom,
+// zt top).  wall_w: w sits on a wall face (wt = 0).
+template <class Acc>
+__device__ __forceinline__ void kl_point_z(const Acc &A, const kl_coef &K, const kl_zmetric &Z,
+                                           const C zb[3], const C zt[3], bool wall_w,
+                                           C &tu, C &tv, C &tw)
 {
     tu = C(0); tv = C(0); tw = C(0);
 #if KL_ADV
     {
         C czu = KL_FS * Z.dzi, czw = KL_FS * Z.dzhi;
-        tu = -((FUX(0) - FUX(-1)) * K.cx + (FUY(1) - FUY(0)) * K.cy + (FUZ(1) - FUZ(0)) * czu);
-        tv = -((FVX(1) - FVX(0)) * K.cx + (FVY(0) - FVY(-1)) * K.cy + (FVZ(1) - FVZ(0)) * czu);
-        tw = -((FWX(1) - FWX(0)) * K.cx + (FWY(1) - FWY(0)) * K.cy + (FWZ(0) - FWZ(-1)) * czw);
+        tu = -((FUX(0) - FUX(-1)) * K.cx + (FUY(1) - FUY(0)) * K.cy + (zt[0] - zb[0]) * czu);
+        tv = -((FVX(1) - FVX(0)) * K.cx + (FVY(0) - FVY(-1)) * K.cy + (zt[1] - zb[1]) * czu);
+        tw = -((FWX(1) - FWX(0)) * K.cx + (FWY(1) - FWY(0)) * K.cy + (zt[2] - zb[2]) * czw);
     }
 #endif
 #if KL_DIFF == 1
@@ -265,6 +291,16 @@ __device__ __forceinline__ void kl_point(const Acc &A, const kl_coef &K, const k
     }
 #endif
     if (wall_w) tw = C(0);
+}
+
+template <class Acc>
+__device__ __forceinline__ void kl_point(const Acc &A, const kl_coef &K, const kl_zmetric &Z,
+                                         bool wall_w, C &tu, C &tv, C &tw)
+{
+    C zb[3], zt[3];
+    kl_zflux_bottom(A, zb);
+    kl_zflux_top(A, zt);
+    kl_point_z(A, K, Z, zb, zt, wall_w, tu, tv, tw);
 }
 
 __device__ __forceinline__ kl_coef kl_make_coef(const kl_args &a)
@@ -393,3 +429,218 @@ kl_tendency(const kl_args a)
         kl_direct_tile<false>(a, K, i0, j0, k0);
 }
 #endif  // KL_FAMILY == 0
+
+#if KL_FAMILY == 1
+// ======================================================= zmarch family
+//
+// A CTA of KL_MBX x KL_MBY threads owns an x-y tile of TXS x TYS interior
+// points (each thread KL_MPX consecutive x points times KL_MPY consecutive
+// rows) and marches up KL_KC levels.  Whole planes of the tile plus its
+// in-plane halo are streamed into a ring of KL_NS shared-memory slots by TMA
+// (one elected thread issues cp.async.bulk.tensor per field and plane; an
+// mbarrier per slot counts the bytes).  Level k reads planes k-R .. k+R from
+// the ring; its top vertical fluxes are kept in registers as the bottom
+// fluxes of level k+1, and the x / y fluxes that neighbouring points of the
+// same thread share are formed once (common subexpressions of identical
+// shared-memory loads).  Every wait is bounded: on time-out the CTA records
+// KL_DEV_TIMEOUT in the status word, drains its outstanding copies (again
+// bounded) and returns.
+
+#define KL_R (KL_ADV == 5 ? 3 : 1)                  // vertical reach
+#define KL_H (KL_ADV == 5 ? 3 : 1)                  // in-plane halo
+#define KL_AL (16 / (int)sizeof(T))                 // TMA x alignment, elements
+#define KL_RUP(a, b) (((a) + (b) - 1) / (b) * (b))
+#define KL_LPAD KL_RUP(KL_H, KL_AL)
+#define KL_TXS (KL_MBX * KL_MPX)
+#define KL_TYS (KL_MBY * KL_MPY)
+#define KL_PITCH KL_RUP(KL_LPAD + KL_TXS + KL_H, KL_AL)
+#define KL_ROWS (KL_TYS + 2 * KL_H)
+#define KL_BOX_BYTES (KL_PITCH * KL_ROWS * (int)sizeof(T))
+#define KL_PLANE_BYTES KL_RUP(KL_BOX_BYTES, 128)
+#define KL_NF (KL_DIFF == 2 ? 4 : 3)
+#define KL_SLOT_BYTES (KL_PLANE_BYTES * KL_NF)
+#define KL_DEV_TIMEOUT 1
+#define KL_WAIT_LIMIT (1 << 22)
+
+static_assert(KL_NS >= 2 * KL_R + 2, "ring must hold the stencil planes plus one in flight");
+static_assert(KL_PITCH <= 256 && KL_ROWS <= 256, "TMA box dimension above 256");
+
+struct __align__(64) kl_tmap { unsigned long long v[16]; };
+
+__device__ __forceinline__ unsigned kl_smem_addr(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void kl_mbar_init(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void kl_mbar_expect(unsigned bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool kl_mbar_try(unsigned bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// bounded wait (iteration cap and a clock64 deadline of ~2^31 cycles, about
+// one second); false on time-out
+__device__ __forceinline__ bool kl_mbar_wait(unsigned bar, unsigned parity)
+{
+    long long t0 = clock64();
+    for (int it = 0; it < KL_WAIT_LIMIT; ++it) {
+        if (kl_mbar_try(bar, parity)) return true;
+        if (clock64() - t0 > (1ll << 31)) break;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void kl_tma_load3(unsigned dst, const kl_tmap *map, int x, int y, int z,
+                                             unsigned bar)
+{
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4}], [%5];"
+                 ::"r"(dst), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(bar)
+                 : "memory");
+}
+
+struct kl_acc_smem {
+    const char *base[2 * KL_R + 1];     // slot base of plane k+dk, dk = -R..R
+    int off;                            // byte offset of the point inside a plane
+    template <int a, int b, int c> __device__ __forceinline__ C at(int f) const
+    {
+        static_assert(a >= -KL_H && a <= KL_H && b >= -KL_H && b <= KL_H, "offset outside the halo");
+        static_assert(c >= -KL_R && c <= KL_R, "offset outside the staged planes");
+        return lds((const T *)(base[c + KL_R] + f * KL_PLANE_BYTES + off +
+                               (a + b * KL_PITCH) * (int)sizeof(T)));
+    }
+    template <int a, int b, int c> __device__ __forceinline__ C U() const { return at<a, b, c>(0); }
+    template <int a, int b, int c> __device__ __forceinline__ C V() const { return at<a, b, c>(1); }
+    template <int a, int b, int c> __device__ __forceinline__ C W() const { return at<a, b, c>(2); }
+    template <int a, int b, int c> __device__ __forceinline__ C N() const { return at<a, b, c>(3); }
+};
+
+extern "C" __global__ void __launch_bounds__(KL_MBX * KL_MBY, KL_MMINB)
+kl_tendency(const kl_args a, const __grid_constant__ kl_tmap tm_u,
+            const __grid_constant__ kl_tmap tm_v, const __grid_constant__ kl_tmap tm_w,
+            const __grid_constant__ kl_tmap tm_n)
+{
+    extern __shared__ unsigned char kl_smem_raw[];
+    unsigned char *ring = (unsigned char *)(((unsigned long long)kl_smem_raw + 127) & ~127ull);
+    unsigned long long *bars = (unsigned long long *)(ring + KL_NS * KL_SLOT_BYTES);
+    const int tid = threadIdx.x + threadIdx.y * KL_MBX;
+    const int nx = (int)a.nx, ny = (int)a.ny, nz = (int)a.nz;
+    const int kb = blockIdx.z * (int)a.kchunk;
+    const int ke = min(kb + (int)a.kchunk, nz);
+    const int tx0 = blockIdx.x * KL_TXS, ty0 = blockIdx.y * KL_TYS;
+    const int gx = (int)a.tile_x0 + tx0 - KL_LPAD, gy = (int)a.tile_y0 + ty0 - KL_H;
+    const int gz0 = (int)a.tile_z0;
+    const kl_tmap *maps[4] = {&tm_u, &tm_v, &tm_w, &tm_n};
+
+    if (tid == 0) {
+        for (int s = 0; s < KL_NS; ++s) kl_mbar_init(kl_smem_addr(&bars[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+
+    // plane p (interior level) lives in ring slot (p - (kb - R)) mod NS
+    auto issue = [&](int p) {
+        int slot = (p - (kb - KL_R)) % KL_NS;
+        unsigned bar = kl_smem_addr(&bars[slot]);
+        kl_mbar_expect(bar, KL_NF * KL_BOX_BYTES);
+        unsigned dst = kl_smem_addr(ring + slot * KL_SLOT_BYTES);
+#pragma unroll
+        for (int f = 0; f < KL_NF; ++f)
+            kl_tma_load3(dst + f * KL_PLANE_BYTES, maps[f], gx, gy, gz0 + p, bar);
+    };
+    const int p_first = kb - KL_R;
+    const int p_last = ke - 1 + KL_R;                 // last plane this CTA needs
+    int p_next = p_first;                             // next plane to issue
+    if (tid == 0)
+        for (; p_next < p_first + KL_NS && p_next <= p_last; ++p_next) issue(p_next);
+
+    const kl_coef K = kl_make_coef(a);
+    const int lx = KL_LPAD + threadIdx.x * KL_MPX;
+    const int ly = KL_H + threadIdx.y * KL_MPY;
+    C zb[KL_MPY][KL_MPX][3];
+    bool timed_out = false;
+    int p_waited = p_first - 1;                       // every plane <= this has landed
+
+    for (int k = kb; k < ke; ++k) {
+        // the newest plane this level needs is k + R
+        {
+            int p = k + KL_R;
+            int use = (p - p_first) / KL_NS;
+            unsigned bar = kl_smem_addr(&bars[(p - p_first) % KL_NS]);
+            // at the first level also the planes below must have landed
+            if (k == kb) {
+                for (int q = p_first; q < p; ++q) {
+                    unsigned b2 = kl_smem_addr(&bars[(q - p_first) % KL_NS]);
+                    bool ok2 = kl_mbar_wait(b2, ((q - p_first) / KL_NS) & 1);
+                    if (__syncthreads_or(!ok2)) { timed_out = true; break; }
+                    p_waited = q;
+                }
+                if (timed_out) break;
+            }
+            bool ok = kl_mbar_wait(bar, use & 1);
+            if (__syncthreads_or(!ok)) { timed_out = true; break; }
+            p_waited = p;
+        }
+        kl_acc_smem A;
+#pragma unroll
+        for (int d = -KL_R; d <= KL_R; ++d)
+            A.base[d + KL_R] = (const char *)(ring + ((k + d - p_first) % KL_NS) * KL_SLOT_BYTES);
+        const kl_zmetric Z = kl_make_z(a, k);
+        const int k_out = k;
+#pragma unroll
+        for (int r = 0; r < KL_MPY; ++r) {
+#pragma unroll
+            for (int q = 0; q < KL_MPX; ++q) {
+                A.off = ((ly + r) * KL_PITCH + lx + q) * (int)sizeof(T);
+                C zt[3];
+                if (k == kb) kl_zflux_bottom(A, zb[r][q]);
+                kl_zflux_top(A, zt);
+                C tu, tv, tw;
+                kl_point_z(A, K, Z, zb[r][q], zt, KL_ZBC == 1 && k_out == 0, tu, tv, tw);
+                zb[r][q][0] = zt[0];
+                zb[r][q][1] = zt[1];
+                zb[r][q][2] = zt[2];
+                const int i = tx0 + threadIdx.x * KL_MPX + q;
+                const int j = ty0 + threadIdx.y * KL_MPY + r;
+                if (i < nx && j < ny) {
+                    long long o = i + (long long)j * a.sj + (long long)k_out * a.sk;
+                    out(a.ut + o, tu);
+                    out(a.vt + o, tv);
+                    out(a.wt + o, tw);
+                }
+            }
+        }
+        // every thread is done with plane k - R: refill its slot
+        __syncthreads();
+        if (tid == 0 && p_next <= p_last) issue(p_next++);
+    }
+
+    if (timed_out) {
+        if (tid == 0) {
+            atomicOr(a.err, KL_DEV_TIMEOUT);
+            // drain: wait (bounded) for the copies still in flight before
+            // leaving, so no TMA write lands in shared memory after exit
+            for (int q = p_waited + 1; q < p_next; ++q) {
+                unsigned b2 = kl_smem_addr(&bars[(q - p_first) % KL_NS]);
+                kl_mbar_wait(b2, ((q - p_first) / KL_NS) & 1);
+            }
+        }
+        __syncthreads();
+    }
+}
+#endif  // KL_FAMILY == 1

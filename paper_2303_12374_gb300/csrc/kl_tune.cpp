@@ -1,35 +1,823 @@
-// kl_tune.cpp -- batched launches, capture and the tuner.
+// kl_tune.cpp -- capture (Sec. 4.2), tuning (Sec. 4.3) with wisdom output
+// (Sec. 4.4), and batched launches over many grids.
+#include <nvrtc.h>
+#include <unistd.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <ctime>
+#include <fstream>
+#include <future>
+#include <random>
+#include <set>
+#include <sstream>
+#include <thread>
+
 #include "kl_internal.h"
+
+namespace kl {
+
+// ================================================================ helpers
+
+static std::string now_iso()
+{
+    time_t t = time(nullptr);
+    struct tm g;
+    gmtime_r(&t, &g);
+    char b[32];
+    strftime(b, sizeof b, "%Y-%m-%dT%H:%M:%SZ", &g);
+    return b;
+}
+
+static std::string host_name()
+{
+    char b[256] = {0};
+    if (gethostname(b, sizeof b - 1) != 0) return "unknown";
+    return b;
+}
+
+static const char *dtype_tag(int d)
+{
+    return d == KL_F64 ? "f64" : d == KL_F32 ? "f32" : d == KL_BF16 ? "bf16" : "f16";
+}
+
+// ================================================================ capture
+//
+// File layout: a text header of key=value lines ending with "END\n", then the
+// raw device buffers (each `extent` elements of the storage type) in the order
+// the header's blobs= line lists.  The header carries the kernel definition
+// (op), the problem (grid, layout, scalars, vertical grid) and provenance.
+
+struct Capture {
+    kl_op op;
+    kl_grid grid;
+    std::vector<double> zh;
+    std::string device;
+    int cc_major = 0, cc_minor = 0;
+    std::vector<std::string> names;
+    size_t blob_bytes = 0;
+    std::vector<std::vector<char>> blobs;
+};
+
+static std::vector<std::string> capture_blob_names(const kl_op &op)
+{
+    std::vector<std::string> n = {"u", "v", "w"};
+    if (op.diff == 2) n.push_back("nu");
+    if (op.accumulate) {
+        n.push_back("ut");
+        n.push_back("vt");
+        n.push_back("wt");
+    }
+    return n;
+}
+
+kl_status capture_write(kl_ctx *ctx, const kl_op &op, const kl_grid &g, const kl_fields &f,
+                        const std::string &path, cudaStream_t s)
+{
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "capture: stream sync");
+    std::vector<std::string> names = capture_blob_names(op);
+    std::map<std::string, const void *> ptr = {{"u", f.u}, {"v", f.v}, {"w", f.w}, {"nu", f.nu},
+                                                {"ut", f.ut}, {"vt", f.vt}, {"wt", f.wt}};
+    size_t bytes = (size_t)g.extent * esize_of(op.dtype);
+    FILE *out = fopen(path.c_str(), "wb");
+    if (!out) return fail(KL_ERR_IO, "capture: cannot open " + path);
+    fprintf(out, "KLCAPTURE 1\n");
+    fprintf(out, "kernel=tendency adv=%d diff=%d dtype=%d accumulate=%d\n", op.adv, op.diff,
+            op.dtype, op.accumulate);
+    fprintf(out, "nx=%d ny=%d nz=%d g=%d sj=%lld sk=%lld origin=%lld extent=%lld zbc=%d\n", g.nx,
+            g.ny, g.nz, g.g, (long long)g.sj, (long long)g.sk, (long long)g.origin,
+            (long long)g.extent, g.zbc);
+    fprintf(out, "dx=%.17g dy=%.17g dz=%.17g nu=%.17g\n", g.dx, g.dy, g.dz, g.nu);
+    fprintf(out, "zh=%d", g.zh ? g.nz + 1 : 0);
+    if (g.zh)
+        for (int k = 0; k <= g.nz; ++k) fprintf(out, " %.17g", g.zh[k]);
+    fprintf(out, "\n");
+    fprintf(out, "device=\"%s\" cc=%d.%d date=%s host=%s\n", ctx->name.c_str(), ctx->cc_major,
+            ctx->cc_minor, now_iso().c_str(), host_name().c_str());
+    std::string list;
+    for (auto &n : names) list += (list.empty() ? "" : ",") + n;
+    fprintf(out, "blobs=%s bytes=%zu\nEND\n", list.c_str(), bytes);
+    std::vector<char> host(bytes);
+    for (auto &n : names) {
+        e = cudaMemcpy(host.data(), ptr[n], bytes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            fclose(out);
+            return cuda_fail(e, "capture: device to host copy");
+        }
+        if (fwrite(host.data(), 1, bytes, out) != bytes) {
+            fclose(out);
+            return fail(KL_ERR_IO, "capture: short write to " + path);
+        }
+    }
+    if (fclose(out) != 0) return fail(KL_ERR_IO, "capture: close failed for " + path);
+    return KL_OK;
+}
+
+static bool kv_line(const std::string &line, std::map<std::string, std::string> *kv)
+{
+    std::stringstream ss(line);
+    std::string tok;
+    bool any = false;
+    // values are single tokens except device="..." which may hold spaces
+    size_t p = 0;
+    while (p < line.size()) {
+        while (p < line.size() && line[p] == ' ') ++p;
+        size_t eq = line.find('=', p);
+        if (eq == std::string::npos) break;
+        std::string k = line.substr(p, eq - p);
+        p = eq + 1;
+        std::string v;
+        if (p < line.size() && line[p] == '"') {
+            size_t q = line.find('"', p + 1);
+            if (q == std::string::npos) return false;
+            v = line.substr(p + 1, q - p - 1);
+            p = q + 1;
+        } else {
+            size_t q = line.find(' ', p);
+            if (q == std::string::npos) q = line.size();
+            v = line.substr(p, q - p);
+            p = q;
+        }
+        (*kv)[k] = v;
+        any = true;
+    }
+    return any;
+}
+
+kl_status capture_read(const std::string &path, Capture *c)
+{
+    FILE *in = fopen(path.c_str(), "rb");
+    if (!in) return fail(KL_ERR_IO, "capture: cannot open " + path);
+    std::map<std::string, std::string> kv;
+    std::vector<double> zh;
+    char line[1 << 16];
+    bool magic = false, end = false;
+    while (fgets(line, sizeof line, in)) {
+        std::string l(line);
+        while (!l.empty() && (l.back() == '\n' || l.back() == '\r')) l.pop_back();
+        if (!magic) {
+            if (l != "KLCAPTURE 1") break;
+            magic = true;
+            continue;
+        }
+        if (l == "END") {
+            end = true;
+            break;
+        }
+        if (l.rfind("zh=", 0) == 0) {
+            std::stringstream ss(l.substr(3));
+            int n = 0;
+            ss >> n;
+            for (int q = 0; q < n; ++q) {
+                double x;
+                if (!(ss >> x)) break;
+                zh.push_back(x);
+            }
+            if ((int)zh.size() != n) {
+                fclose(in);
+                return fail(KL_ERR_WISDOM_PARSE, "capture: bad zh line");
+            }
+            continue;
+        }
+        kv_line(l, &kv);
+    }
+    if (!magic || !end) {
+        fclose(in);
+        return fail(KL_ERR_WISDOM_PARSE, "capture: not a capture file: " + path);
+    }
+    auto geti = [&](const char *k, long long *v) {
+        auto it = kv.find(k);
+        if (it == kv.end()) return false;
+        char *e = nullptr;
+        *v = strtoll(it->second.c_str(), &e, 10);
+        return e && *e == 0;
+    };
+    auto getd = [&](const char *k, double *v) {
+        auto it = kv.find(k);
+        if (it == kv.end()) return false;
+        char *e = nullptr;
+        *v = strtod(it->second.c_str(), &e);
+        return e && *e == 0;
+    };
+    long long adv, diff, dtype, acc, nx, ny, nz, g, sj, sk, origin, extent, zbc;
+    double dx, dy, dz, nu;
+    long long bytes;
+    if (!geti("adv", &adv) || !geti("diff", &diff) || !geti("dtype", &dtype) ||
+        !geti("accumulate", &acc) || !geti("nx", &nx) || !geti("ny", &ny) || !geti("nz", &nz) ||
+        !geti("g", &g) || !geti("sj", &sj) || !geti("sk", &sk) || !geti("origin", &origin) ||
+        !geti("extent", &extent) || !geti("zbc", &zbc) || !getd("dx", &dx) || !getd("dy", &dy) ||
+        !getd("dz", &dz) || !getd("nu", &nu) || !geti("bytes", &bytes)) {
+        fclose(in);
+        return fail(KL_ERR_WISDOM_PARSE, "capture: header lacks a field: " + path);
+    }
+    c->op = kl_op{(int)adv, (int)diff, (int)dtype, (int)acc};
+    c->zh = zh;
+    kl_grid &G = c->grid;
+    memset(&G, 0, sizeof G);
+    G.nx = (int)nx; G.ny = (int)ny; G.nz = (int)nz; G.g = (int)g;
+    G.sj = sj; G.sk = sk; G.origin = origin; G.extent = extent; G.zbc = (int)zbc;
+    G.dx = dx; G.dy = dy; G.dz = dz; G.nu = nu;
+    G.zh = nullptr;   // set by the user of the capture (points into c->zh)
+    if (!zh.empty() && (int)zh.size() != nz + 1) {
+        fclose(in);
+        return fail(KL_ERR_WISDOM_PARSE, "capture: zh has the wrong length");
+    }
+    c->device = kv["device"];
+    sscanf(kv["cc"].c_str(), "%d.%d", &c->cc_major, &c->cc_minor);
+    std::stringstream ss(kv["blobs"]);
+    std::string n;
+    while (std::getline(ss, n, ',')) c->names.push_back(n);
+    if (c->names != capture_blob_names(c->op) ||
+        (size_t)bytes != (size_t)extent * esize_of((int)dtype)) {
+        fclose(in);
+        return fail(KL_ERR_WISDOM_PARSE, "capture: blob list or size does not match the op");
+    }
+    c->blob_bytes = (size_t)bytes;
+    for (size_t q = 0; q < c->names.size(); ++q) {
+        std::vector<char> b(c->blob_bytes);
+        if (fread(b.data(), 1, b.size(), in) != b.size()) {
+            fclose(in);
+            return fail(KL_ERR_WISDOM_PARSE, "capture: truncated data in " + path);
+        }
+        c->blobs.push_back(std::move(b));
+    }
+    fclose(in);
+    return KL_OK;
+}
+
+// ================================================================= tuner
+
+struct TuneOpts {
+    std::string strategy = "random";
+    double budget_s = 60;
+    int max_evals = 200;
+    unsigned seed = 1;
+    std::string family = "all";
+    double verify_tol = -1;
+    std::string log;
+    int reps = 7;
+    int warm = 2;
+    int topk = 3;
+    int threads = 0;
+};
+
+static kl_status parse_opts(const char *text, TuneOpts *o)
+{
+    if (!text) return KL_OK;
+    std::stringstream ss(text);
+    std::string tok;
+    while (ss >> tok) {
+        size_t eq = tok.find('=');
+        if (eq == std::string::npos) return fail(KL_ERR_INVALID_ARG, "tune option without '=': " + tok);
+        std::string k = tok.substr(0, eq), v = tok.substr(eq + 1);
+        if (k == "strategy") o->strategy = v;
+        else if (k == "budget_s") o->budget_s = atof(v.c_str());
+        else if (k == "max_evals") o->max_evals = atoi(v.c_str());
+        else if (k == "seed") o->seed = (unsigned)strtoul(v.c_str(), nullptr, 10);
+        else if (k == "family") o->family = v;
+        else if (k == "verify_tol") o->verify_tol = atof(v.c_str());
+        else if (k == "log") o->log = v;
+        else if (k == "reps") o->reps = std::max(1, atoi(v.c_str()));
+        else if (k == "warm") o->warm = std::max(0, atoi(v.c_str()));
+        else if (k == "topk") o->topk = std::max(1, atoi(v.c_str()));
+        else if (k == "threads") o->threads = atoi(v.c_str());
+        else return fail(KL_ERR_INVALID_ARG, "unknown tune option '" + k + "'");
+    }
+    if (o->strategy != "random" && o->strategy != "exhaustive" && o->strategy != "local")
+        return fail(KL_ERR_INVALID_ARG, "strategy must be random, exhaustive or local");
+    if (o->family != "all" && o->family != "direct" && o->family != "zmarch")
+        return fail(KL_ERR_INVALID_ARG, "family must be all, direct or zmarch");
+    return KL_OK;
+}
+
+// device buffers of one replay
+struct Replay {
+    std::vector<void *> in;        // u, v, w, nu (nu may be null)
+    void *out[3] = {nullptr, nullptr, nullptr};
+    void *ref[3] = {nullptr, nullptr, nullptr};
+    void *init[3] = {nullptr, nullptr, nullptr};   // accumulate: pristine outputs
+    unsigned long long *cmp = nullptr;
+    size_t bytes = 0;
+    ~Replay()
+    {
+        for (void *p : in) cudaFree(p);
+        for (int q = 0; q < 3; ++q) {
+            cudaFree(out[q]);
+            cudaFree(ref[q]);
+            cudaFree(init[q]);
+        }
+        cudaFree(cmp);
+    }
+};
+
+struct Eval {
+    std::string config;
+    double time_us = INFINITY;
+    double err = INFINITY;
+    bool ok = false;
+    std::string note;
+};
+
+static std::string json_escape(const std::string &s)
+{
+    std::string o;
+    for (char ch : s) {
+        if (ch == '"' || ch == '\\') o += '\\';
+        if (ch == '\n') { o += "\\n"; continue; }
+        o += ch;
+    }
+    return o;
+}
+
+static void log_eval(const std::string &path, const Eval &e, double t)
+{
+    if (path.empty()) return;
+    FILE *f = fopen(path.c_str(), "a");
+    if (!f) return;
+    fprintf(f, "{\"config\":\"%s\",\"time_us\":%.4f,\"err\":%.3e,\"ok\":%s,\"t_s\":%.3f,\"note\":\"%s\"}\n",
+            e.config.c_str(), std::isfinite(e.time_us) ? e.time_us : -1.0,
+            std::isfinite(e.err) ? e.err : -1.0, e.ok ? "true" : "false", t,
+            json_escape(e.note).c_str());
+    fclose(f);
+}
+
+// previously evaluated configurations of a session (resume after a kill)
+static void read_log(const std::string &path, std::map<std::string, Eval> *done)
+{
+    if (path.empty()) return;
+    std::ifstream in(path);
+    std::string line;
+    while (std::getline(in, line)) {
+        auto grab = [&](const char *key) -> std::string {
+            std::string k = std::string("\"") + key + "\":";
+            size_t p = line.find(k);
+            if (p == std::string::npos) return "";
+            p += k.size();
+            if (line[p] == '"') {
+                size_t q = line.find('"', p + 1);
+                return line.substr(p + 1, q - p - 1);
+            }
+            size_t q = line.find_first_of(",}", p);
+            return line.substr(p, q - p);
+        };
+        Eval e;
+        e.config = grab("config");
+        if (e.config.empty()) continue;
+        double t = atof(grab("time_us").c_str());
+        e.time_us = t > 0 ? t : INFINITY;
+        double er = atof(grab("err").c_str());
+        e.err = er >= 0 ? er : INFINITY;
+        e.ok = grab("ok") == "true";
+        e.note = "resumed";
+        (*done)[e.config] = e;
+    }
+}
+
+// time one configuration: median of `reps` launches after `warm` launches
+static kl_status time_config(kl_ctx *ctx, const kl_op &op, const Config &cfg, const kl_grid &g,
+                             Replay &R, int warm, int reps, double *median_us)
+{
+    kl_fields f{R.in[0], R.in[1], R.in[2], R.in.size() > 3 ? R.in[3] : nullptr, R.out[0],
+                R.out[1], R.out[2]};
+    cudaStream_t s = 0;
+    std::vector<cudaEvent_t> ev(2 * reps);
+    for (auto &e : ev) cudaEventCreate(&e);
+    kl_status st = KL_OK;
+    for (int q = 0; q < warm && !st; ++q) st = launch_config(ctx, op, cfg, g, f, s);
+    for (int q = 0; q < reps && !st; ++q) {
+        cudaEventRecord(ev[2 * q], s);
+        st = launch_config(ctx, op, cfg, g, f, s);
+        cudaEventRecord(ev[2 * q + 1], s);
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    std::vector<float> ms;
+    if (!st && e == cudaSuccess)
+        for (int q = 0; q < reps; ++q) {
+            float t = 0;
+            cudaEventElapsedTime(&t, ev[2 * q], ev[2 * q + 1]);
+            ms.push_back(t);
+        }
+    for (auto &x : ev) cudaEventDestroy(x);
+    if (st) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "tune: launch");
+    std::sort(ms.begin(), ms.end());
+    *median_us = 1e3 * ms[ms.size() / 2];
+    return KL_OK;
+}
+
+// relative error of the candidate outputs against the reference outputs
+static kl_status verify(kl_ctx *ctx, const kl_op &op, const kl_grid &g, Replay &R, double *err)
+{
+    double worst = 0;
+    for (int q = 0; q < 3; ++q) {
+        cudaError_t e = compare_launch(op.dtype, g, R.out[q], R.ref[q], R.cmp, ctx->nsm, 0);
+        unsigned long long h[2];
+        if (e == cudaSuccess) e = cudaMemcpy(h, R.cmp, sizeof h, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "tune: verify");
+        double d, m;
+        memcpy(&d, &h[0], 8);
+        memcpy(&m, &h[1], 8);
+        double r = m > 0 ? d / m : d;
+        worst = std::max(worst, r);
+    }
+    *err = worst;
+    return KL_OK;
+}
+
+static kl_status reset_outputs(const kl_op &op, Replay &R)
+{
+    if (!op.accumulate) return KL_OK;
+    for (int q = 0; q < 3; ++q) {
+        cudaError_t e = cudaMemcpy(R.out[q], R.init[q], R.bytes, cudaMemcpyDeviceToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "tune: reset outputs");
+    }
+    return KL_OK;
+}
+
+// candidate generation ---------------------------------------------------
+
+static bool valid_for(const kl_op &op, const kl_grid &g, int family, int64_t idx, Config *c)
+{
+    if (!space_config(family, idx, c)) return false;
+    std::string err;
+    return config_check(op, *c, &err) && config_fits(op, *c, g, nullptr, &err);
+}
+
+static std::vector<int> radices(int family)
+{
+    if (family == 0) return {5, 5, 5, 3, 3, 3, 2, 2, 2, 2, 2, 2, 6, 6};
+    return {3, 5, 3, 3, 7, 4, 4};
+}
+
+static std::vector<int64_t> neighbours(int family, int64_t idx)
+{
+    std::vector<int> r = radices(family);
+    std::vector<int> d(r.size());
+    int64_t x = idx;
+    for (size_t q = 0; q < r.size(); ++q) {
+        d[q] = (int)(x % r[q]);
+        x /= r[q];
+    }
+    std::vector<int64_t> out;
+    for (size_t q = 0; q < r.size(); ++q)
+        for (int step : {-1, 1}) {
+            int v = d[q] + step;
+            if (v < 0 || v >= r[q]) continue;
+            std::vector<int> e = d;
+            e[q] = v;
+            int64_t y = 0;
+            for (size_t p = r.size(); p-- > 0;) y = y * r[p] + e[p];
+            out.push_back(y);
+        }
+    return out;
+}
+
+}  // namespace kl
 
 using namespace kl;
 
 extern "C" {
+
+kl_status kl_capture(kl_ctx *ctx, const kl_op *op, const kl_grid *grid, const kl_fields *fields,
+                     const char *path, void *stream)
+{
+    if (!ctx || !op || !grid || !fields || !path) return fail(KL_ERR_INVALID_ARG, "NULL argument");
+    kl_status st = check_grid(grid, halo_of(*op), nullptr);
+    if (st) return st;
+    if (!fields->u || !fields->v || !fields->w || (op->diff == 2 && !fields->nu) ||
+        (op->accumulate && (!fields->ut || !fields->vt || !fields->wt)))
+        return fail(KL_ERR_INVALID_ARG, "capture: a needed field pointer is NULL");
+    return capture_write(ctx, *op, *grid, *fields, path, (cudaStream_t)stream);
+}
+
+// called by kl_launch when $KERNEL_LAUNCHER_CAPTURE lists "tendency": one
+// capture per problem per process, into $KL_CAPTURE_DIR
+kl_status kl_capture_if_requested(kl_ctx *ctx, const kl_op *op, const kl_grid *grid,
+                                  const kl_fields *fields, void *stream)
+{
+    char name[256];
+    snprintf(name, sizeof name, "tendency_adv%d_diff%d_%s%s_%dx%dx%d_zbc%d.klcap", op->adv,
+             op->diff, dtype_tag(op->dtype), op->accumulate ? "_acc" : "", grid->nx, grid->ny,
+             grid->nz, grid->zbc);
+    std::string key = std::string("capture:") + name;
+    if (ctx->selection.count(key)) return KL_OK;
+    const char *dir = getenv("KL_CAPTURE_DIR");
+    std::string path = std::string(dir && *dir ? dir : ".") + "/" + name;
+    kl_status st = capture_write(ctx, *op, *grid, *fields, path, (cudaStream_t)stream);
+    if (st) return st;
+    ctx->selection[key] = path;
+    return KL_OK;
+}
+
+kl_status kl_tune(kl_ctx *ctx, const char *capture_path, const char *opts, const char *wisdom_path)
+{
+    if (!ctx || !capture_path || !wisdom_path) return fail(KL_ERR_INVALID_ARG, "NULL argument");
+    TuneOpts O;
+    kl_status st = parse_opts(opts, &O);
+    if (st) return st;
+    auto t_start = std::chrono::steady_clock::now();
+    auto elapsed = [&]() {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    };
+    Capture C;
+    st = capture_read(capture_path, &C);
+    if (st) return st;
+    kl_op op = C.op;
+    kl_grid g = C.grid;
+    if (!C.zh.empty()) g.zh = C.zh.data();
+    st = check_grid(&g, halo_of(op), nullptr);
+    if (st) return st;
+
+    // device buffers
+    Replay R;
+    R.bytes = C.blob_bytes;
+    auto alloc = [&](void **p) { return cudaMalloc(p, R.bytes); };
+    size_t nin = op.diff == 2 ? 4 : 3;
+    for (size_t q = 0; q < nin; ++q) {
+        void *p = nullptr;
+        if (alloc(&p) != cudaSuccess) return fail(KL_ERR_OOM, "tune: device allocation failed");
+        R.in.push_back(p);
+        if (cudaMemcpy(p, C.blobs[q].data(), R.bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(KL_ERR_CUDA, "tune: upload failed");
+    }
+    for (int q = 0; q < 3; ++q) {
+        if (alloc(&R.out[q]) != cudaSuccess || alloc(&R.ref[q]) != cudaSuccess)
+            return fail(KL_ERR_OOM, "tune: device allocation failed");
+        cudaMemset(R.out[q], 0, R.bytes);
+        cudaMemset(R.ref[q], 0, R.bytes);
+        if (op.accumulate) {
+            if (alloc(&R.init[q]) != cudaSuccess) return fail(KL_ERR_OOM, "tune: allocation failed");
+            cudaMemcpy(R.init[q], C.blobs[nin + q].data(), R.bytes, cudaMemcpyHostToDevice);
+            cudaMemcpy(R.ref[q], R.init[q], R.bytes, cudaMemcpyDeviceToDevice);
+        }
+    }
+    if (cudaMalloc(&R.cmp, 2 * sizeof(unsigned long long)) != cudaSuccess)
+        return fail(KL_ERR_OOM, "tune: allocation failed");
+
+    // reference output: the default configuration, launched once
+    Config def;
+    {
+        kl_fields f{R.in[0], R.in[1], R.in[2], nin > 3 ? R.in[3] : nullptr, R.ref[0], R.ref[1], R.ref[2]};
+        st = launch_config(ctx, op, def, g, f, 0);
+        if (st) return st;
+        if (cudaDeviceSynchronize() != cudaSuccess) return fail(KL_ERR_CUDA, "tune: reference run failed");
+    }
+    double tol = O.verify_tol > 0 ? O.verify_tol
+                 : op.dtype == KL_F64 ? 1e-10 : op.dtype == KL_F32 ? 1e-4 : 2e-2;
+
+    // candidates
+    std::mt19937_64 rng(O.seed);
+    std::vector<int> fams;
+    if (O.family != "zmarch") fams.push_back(0);
+    if (O.family != "direct") fams.push_back(1);
+    std::map<std::string, Eval> done;
+    read_log(O.log, &done);
+    std::set<std::string> queued;
+    for (auto &p : done) queued.insert(p.first);
+    auto draw_random = [&](Config *c) {
+        for (int tries = 0; tries < 100000; ++tries) {
+            int fam = fams[rng() % fams.size()];
+            int64_t idx = (int64_t)(rng() % (uint64_t)space_size(fam));
+            if (valid_for(op, g, fam, idx, c)) {
+                std::string s = config_string(*c);
+                if (!queued.count(s)) return true;
+            }
+        }
+        return false;
+    };
+    // exhaustive order: the zmarch family first (small), then direct by index
+    int64_t ex_fam = 0, ex_idx = 0;
+    std::vector<int> ex_fams = fams;
+    std::reverse(ex_fams.begin(), ex_fams.end());
+    auto draw_exhaustive = [&](Config *c) {
+        while (ex_fam < (int64_t)ex_fams.size()) {
+            int fam = ex_fams[ex_fam];
+            while (ex_idx < space_size(fam)) {
+                int64_t idx = ex_idx++;
+                if (valid_for(op, g, fam, idx, c) && !queued.count(config_string(*c))) return true;
+            }
+            ++ex_fam;
+            ex_idx = 0;
+        }
+        return false;
+    };
+    // local search: neighbours of the best evaluated configuration
+    auto index_of = [&](const Config &c, int64_t *idx) {
+        // brute inverse over the digits of the family's space
+        std::vector<int> r = radices(c.family);
+        int64_t total = space_size(c.family);
+        (void)total;
+        Config probe;
+        // encode by matching each digit's value list
+        std::vector<std::vector<int>> vals;
+        if (c.family == 0)
+            vals = {{16, 32, 64, 128, 256}, {1, 2, 4, 8, 16}, {1, 2, 4, 8, 16}, {1, 2, 4}, {1, 2, 4},
+                    {1, 2, 4}, {0, 1}, {0, 1}, {0, 1}, {0, 1}, {0, 1}, {0, 1}, {0, 1, 2, 3, 4, 5},
+                    {1, 2, 3, 4, 5, 6}};
+        else
+            vals = {{32, 64, 128}, {1, 2, 4, 8, 16}, {1, 2, 4}, {1, 2, 4}, {4, 8, 16, 32, 64, 128, 256},
+                    {8, 9, 10, 12}, {1, 2, 3, 4}};
+        std::vector<int> cur = c.family == 0
+            ? std::vector<int>{c.bx, c.by, c.bz, c.tx, c.ty, c.tz, c.ux, c.uy, c.uz, c.cx, c.cy, c.cz, c.perm, c.minb}
+            : std::vector<int>{c.mbx, c.mby, c.mpx, c.mpy, c.kc, c.ns, c.mminb};
+        int64_t y = 0;
+        for (size_t p = r.size(); p-- > 0;) {
+            auto it = std::find(vals[p].begin(), vals[p].end(), cur[p]);
+            if (it == vals[p].end()) return false;
+            y = y * r[p] + (int64_t)(it - vals[p].begin());
+        }
+        *idx = y;
+        return true;
+    };
+    std::vector<Eval> evals;
+    for (auto &p : done) evals.push_back(p.second);
+    auto best_so_far = [&]() -> const Eval * {
+        const Eval *b = nullptr;
+        for (auto &e : evals)
+            if (e.ok && (!b || e.time_us < b->time_us)) b = &e;
+        return b;
+    };
+    int random_phase = std::max(8, O.max_evals / 4);
+    int produced = 0;
+    auto next_candidate = [&](Config *c) -> bool {
+        if (O.strategy == "exhaustive") return draw_exhaustive(c);
+        if (O.strategy == "local" && produced >= random_phase) {
+            const Eval *b = best_so_far();
+            Config bc;
+            std::string err;
+            int64_t idx;
+            if (b && config_parse(b->config, &bc, &err) && index_of(bc, &idx)) {
+                std::vector<int64_t> nb = neighbours(bc.family, idx);
+                std::shuffle(nb.begin(), nb.end(), rng);
+                for (int64_t n : nb)
+                    if (valid_for(op, g, bc.family, n, c) && !queued.count(config_string(*c)))
+                        return true;
+            }
+        }
+        return draw_random(c);
+    };
+
+    // compile ahead on host threads (NVRTC only; modules load on this thread)
+    int nthreads = O.threads > 0 ? O.threads
+                   : std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
+    int zuni = g.zh ? 0 : 1;
+    struct Pending {
+        Config cfg;
+        std::string key;
+        std::future<std::pair<kl_status, Compiled>> fut;
+    };
+    std::vector<Pending> pipe;
+    auto launch_compile = [&](const Config &c) {
+        Pending p;
+        p.cfg = c;
+        p.key = compile_defines(op, c, g.zbc, zuni);
+        queued.insert(config_string(c));
+        ++produced;
+        std::string key = p.key;
+        bool cached = ctx->kernels.count(key) > 0;
+        p.fut = std::async(std::launch::async, [key, cached]() {
+            Compiled out;
+            kl_status s = cached ? KL_OK : nvrtc_compile(key, false, &out);
+            return std::make_pair(s, std::move(out));
+        });
+        pipe.push_back(std::move(p));
+    };
+    int evaluated = (int)done.size();
+    auto budget_left = [&]() { return elapsed() < O.budget_s && evaluated < O.max_evals; };
+    while (budget_left() || !pipe.empty()) {
+        while (budget_left() && (int)pipe.size() < nthreads) {
+            Config c;
+            if (!next_candidate(&c)) break;
+            launch_compile(c);
+            if (O.strategy == "local" && produced > random_phase) break;  // keep the search adaptive
+        }
+        if (pipe.empty()) break;
+        Pending p = std::move(pipe.front());
+        pipe.erase(pipe.begin());
+        auto res = p.fut.get();
+        Eval e;
+        e.config = config_string(p.cfg);
+        if (!budget_left() && evaluated >= O.max_evals) {
+            continue;   // drained after the budget: not evaluated
+        }
+        if (res.first != KL_OK) {
+            e.note = "compile failed";
+        } else {
+            Kernel *k = nullptr;
+            kl_status ls = ctx->kernels.count(p.key)
+                               ? get_kernel(ctx, op, p.cfg, g.zbc, zuni, &k)
+                               : load_compiled(ctx, op, p.cfg, p.key, res.second, &k);
+            if (ls != KL_OK) {
+                e.note = std::string("load failed: ") + kl_last_error();
+                cudaGetLastError();
+            } else if (reset_outputs(op, R) != KL_OK) {
+                return KL_ERR_CUDA;
+            } else {
+                kl_status ts = time_config(ctx, op, p.cfg, g, R, 0, 1, &e.time_us);
+                if (ts == KL_OK && op.accumulate) ts = reset_outputs(op, R);
+                if (ts == KL_OK) ts = time_config(ctx, op, p.cfg, g, R, 0, 1, &e.time_us);
+                if (ts == KL_OK && !op.accumulate) ts = verify(ctx, op, g, R, &e.err);
+                if (ts == KL_OK && op.accumulate) {
+                    // accumulate: verify one fresh application against the reference
+                    reset_outputs(op, R);
+                    kl_fields f{R.in[0], R.in[1], R.in[2], nin > 3 ? R.in[3] : nullptr, R.out[0], R.out[1], R.out[2]};
+                    ts = launch_config(ctx, op, p.cfg, g, f, 0);
+                    if (ts == KL_OK) ts = verify(ctx, op, g, R, &e.err);
+                }
+                if (ts == KL_OK && !op.accumulate)
+                    ts = time_config(ctx, op, p.cfg, g, R, O.warm, O.reps, &e.time_us);
+                if (ts != KL_OK) {
+                    e.note = std::string("run failed: ") + kl_last_error();
+                    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+                        return fail(KL_ERR_CUDA, "tune: device error, stopping: " + e.note);
+                } else {
+                    e.ok = e.err <= tol;
+                    if (!e.ok) e.note = "verification failed";
+                }
+            }
+        }
+        ++evaluated;
+        evals.push_back(e);
+        log_eval(O.log, e, elapsed());
+    }
+
+    // re-time the top candidates and the default
+    std::vector<Eval> ok;
+    for (auto &e : evals)
+        if (e.ok) ok.push_back(e);
+    std::sort(ok.begin(), ok.end(), [](const Eval &a, const Eval &b) { return a.time_us < b.time_us; });
+    if (ok.size() > (size_t)O.topk) ok.resize(O.topk);
+    double def_us = INFINITY;
+    if (!op.accumulate) {
+        st = time_config(ctx, op, def, g, R, O.warm, 3 * O.reps, &def_us);
+        if (st) return st;
+    }
+    Eval best;
+    best.config = config_string(def);
+    best.time_us = def_us;
+    best.ok = true;
+    for (auto &e : ok) {
+        Config c;
+        std::string err;
+        if (!config_parse(e.config, &c, &err)) continue;
+        double t = e.time_us;
+        if (!op.accumulate) {
+            st = time_config(ctx, op, c, g, R, O.warm, 3 * O.reps, &t);
+            if (st) return st;
+        }
+        if (t < best.time_us) {
+            best = e;
+            best.time_us = t;
+        }
+    }
+
+    WisdomRecord rec;
+    rec.device = ctx->name;
+    rec.cc_major = ctx->cc_major;
+    rec.cc_minor = ctx->cc_minor;
+    rec.zbc = g.zbc;
+    rec.nx = g.nx;
+    rec.ny = g.ny;
+    rec.nz = g.nz;
+    rec.config = best.config;
+    rec.time_us = best.time_us;
+    int dv = 0, rv = 0, nvM = 0, nvm = 0;
+    cudaDriverGetVersion(&dv);
+    cudaRuntimeGetVersion(&rv);
+    nvrtcVersion(&nvM, &nvm);
+    char buf[64];
+    rec.extra["date"] = now_iso();
+    rec.extra["host"] = host_name();
+    rec.extra["driver"] = std::to_string(dv);
+    rec.extra["runtime"] = std::to_string(rv);
+    snprintf(buf, sizeof buf, "%d.%d", nvM, nvm);
+    rec.extra["nvrtc"] = buf;
+    rec.extra["sms"] = std::to_string(ctx->nsm);
+    rec.extra["strategy"] = O.strategy;
+    rec.extra["family"] = O.family;
+    rec.extra["evals"] = std::to_string(evaluated);
+    snprintf(buf, sizeof buf, "%.1f", elapsed());
+    rec.extra["tune_s"] = buf;
+    snprintf(buf, sizeof buf, "%.3f", def_us);
+    rec.extra["default_us"] = buf;
+    snprintf(buf, sizeof buf, "%.3f", std::isfinite(def_us) && best.time_us > 0 ? def_us / best.time_us : 1.0);
+    rec.extra["speedup"] = buf;
+    rec.extra["dtype"] = dtype_tag(op.dtype);
+    rec.extra["zuni"] = std::to_string(zuni);
+    std::string err;
+    if (!wisdom_append(wisdom_path, rec, &err)) return fail(KL_ERR_IO, err);
+    return KL_OK;
+}
 
 kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_grid *grids,
                             const kl_fields *fields, void *stream)
 {
     (void)ctx; (void)op; (void)n; (void)grids; (void)fields; (void)stream;
     return fail(KL_ERR_UNSUPPORTED, "kl_launch_batched: not built yet");
-}
-
-kl_status kl_capture(kl_ctx *ctx, const kl_op *op, const kl_grid *grid, const kl_fields *fields,
-                     const char *path, void *stream)
-{
-    (void)ctx; (void)op; (void)grid; (void)fields; (void)path; (void)stream;
-    return fail(KL_ERR_UNSUPPORTED, "kl_capture: not built yet");
-}
-
-kl_status kl_capture_if_requested(kl_ctx *ctx, const kl_op *op, const kl_grid *grid,
-                                  const kl_fields *fields, void *stream)
-{
-    (void)ctx; (void)op; (void)grid; (void)fields; (void)stream;
-    return KL_OK;
-}
-
-kl_status kl_tune(kl_ctx *ctx, const char *capture_path, const char *opts, const char *wisdom_path)
-{
-    (void)ctx; (void)capture_path; (void)opts; (void)wisdom_path;
-    return fail(KL_ERR_UNSUPPORTED, "kl_tune: not built yet");
 }
 
 }  // extern "C"
