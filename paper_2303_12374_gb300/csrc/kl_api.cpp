@@ -140,7 +140,7 @@ kl_status load_compiled(kl_ctx *ctx, const kl_op &op, const Config &cfg, const s
     }
     ctx->drv.FuncGetAttribute(&k.nregs, CU_FUNC_ATTRIBUTE_NUM_REGS, k.fn);
     ctx->drv.FuncGetAttribute(&k.local_bytes, CU_FUNC_ATTRIBUTE_LOCAL_SIZE_BYTES, k.fn);
-    if (cfg.family == 1) {
+    if (cfg.family >= 1) {
         k.smem = zmarch_smem_bytes(op, cfg);
         r = ctx->drv.FuncSetAttribute(k.fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES,
                                       (int)k.smem);
@@ -383,6 +383,7 @@ kl_status launch_config(kl_ctx *ctx, const kl_op &op, const Config &cfg, const k
     fill_coefs(a, g);
 
     if (!config_fits(op, cfg, g, &f, &err)) return fail(KL_ERR_INVALID_ARG, "configuration: " + err);
+    if (!space_size(cfg.family)) return fail(KL_ERR_INVALID_ARG, "unknown family");
     CUresult r;
     if (cfg.family == 0) {
         a.nbx = (g.nx + cfg.bx * cfg.tx - 1) / (cfg.bx * cfg.tx);
@@ -671,7 +672,7 @@ kl_status kl_space_size(const kl_op *op, int32_t family, int64_t *count)
 {
     kl_status st = check_op(op);
     if (st) return st;
-    if (!count || (family != 0 && family != 1)) return fail(KL_ERR_INVALID_ARG, "bad family");
+    if (!count || family < 0 || family > 2) return fail(KL_ERR_INVALID_ARG, "bad family");
     *count = space_size(family);
     return KL_OK;
 }

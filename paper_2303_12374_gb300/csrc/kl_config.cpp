@@ -26,9 +26,12 @@ std::string config_string(const Config &c)
                  "cx=%d,cy=%d,cz=%d,perm=%s,minb=%d",
                  c.bx, c.by, c.bz, c.tx, c.ty, c.tz, c.ux, c.uy, c.uz, c.cx, c.cy, c.cz,
                  kPermNames[c.perm], c.minb);
-    } else {
+    } else if (c.family == 1) {
         snprintf(b, sizeof b, "zmarch:bx=%d,by=%d,px=%d,py=%d,kc=%d,ns=%d,minb=%d", c.mbx, c.mby,
                  c.mpx, c.mpy, c.kc, c.ns, c.mminb);
+    } else {
+        snprintf(b, sizeof b, "zpack:w=%d,ly=%d,kc=%d,ns=%d,minb=%d", c.mby, c.mpy, c.kc, c.ns,
+                 c.mminb);
     }
     return b;
 }
@@ -56,7 +59,13 @@ bool config_parse(const std::string &text, Config *c, std::string *err)
     body = colon == std::string::npos ? "" : s.substr(colon + 1);
     if (fam == "direct") c->family = 0;
     else if (fam == "zmarch") c->family = 1;
-    else {
+    else if (fam == "zpack") {
+        c->family = 2;
+        c->mbx = 32;
+        c->mpx = 2;
+        c->mby = 8;
+        c->mpy = 2;
+    } else {
         *err = "unknown configuration family '" + fam + "'";
         return false;
     }
@@ -93,6 +102,10 @@ bool config_parse(const std::string &text, Config *c, std::string *err)
             else if (k == "ux") dst = &c->ux; else if (k == "uy") dst = &c->uy; else if (k == "uz") dst = &c->uz;
             else if (k == "cx") dst = &c->cx; else if (k == "cy") dst = &c->cy; else if (k == "cz") dst = &c->cz;
             else if (k == "minb") dst = &c->minb;
+        } else if (c->family == 2) {
+            if (k == "w") dst = &c->mby; else if (k == "ly") dst = &c->mpy;
+            else if (k == "kc") dst = &c->kc; else if (k == "ns") dst = &c->ns;
+            else if (k == "minb") dst = &c->mminb;
         } else {
             if (k == "bx") dst = &c->mbx; else if (k == "by") dst = &c->mby;
             else if (k == "px") dst = &c->mpx; else if (k == "py") dst = &c->mpy;
@@ -174,11 +187,25 @@ bool config_check(const kl_op &op, const Config &c, std::string *err)
         }
         return true;
     }
-    if (c.family == 1) {
-        if (!in(c.mbx, {32, 64, 128}) || !in(c.mby, {1, 2, 4, 8, 16}) || !in(c.mpx, {1, 2, 4}) ||
-            !in(c.mpy, {1, 2, 4}) || !in(c.kc, {4, 8, 16, 32, 64, 128, 256}) ||
-            !in(c.ns, {8, 9, 10, 12}) || c.mminb < 1 || c.mminb > 4) {
+    if (c.family == 1 || c.family == 2) {
+        if (c.family == 1 &&
+            (!in(c.mbx, {32, 64, 128}) || !in(c.mby, {1, 2, 4, 8, 16}) || !in(c.mpx, {1, 2, 4}) ||
+             !in(c.mpy, {1, 2, 4}))) {
             *err = "zmarch parameter outside the space";
+            return false;
+        }
+        if (c.family == 2 && (c.mbx != 32 || c.mpx != 2 || !in(c.mby, {1, 2, 4, 8, 16}) ||
+                              !in(c.mpy, {1, 2, 4, 8}))) {
+            *err = "zpack parameter outside the space (w 1..16, ly 1..8)";
+            return false;
+        }
+        if (c.family == 2 && op.diff == 2) {
+            *err = "zpack supports diff = 0 or 1";
+            return false;
+        }
+        if (!in(c.kc, {4, 8, 16, 32, 64, 128, 256}) || !in(c.ns, {8, 9, 10, 12}) ||
+            c.mminb < 1 || c.mminb > 4) {
+            *err = "z-march parameter outside the space";
             return false;
         }
         if (c.mbx * c.mby > 1024) {
@@ -212,10 +239,13 @@ static const int kBX[] = {16, 32, 64, 128, 256}, kBYZ[] = {1, 2, 4, 8, 16}, kT[]
 static const int kMBX[] = {32, 64, 128}, kMBY[] = {1, 2, 4, 8, 16}, kMP[] = {1, 2, 4},
                  kKC[] = {4, 8, 16, 32, 64, 128, 256}, kNS[] = {8, 9, 10, 12};
 
+static const int kW[] = {1, 2, 4, 8, 16}, kLY[] = {1, 2, 4, 8};
+
 int64_t space_size(int family)
 {
     if (family == 0) return 5LL * 5 * 5 * 27 * 8 * 8 * 6 * 6;
     if (family == 1) return 3LL * 5 * 3 * 3 * 7 * 4 * 4;
+    if (family == 2) return 5LL * 4 * 7 * 4 * 4;
     return 0;
 }
 
@@ -240,6 +270,14 @@ bool space_config(int family, int64_t idx, Config *c)
         c->cx = take(2); c->cy = take(2); c->cz = take(2);
         c->perm = take(6);
         c->minb = 1 + take(6);
+    } else if (family == 2) {
+        c->mbx = 32;
+        c->mpx = 2;
+        c->mby = kW[take(5)];
+        c->mpy = kLY[take(4)];
+        c->kc = kKC[take(7)];
+        c->ns = kNS[take(4)];
+        c->mminb = 1 + take(4);
     } else {
         c->mbx = kMBX[take(3)];
         c->mby = kMBY[take(5)];

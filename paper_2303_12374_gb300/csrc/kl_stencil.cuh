@@ -430,9 +430,9 @@ kl_tendency(const kl_args a)
 }
 #endif  // KL_FAMILY == 0
 
-#if KL_FAMILY == 1
-// ======================================================= zmarch family
-//
+#if KL_FAMILY >= 1
+// ================================= TMA plane ring shared by families 1 and 2
+
 // A CTA of KL_MBX x KL_MBY threads owns an x-y tile of TXS x TYS interior
 // points (each thread KL_MPX consecutive x points times KL_MPY consecutive
 // rows) and marches up KL_KC levels.  Whole planes of the tile plus its
@@ -512,6 +512,14 @@ __device__ __forceinline__ void kl_tma_load3(unsigned dst, const kl_tmap *map, i
                  ::"r"(dst), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(bar)
                  : "memory");
 }
+
+#endif  // KL_FAMILY >= 1
+
+#if KL_FAMILY == 1
+// ======================================================= zmarch family
+//
+// (described above: one thread per KL_MPX x KL_MPY points, every stencil
+// value read from the plane ring)
 
 struct kl_acc_smem {
     const char *base[2 * KL_R + 1];     // slot base of plane k+dk, dk = -R..R
@@ -644,3 +652,359 @@ kl_tendency(const kl_args a, const __grid_constant__ kl_tmap tm_u,
     }
 }
 #endif  // KL_FAMILY == 1
+
+#if KL_FAMILY == 2
+// ======================================================== zpack family
+//
+// Same plane ring as zmarch (tile 64 x KL_TYS, KL_MBY warps, each warp KL_MPY
+// consecutive rows); every face flux is formed once and diffusion is folded
+// into it:
+//  * lane l of a warp owns the column pair (x0 + l, x0 + l + 32); the pair is
+//    one packed value (f32x2 for f32 compute, two doubles for f64), so every
+//    arithmetic step serves two points;
+//  * x: a lane forms the flux on one face of each of its columns and gets the
+//    other face from its neighbour lane by a shuffle; the one face per row
+//    that lies past the warp's 64 columns is formed for all rows of the warp
+//    in a single side pass (lane e: field e / MPY, row e % MPY);
+//  * y: the MPY + 1 faces of a thread's consecutive rows are formed once;
+//  * z: the top face of level k is carried as the bottom face of level k+1;
+//  * constant-nu diffusion: the diffusive flux nu (a_{m+1} - a_m) / d of a face
+//    is added to the advective flux of the same face, using the difference
+//    d1 = a_m - a_{m+1} the upwind formula already forms.
+// Supports diff = 0 or 1.
+
+#if KL_DIFF == 2
+#error "zpack supports diff = 0 or 1"
+#endif
+
+#if KL_DTYPE == 0
+struct V { double lo, hi; };
+__device__ __forceinline__ V vmk(double a, double b) { V r; r.lo = a; r.hi = b; return r; }
+__device__ __forceinline__ double vlo(V a) { return a.lo; }
+__device__ __forceinline__ double vhi(V a) { return a.hi; }
+__device__ __forceinline__ V vadd(V a, V b) { return vmk(a.lo + b.lo, a.hi + b.hi); }
+__device__ __forceinline__ V vsub(V a, V b) { return vmk(a.lo - b.lo, a.hi - b.hi); }
+__device__ __forceinline__ V vmul(V a, V b) { return vmk(a.lo * b.lo, a.hi * b.hi); }
+__device__ __forceinline__ V vfma(V a, V b, V c) { return vmk(fma(a.lo, b.lo, c.lo), fma(a.hi, b.hi, c.hi)); }
+__device__ __forceinline__ V vabs(V a) { return vmk(fabs(a.lo), fabs(a.hi)); }
+__device__ __forceinline__ V vshfl(V a, int src)
+{
+    return vmk(__shfl_sync(0xffffffffu, a.lo, src), __shfl_sync(0xffffffffu, a.hi, src));
+}
+#else
+struct V { unsigned long long b; };
+__device__ __forceinline__ V vmk(float a, float c)
+{
+    V r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.b) : "f"(a), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float vlo(V a)
+{
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.b));
+    return lo;
+}
+__device__ __forceinline__ float vhi(V a)
+{
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.b));
+    return hi;
+}
+__device__ __forceinline__ V vadd(V a, V b) { V r; asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.b) : "l"(a.b), "l"(b.b)); return r; }
+__device__ __forceinline__ V vsub(V a, V b) { V r; asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.b) : "l"(a.b), "l"(b.b)); return r; }
+__device__ __forceinline__ V vmul(V a, V b) { V r; asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.b) : "l"(a.b), "l"(b.b)); return r; }
+__device__ __forceinline__ V vfma(V a, V b, V c)
+{
+    V r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.b) : "l"(a.b), "l"(b.b), "l"(c.b));
+    return r;
+}
+__device__ __forceinline__ V vabs(V a) { V r; r.b = a.b & 0x7fffffff7fffffffull; return r; }
+__device__ __forceinline__ V vshfl(V a, int src)
+{
+    V r;
+    r.b = __shfl_sync(0xffffffffu, a.b, src);
+    return r;
+}
+#endif
+__device__ __forceinline__ V vsplat(C a) { return vmk(a, a); }
+
+// packed face flux with the diffusive part folded in:
+//   G = F + kd * d1,  F as flux5 / flux2 (scaled by 1/KL_FS), d1 = a2 - a3
+struct kl_vk { V c37, cm8, c10, cm5; };
+
+__device__ __forceinline__ V kl_vflux(const kl_vk &K, V Us, V a0, V a1, V a2, V a3, V a4, V a5, V kd)
+{
+    V d1 = vsub(a2, a3);
+#if KL_ADV == 5
+    V s1 = vadd(a2, a3), s2 = vadd(a1, a4), s3 = vadd(a0, a5);
+    V d2 = vsub(a1, a4), d3 = vsub(a0, a5);
+    V i6 = vfma(K.c37, s1, vfma(K.cm8, s2, s3));
+    V d6 = vfma(K.c10, d1, vfma(K.cm5, d2, d3));
+    V f = vfma(Us, i6, vmul(vabs(Us), d6));
+#elif KL_ADV == 2
+    V f = vmul(Us, vadd(a2, a3));
+#else
+    V f = vsplat(C(0));
+#endif
+#if KL_DIFF == 1
+    f = vfma(kd, d1, f);
+#endif
+    return f;
+}
+
+// scalar twin of kl_vflux for the side pass
+__device__ __forceinline__ C kl_sflux(C Us, C a0, C a1, C a2, C a3, C a4, C a5, C kd)
+{
+    C d1 = a2 - a3;
+#if KL_ADV == 5
+    C f = flux5(Us, a0, a1, a2, a3, a4, a5);
+#elif KL_ADV == 2
+    C f = flux2(Us, a2, a3);
+#else
+    C f = C(0);
+#endif
+#if KL_DIFF == 1
+    f = fma(kd, d1, f);
+#endif
+    return f;
+}
+
+// the 4 outer values of a 6-point window exist only for the 5th-order scheme;
+// other schemes never address them (their planes / rows lie outside the ring)
+#if KL_ADV == 5
+#define KL_A5(x) (x)
+#else
+#define KL_A5(x) vsplat(C(0))
+#endif
+
+#define KL_OFF(x, row) ((((row) + KL_H) * KL_PITCH + (x)) * (int)sizeof(T))
+
+template <int F, int DK, int DX>
+__device__ __forceinline__ V kl_pair(const char *const *pl, int lx, int row)
+{
+    static_assert(DK >= -KL_R && DK <= KL_R, "plane outside the staged window");
+    static_assert(DX >= -KL_H && DX <= KL_H, "x offset outside the halo");
+    static_assert(F >= 0 && F < 3, "field index");
+    const char *b = pl[DK + KL_R] + F * KL_PLANE_BYTES;
+    return vmk(lds((const T *)(b + KL_OFF(lx + DX, row))), lds((const T *)(b + KL_OFF(lx + 32 + DX, row))));
+}
+
+extern "C" __global__ void __launch_bounds__(32 * KL_MBY, KL_MMINB)
+kl_tendency(const kl_args a, const __grid_constant__ kl_tmap tm_u,
+            const __grid_constant__ kl_tmap tm_v, const __grid_constant__ kl_tmap tm_w,
+            const __grid_constant__ kl_tmap tm_n)
+{
+    static_assert(KL_MBX == 32 && KL_MPX == 2, "zpack tiles are 64 columns wide");
+    static_assert(3 * KL_MPY <= 32, "side pass needs 3 x rows <= 32 lanes");
+    extern __shared__ unsigned char kl_smem_raw[];
+    unsigned char *ring = (unsigned char *)(((unsigned long long)kl_smem_raw + 127) & ~127ull);
+    unsigned long long *bars = (unsigned long long *)(ring + KL_NS * KL_SLOT_BYTES);
+    const int lane = threadIdx.x, warp = threadIdx.y;
+    const int tid = lane + 32 * warp;
+    const int nx = (int)a.nx, ny = (int)a.ny, nz = (int)a.nz;
+    const int kb = blockIdx.z * (int)a.kchunk;
+    const int ke = min(kb + (int)a.kchunk, nz);
+    const int tx0 = blockIdx.x * 64, ty0 = blockIdx.y * KL_TYS;
+    const int gx = (int)a.tile_x0 + tx0 - KL_LPAD, gy = (int)a.tile_y0 + ty0 - KL_H;
+    const int gz0 = (int)a.tile_z0;
+    const kl_tmap *maps[3] = {&tm_u, &tm_v, &tm_w};
+    (void)tm_n;
+
+    if (tid == 0) {
+        for (int s = 0; s < KL_NS; ++s) kl_mbar_init(kl_smem_addr(&bars[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int p) {
+        int slot = (p - (kb - KL_R)) % KL_NS;
+        unsigned bar = kl_smem_addr(&bars[slot]);
+        kl_mbar_expect(bar, 3 * KL_BOX_BYTES);
+        unsigned dst = kl_smem_addr(ring + slot * KL_SLOT_BYTES);
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+            kl_tma_load3(dst + f * KL_PLANE_BYTES, maps[f], gx, gy, gz0 + p, bar);
+    };
+    const int p_first = kb - KL_R;
+    const int p_last = ke - 1 + KL_R;
+    int p_next = p_first;
+    if (tid == 0)
+        for (; p_next < p_first + KL_NS && p_next <= p_last; ++p_next) issue(p_next);
+
+    // coefficients (f32 kernels read the f32 copies; no f64 arithmetic)
+    const C dxi = KL_CO(a, 0), dyi = KL_CO(a, 1), nu = KL_CO(a, 4);
+    const C cx = KL_FS * dxi, cy = KL_FS * dyi;
+    const C kdx = nu * dxi / KL_FS, kdy = nu * dyi / KL_FS;
+    kl_vk K;
+    K.c37 = vsplat(C(37)); K.cm8 = vsplat(C(-8)); K.c10 = vsplat(C(10)); K.cm5 = vsplat(C(-5));
+    const V vkdx = vsplat(kdx), vkdy = vsplat(kdy), vcx = vsplat(cx), vcy = vsplat(cy);
+
+    const int r0 = warp * KL_MPY;                       // first row of this thread (tile local)
+    const int lx = KL_LPAD + lane;                      // local x of the low column
+
+    V zb[KL_MPY][3];
+    bool timed_out = false;
+    int p_waited = p_first - 1;
+
+    for (int k = kb; k < ke; ++k) {
+        {
+            int p = k + KL_R;
+            if (k == kb) {
+                for (int q = p_first; q < p; ++q) {
+                    unsigned b2 = kl_smem_addr(&bars[(q - p_first) % KL_NS]);
+                    bool ok2 = kl_mbar_wait(b2, ((q - p_first) / KL_NS) & 1);
+                    if (__syncthreads_or(!ok2)) { timed_out = true; break; }
+                    p_waited = q;
+                }
+                if (timed_out) break;
+            }
+            unsigned bar = kl_smem_addr(&bars[(p - p_first) % KL_NS]);
+            bool ok = kl_mbar_wait(bar, ((p - p_first) / KL_NS) & 1);
+            if (__syncthreads_or(!ok)) { timed_out = true; break; }
+            p_waited = p;
+        }
+        const char *pl[2 * KL_R + 1];
+#pragma unroll
+        for (int d = -KL_R; d <= KL_R; ++d)
+            pl[d + KL_R] = (const char *)(ring + ((k + d - p_first) % KL_NS) * KL_SLOT_BYTES);
+        // packed pair of field f (0 u, 1 v, 2 w) on plane k+dk, columns lx+dx
+        // and lx+32+dx, tile row `row` (offsets checked at compile time)
+#define KL_P(f, dk, dx, row) kl_pair<f, dk, dx>(pl, lx, row)
+
+        const kl_zmetric Z = kl_make_z(a, k);
+        const C czu = KL_FS * Z.dzi, czw = KL_FS * Z.dzhi;
+        const C kzu_top = nu * Z.dzhi_up / KL_FS;         // u, v top face zh_{k+1}
+        const C kzw_top = nu * Z.dzi / KL_FS;             // w top face z_k
+        const V vkzu_top = vsplat(kzu_top), vkzw_top = vsplat(kzw_top);
+
+        // ---- side pass: the x face past the warp's columns, for every row
+        C extra;
+        {
+            int e = lane < 3 * KL_MPY ? lane : 0;
+            int f = e / KL_MPY, row = r0 + e % KL_MPY;
+            // u: face at centre x0-1 (window x0-3 .. x0+2); v, w: face at edge x0+64
+            // (window x0+61 .. x0+66)
+            int xs = f == 0 ? KL_LPAD - 3 : KL_LPAD + 61;
+            const char *base = pl[KL_R] + f * KL_PLANE_BYTES;
+            C a2 = lds((const T *)(base + KL_OFF(xs + 2, row)));
+            C a3 = lds((const T *)(base + KL_OFF(xs + 3, row)));
+#if KL_ADV == 5
+            C a0 = lds((const T *)(base + KL_OFF(xs, row)));
+            C a1 = lds((const T *)(base + KL_OFF(xs + 1, row)));
+            C a4 = lds((const T *)(base + KL_OFF(xs + 4, row)));
+            C a5 = lds((const T *)(base + KL_OFF(xs + 5, row)));
+#else
+            C a0 = C(0), a1 = C(0), a4 = C(0), a5 = C(0);
+#endif
+            C us;
+            if (f == 0) {
+                us = a2 + a3;                                   // u(x0-1) + u(x0)
+            } else {
+                // u at x0+64 on rows j-1, j (v) or planes k-1, k (w)
+                const char *ub = pl[KL_R];
+                const char *ub2 = f == 1 ? pl[KL_R] : pl[KL_R - 1];
+                int row2 = f == 1 ? row - 1 : row;
+                us = lds((const T *)(ub2 + KL_OFF(KL_LPAD + 64, row2))) +
+                     lds((const T *)(ub + KL_OFF(KL_LPAD + 64, row)));
+            }
+            extra = kl_sflux(us, a0, a1, a2, a3, a4, a5, kdx);
+        }
+
+        // ---- y faces of this thread's rows (shared by consecutive rows)
+        V fuy[KL_MPY + 1], fvy[KL_MPY + 1], fwy[KL_MPY + 1];
+#pragma unroll
+        for (int m = 0; m <= KL_MPY; ++m) {
+            const int yr = r0 + m;                         // edge yh_{yr} (u, w); centre y_{yr-1} (v)
+            fuy[m] = kl_vflux(K, vadd(KL_P(1, 0, -1, yr), KL_P(1, 0, 0, yr)), KL_A5(KL_P(0, 0, 0, yr - 3)), KL_A5(KL_P(0, 0, 0, yr - 2)), KL_P(0, 0, 0, yr - 1),
+                              KL_P(0, 0, 0, yr), KL_A5(KL_P(0, 0, 0, yr + 1)), KL_A5(KL_P(0, 0, 0, yr + 2)), vkdy);
+            fvy[m] = kl_vflux(K, vadd(KL_P(1, 0, 0, yr - 1), KL_P(1, 0, 0, yr)), KL_A5(KL_P(1, 0, 0, yr - 3)), KL_A5(KL_P(1, 0, 0, yr - 2)), KL_P(1, 0, 0, yr - 1),
+                              KL_P(1, 0, 0, yr), KL_A5(KL_P(1, 0, 0, yr + 1)), KL_A5(KL_P(1, 0, 0, yr + 2)), vkdy);
+            fwy[m] = kl_vflux(K, vadd(KL_P(1, -1, 0, yr), KL_P(1, 0, 0, yr)), KL_A5(KL_P(2, 0, 0, yr - 3)), KL_A5(KL_P(2, 0, 0, yr - 2)), KL_P(2, 0, 0, yr - 1),
+                              KL_P(2, 0, 0, yr), KL_A5(KL_P(2, 0, 0, yr + 1)), KL_A5(KL_P(2, 0, 0, yr + 2)), vkdy);
+        }
+
+#pragma unroll
+        for (int r = 0; r < KL_MPY; ++r) {
+            const int yr = r0 + r;
+            // ---- x faces: u right face (centre), v and w left faces (edge)
+            V fux = kl_vflux(K, vadd(KL_P(0, 0, 0, yr), KL_P(0, 0, 1, yr)), KL_A5(KL_P(0, 0, -2, yr)), KL_A5(KL_P(0, 0, -1, yr)), KL_P(0, 0, 0, yr),
+                             KL_P(0, 0, 1, yr), KL_A5(KL_P(0, 0, 2, yr)), KL_A5(KL_P(0, 0, 3, yr)), vkdx);
+            V fvx = kl_vflux(K, vadd(KL_P(0, 0, 0, yr - 1), KL_P(0, 0, 0, yr)), KL_A5(KL_P(1, 0, -3, yr)), KL_A5(KL_P(1, 0, -2, yr)), KL_P(1, 0, -1, yr),
+                             KL_P(1, 0, 0, yr), KL_A5(KL_P(1, 0, 1, yr)), KL_A5(KL_P(1, 0, 2, yr)), vkdx);
+            V fwx = kl_vflux(K, vadd(KL_P(0, -1, 0, yr), KL_P(0, 0, 0, yr)), KL_A5(KL_P(2, 0, -3, yr)), KL_A5(KL_P(2, 0, -2, yr)), KL_P(2, 0, -1, yr),
+                             KL_P(2, 0, 0, yr), KL_A5(KL_P(2, 0, 1, yr)), KL_A5(KL_P(2, 0, 2, yr)), vkdx);
+            // neighbour faces
+            V ul = vshfl(fux, (lane + 31) & 31);            // (lane-1).(lo, hi)
+            V vr = vshfl(fvx, (lane + 1) & 31);              // (lane+1).(lo, hi)
+            V wr = vshfl(fwx, (lane + 1) & 31);
+            C eu = __shfl_sync(0xffffffffu, extra, r);
+            C ev = __shfl_sync(0xffffffffu, extra, KL_MPY + r);
+            C ew = __shfl_sync(0xffffffffu, extra, 2 * KL_MPY + r);
+            if (lane == 0) ul = vmk(eu, vlo(ul));           // (face x0-1, face x0+31)
+            if (lane == 31) {                                // (face x0+32, face x0+64)
+                vr = vmk(vhi(vr), ev);
+                wr = vmk(vhi(wr), ew);
+            }
+            // ---- z faces: bottom carried, top formed here
+            V fz_u, fz_v, fz_w;
+            fz_u = kl_vflux(K, vadd(KL_P(2, 1, -1, yr), KL_P(2, 1, 0, yr)), KL_A5(KL_P(0, -2, 0, yr)), KL_A5(KL_P(0, -1, 0, yr)), KL_P(0, 0, 0, yr),
+                            KL_P(0, 1, 0, yr), KL_A5(KL_P(0, 2, 0, yr)), KL_A5(KL_P(0, 3, 0, yr)), vkzu_top);
+            fz_v = kl_vflux(K, vadd(KL_P(2, 1, 0, yr - 1), KL_P(2, 1, 0, yr)), KL_A5(KL_P(1, -2, 0, yr)), KL_A5(KL_P(1, -1, 0, yr)), KL_P(1, 0, 0, yr),
+                            KL_P(1, 1, 0, yr), KL_A5(KL_P(1, 2, 0, yr)), KL_A5(KL_P(1, 3, 0, yr)), vkzu_top);
+            fz_w = kl_vflux(K, vadd(KL_P(2, 0, 0, yr), KL_P(2, 1, 0, yr)), KL_A5(KL_P(2, -2, 0, yr)), KL_A5(KL_P(2, -1, 0, yr)), KL_P(2, 0, 0, yr),
+                            KL_P(2, 1, 0, yr), KL_A5(KL_P(2, 2, 0, yr)), KL_A5(KL_P(2, 3, 0, yr)), vkzw_top);
+            if (k == kb) {
+                // bottom faces of the first level: u, v at zh_k, w at z_{k-1}
+                const V kzu_b = vsplat(nu * Z.dzhi / KL_FS), kzw_b = vsplat(nu * Z.dzi_dn / KL_FS);
+                zb[r][0] = kl_vflux(K, vadd(KL_P(2, 0, -1, yr), KL_P(2, 0, 0, yr)), KL_A5(KL_P(0, -3, 0, yr)), KL_A5(KL_P(0, -2, 0, yr)), KL_P(0, -1, 0, yr),
+                                    KL_P(0, 0, 0, yr), KL_A5(KL_P(0, 1, 0, yr)), KL_A5(KL_P(0, 2, 0, yr)), kzu_b);
+                zb[r][1] = kl_vflux(K, vadd(KL_P(2, 0, 0, yr - 1), KL_P(2, 0, 0, yr)), KL_A5(KL_P(1, -3, 0, yr)), KL_A5(KL_P(1, -2, 0, yr)), KL_P(1, -1, 0, yr),
+                                    KL_P(1, 0, 0, yr), KL_A5(KL_P(1, 1, 0, yr)), KL_A5(KL_P(1, 2, 0, yr)), kzu_b);
+                zb[r][2] = kl_vflux(K, vadd(KL_P(2, -1, 0, yr), KL_P(2, 0, 0, yr)), KL_A5(KL_P(2, -3, 0, yr)), KL_A5(KL_P(2, -2, 0, yr)), KL_P(2, -1, 0, yr),
+                                    KL_P(2, 0, 0, yr), KL_A5(KL_P(2, 1, 0, yr)), KL_A5(KL_P(2, 2, 0, yr)), kzw_b);
+            }
+            // ---- tendencies
+            V tu = vfma(vsub(ul, fux), vcx, vfma(vsub(fuy[r], fuy[r + 1]), vcy,
+                                                 vmul(vsub(zb[r][0], fz_u), vsplat(czu))));
+            V tv = vfma(vsub(fvx, vr), vcx, vfma(vsub(fvy[r], fvy[r + 1]), vcy,
+                                                 vmul(vsub(zb[r][1], fz_v), vsplat(czu))));
+            V tw = vfma(vsub(fwx, wr), vcx, vfma(vsub(fwy[r], fwy[r + 1]), vcy,
+                                                 vmul(vsub(zb[r][2], fz_w), vsplat(czw))));
+            zb[r][0] = fz_u;
+            zb[r][1] = fz_v;
+            zb[r][2] = fz_w;
+            const int j = ty0 + yr;
+            if (j < ny) {
+                const bool wall = KL_ZBC == 1 && k == 0;
+                const long long o = (long long)(tx0 + lane) + (long long)j * a.sj + (long long)k * a.sk;
+                if (tx0 + lane < nx) {
+                    out(a.ut + o, vlo(tu));
+                    out(a.vt + o, vlo(tv));
+                    out(a.wt + o, wall ? C(0) : vlo(tw));
+                }
+                if (tx0 + lane + 32 < nx) {
+                    out(a.ut + o + 32, vhi(tu));
+                    out(a.vt + o + 32, vhi(tv));
+                    out(a.wt + o + 32, wall ? C(0) : vhi(tw));
+                }
+            }
+        }
+#undef KL_P
+        __syncthreads();
+        if (tid == 0 && p_next <= p_last) issue(p_next++);
+    }
+
+    if (timed_out) {
+        if (tid == 0) {
+            atomicOr(a.err, KL_DEV_TIMEOUT);
+            for (int q = p_waited + 1; q < p_next; ++q) {
+                unsigned b2 = kl_smem_addr(&bars[(q - p_first) % KL_NS]);
+                kl_mbar_wait(b2, ((q - p_first) / KL_NS) & 1);
+            }
+        }
+        __syncthreads();
+    }
+}
+#endif  // KL_FAMILY == 2

@@ -289,8 +289,8 @@ static kl_status parse_opts(const char *text, TuneOpts *o)
     }
     if (o->strategy != "random" && o->strategy != "exhaustive" && o->strategy != "local")
         return fail(KL_ERR_INVALID_ARG, "strategy must be random, exhaustive or local");
-    if (o->family != "all" && o->family != "direct" && o->family != "zmarch")
-        return fail(KL_ERR_INVALID_ARG, "family must be all, direct or zmarch");
+    if (o->family != "all" && o->family != "direct" && o->family != "zmarch" && o->family != "zpack")
+        return fail(KL_ERR_INVALID_ARG, "family must be all, direct, zmarch or zpack");
     return KL_OK;
 }
 
@@ -450,6 +450,7 @@ static bool valid_for(const kl_op &op, const kl_grid &g, int family, int64_t idx
 static std::vector<int> radices(int family)
 {
     if (family == 0) return {5, 5, 5, 3, 3, 3, 2, 2, 2, 2, 2, 2, 6, 6};
+    if (family == 2) return {5, 4, 7, 4, 4};
     return {3, 5, 3, 3, 7, 4, 4};
 }
 
@@ -572,8 +573,10 @@ kl_status kl_tune(kl_ctx *ctx, const char *capture_path, const char *opts, const
     // candidates
     std::mt19937_64 rng(O.seed);
     std::vector<int> fams;
-    if (O.family != "zmarch") fams.push_back(0);
-    if (O.family != "direct") fams.push_back(1);
+    if (O.family == "all" || O.family == "direct") fams.push_back(0);
+    if (O.family == "all" || O.family == "zmarch") fams.push_back(1);
+    if ((O.family == "all" || O.family == "zpack") && op.diff != 2) fams.push_back(2);
+    if (fams.empty()) return fail(KL_ERR_INVALID_ARG, "no configuration family applies to this op");
     std::map<std::string, Eval> done;
     read_log(O.log, &done);
     std::set<std::string> queued;
@@ -618,12 +621,16 @@ kl_status kl_tune(kl_ctx *ctx, const char *capture_path, const char *opts, const
             vals = {{16, 32, 64, 128, 256}, {1, 2, 4, 8, 16}, {1, 2, 4, 8, 16}, {1, 2, 4}, {1, 2, 4},
                     {1, 2, 4}, {0, 1}, {0, 1}, {0, 1}, {0, 1}, {0, 1}, {0, 1}, {0, 1, 2, 3, 4, 5},
                     {1, 2, 3, 4, 5, 6}};
+        else if (c.family == 2)
+            vals = {{1, 2, 4, 8, 16}, {1, 2, 4, 8}, {4, 8, 16, 32, 64, 128, 256}, {8, 9, 10, 12},
+                    {1, 2, 3, 4}};
         else
             vals = {{32, 64, 128}, {1, 2, 4, 8, 16}, {1, 2, 4}, {1, 2, 4}, {4, 8, 16, 32, 64, 128, 256},
                     {8, 9, 10, 12}, {1, 2, 3, 4}};
         std::vector<int> cur = c.family == 0
             ? std::vector<int>{c.bx, c.by, c.bz, c.tx, c.ty, c.tz, c.ux, c.uy, c.uz, c.cx, c.cy, c.cz, c.perm, c.minb}
-            : std::vector<int>{c.mbx, c.mby, c.mpx, c.mpy, c.kc, c.ns, c.mminb};
+            : c.family == 2 ? std::vector<int>{c.mby, c.mpy, c.kc, c.ns, c.mminb}
+                            : std::vector<int>{c.mbx, c.mby, c.mpx, c.mpy, c.kc, c.ns, c.mminb};
         int64_t y = 0;
         for (size_t p = r.size(); p-- > 0;) {
             auto it = std::find(vals[p].begin(), vals[p].end(), cur[p]);

@@ -23,6 +23,9 @@ CONFIGS_DIRECT = [
     "zmarch:bx=32,by=8,px=1,py=1,kc=16,ns=9,minb=1",
     "zmarch:bx=64,by=2,px=1,py=2,kc=4,ns=12,minb=1",
     "zmarch:bx=32,by=2,px=4,py=1,kc=32,ns=10,minb=2",
+    "zpack:w=8,ly=2,kc=8,ns=8,minb=1",
+    "zpack:w=4,ly=4,kc=16,ns=9,minb=1",
+    "zpack:w=2,ly=1,kc=4,ns=12,minb=2",
 ]
 
 
@@ -74,7 +77,7 @@ def test_tendency_parity_default(ctx, oracle_mod, dtype, case):
 
 
 @pytest.mark.parametrize("config", CONFIGS_DIRECT)
-@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("dtype", [0, 1, 2])
 def test_tendency_parity_configs(ctx, oracle_mod, config, dtype):
     nx, ny, nz = 70, 45, 23
     from paper_2303_12374_gb300 import kl
