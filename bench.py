@@ -36,6 +36,12 @@ G = 3
 NU = 1e-3
 
 
+def kernel_source_hash() -> str:
+    import hashlib
+    src = os.path.join(ROOT, "paper_2303_12374_gb300", "csrc", "kl_stencil.cuh")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -262,8 +268,10 @@ def main():
     traffic = None
     tp = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tp):
+        # DRAM bytes per launch from an ncu capture, valid only for the kernel
+        # source it was taken with
         tr = json.load(open(tp))
-        key = f"{WORKLOAD}:{args.dtype}:{tuned_cfg}"
+        key = f"{WORKLOAD}:{args.dtype}:{tuned_cfg}:{kernel_source_hash()}"
         traffic = tr.get(key)
 
     extras = {}

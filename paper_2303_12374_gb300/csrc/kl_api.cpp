@@ -514,6 +514,7 @@ kl_status kl_fill_ghosts(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, void *
     kl_status st = check_grid(grid, 1, nullptr);
     if (st) return st;
     if (!u || !v || !w) return fail(KL_ERR_INVALID_ARG, "u, v, w must not be NULL");
+    if (grid->g > 4) return fail(KL_ERR_UNSUPPORTED, "ghost fill supports g <= 4");
     cudaError_t e = fill_ghosts_launch(esize_of(dtype), *grid, u, v, w, nu, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "fill ghosts launch");
     ctx->launches++;

@@ -384,7 +384,8 @@ bool wisdom_read(const std::string &path, std::vector<WisdomRecord> *out, std::s
     return true;
 }
 
-// Sec. 4.5 heuristic.  Exact-key duplicates: the newest (last) record wins.
+// Sec. 4.5 heuristic.  Several records with the same device and size (one per
+// tuning session): the fastest (smallest time_us) wins, ties go to the newest.
 // Distance ties: the first record in file order.  Records of another zbc are
 // never chosen.
 int wisdom_select(const std::vector<WisdomRecord> &recs, const std::string &device, int ccM,
@@ -395,12 +396,13 @@ int wisdom_select(const std::vector<WisdomRecord> &recs, const std::string &devi
         return std::sqrt(a * a + b * b + c * c);
     };
     // rule 1
-    for (size_t q = recs.size(); q-- > 0;) {
-        const WisdomRecord &r = recs[q];
-        if (r.zbc == zbc && r.device == device && r.nx == nx && r.ny == ny && r.nz == nz) {
-            *config = r.config;
-            return 1;
-        }
+    const WisdomRecord *exact = nullptr;
+    for (const WisdomRecord &r : recs)
+        if (r.zbc == zbc && r.device == device && r.nx == nx && r.ny == ny && r.nz == nz)
+            if (!exact || r.time_us <= exact->time_us) exact = &r;
+    if (exact) {
+        *config = exact->config;
+        return 1;
     }
     auto nearest = [&](auto pred) -> const WisdomRecord * {
         const WisdomRecord *best = nullptr;

@@ -2,6 +2,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 
@@ -11,77 +12,96 @@ namespace {
 
 // ------------------------------------------------------------ ghost fill
 //
-// Ghost points are enumerated in three disjoint groups: the 2g full z planes
-// (with x and y ghosts), the 2g y rows of every interior level (with x
-// ghosts), and the 2g x points of every interior row.  Each maps straight to
-// an interior source point, axis by axis, so one launch fills faces, edges
-// and corners with no ordering between them.  The copy moves raw bits; the
-// odd (w) mirror flips the sign bit, which negates exactly in every format.
+// Ghost points form three disjoint groups, one per blockIdx.z: the 2g full z
+// planes (x and y ghosts included), the 2g y rows of every interior level (x
+// ghosts included), and the 2g x points of every interior row.  Each ghost maps
+// straight to an interior source point, axis by axis, so one launch fills
+// faces, edges and corners with no ordering between them.  The copy moves raw
+// bits; the odd (w) mirror flips the sign bit, which negates exactly in every
+// format.  blockIdx.x / blockIdx.y index x and the row inside a group, so no
+// thread divides by a run-time extent.
 
 struct FillArgs {
     char *f[4];              // u, v, w, nu at interior (0,0,0); nu may be NULL
     long long sj, sk;
-    int nx, ny, nz, g, zbc;
-    long long px, py;        // padded row length / rows per plane
-    long long n_zp, n_yr, n_xp, total;
+    int nx, ny, nz, zbc;
+    int px, py;              // padded row length / rows per plane
+    int gxp, gxx;            // blocks per padded row, per row of x ghosts
+    int b0, b1;              // first block of the y-row group, of the x group
 };
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-template <typename B>
-__global__ void __launch_bounds__(256) fill_kernel(FillArgs a)
+template <typename B, int G>
+__device__ __forceinline__ void fill_one(const FillArgs &a, int i, int j, int k)
 {
     const B sign_bit = (B)1 << (sizeof(B) * 8 - 1);
-    const int g = a.g, g2 = 2 * a.g;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < a.total;
-         t += (long long)gridDim.x * blockDim.x) {
-        int i, j, k;
-        if (t < a.n_zp) {
-            long long plane = a.px * a.py;
-            int p = (int)(t / plane);
-            long long r = t % plane;
-            j = (int)(r / a.px) - g;
-            i = (int)(r % a.px) - g;
-            k = p < g ? p - g : a.nz + (p - g);
-        } else if (t < a.n_zp + a.n_yr) {
-            long long t2 = t - a.n_zp;
-            long long row = t2 / a.px;
-            i = (int)(t2 % a.px) - g;
-            k = (int)(row / g2);
-            int q = (int)(row % g2);
-            j = q < g ? q - g : a.ny + (q - g);
-        } else {
-            long long t3 = t - a.n_zp - a.n_yr;
-            int q = (int)(t3 % g2);
-            long long rest = t3 / g2;
-            j = (int)(rest % a.ny);
-            k = (int)(rest / a.ny);
-            i = q < g ? q - g : a.nx + (q - g);
-        }
-        int si = wrapi(i, a.nx), sj = wrapi(j, a.ny);
-        long long dst = i + j * a.sj + k * a.sk;
-        // even fields (u, v, nu)
-        int ske;
-        if (a.zbc == 0) ske = wrapi(k, a.nz);
-        else ske = k < 0 ? -1 - k : (k >= a.nz ? 2 * a.nz - 1 - k : k);
-        long long srce = si + sj * a.sj + (long long)ske * a.sk;
-        for (int f = 0; f < 4; ++f) {
-            if (f == 2 || !a.f[f]) continue;
-            B *p = (B *)a.f[f];
-            p[dst] = p[srce];
-        }
-        // w: odd about the walls, w(nz) = 0
-        B *pw = (B *)a.f[2];
-        if (a.zbc == 0) {
-            pw[dst] = pw[srce];
-        } else if (k == a.nz) {
-            pw[dst] = (B)0;
-        } else {
-            int sko = k < 0 ? -k : (k > a.nz ? 2 * a.nz - k : k);
-            B v = pw[si + sj * a.sj + (long long)sko * a.sk];
-            pw[dst] = (k < 0 || k > a.nz) ? (B)(v ^ sign_bit) : v;
-        }
+    int si = wrapi(i, a.nx), sj = wrapi(j, a.ny);
+    long long dst = i + j * a.sj + k * a.sk;
+    int ske;
+    if (a.zbc == 0) ske = wrapi(k, a.nz);
+    else ske = k < 0 ? -1 - k : (k >= a.nz ? 2 * a.nz - 1 - k : k);
+    long long srce = si + sj * a.sj + (long long)ske * a.sk;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        if (f == 2 || !a.f[f]) continue;
+        B *p = (B *)a.f[f];
+        p[dst] = p[srce];
     }
+    B *pw = (B *)a.f[2];
+    if (a.zbc == 0) {
+        pw[dst] = pw[srce];
+    } else if (k == a.nz) {
+        pw[dst] = (B)0;
+    } else {
+        int sko = k < 0 ? -k : (k > a.nz ? 2 * a.nz - k : k);
+        B v = pw[si + sj * a.sj + (long long)sko * a.sk];
+        pw[dst] = (k < 0 || k > a.nz) ? (B)(v ^ sign_bit) : v;
+    }
+}
+
+template <typename B, int G>
+__global__ void __launch_bounds__(128) fill_kernel(FillArgs a)
+{
+    // blocks [0, b0): z planes; [b0, b1): y rows; [b1, end): x ghosts
+    int b = blockIdx.x;
+    if (b < a.b0) {                        // full z planes: row r of 2G * py rows
+        int r = b / a.gxp, bx = b - r * a.gxp;
+        int i = bx * 128 + threadIdx.x - G;
+        if (i >= a.nx + G) return;
+        int p = r / a.py, j = r - p * a.py - G;
+        int k = p < G ? p - G : a.nz + (p - G);
+        fill_one<B, G>(a, i, j, k);
+    } else if (b < a.b1) {                 // y rows of interior levels
+        b -= a.b0;
+        int r = b / a.gxp, bx = b - r * a.gxp;
+        int i = bx * 128 + threadIdx.x - G;
+        if (i >= a.nx + G) return;
+        int k = r / (2 * G), q = r - k * (2 * G);
+        int j = q < G ? q - G : a.ny + (q - G);
+        fill_one<B, G>(a, i, j, k);
+    } else {                               // x ghosts of interior rows
+        b -= a.b1;
+        int k = b / a.gxx, bx = b - k * a.gxx;
+        int t = bx * 128 + threadIdx.x;
+        if (t >= 2 * G * a.ny) return;
+        int j = t / (2 * G), q = t - j * (2 * G);
+        int i = q < G ? q - G : a.nx + (q - G);
+        fill_one<B, G>(a, i, j, k);
+    }
+}
+
+template <typename B>
+static cudaError_t fill_dispatch(int g, unsigned grid, const FillArgs &a, cudaStream_t s)
+{
+    switch (g) {
+    case 1: fill_kernel<B, 1><<<grid, 128, 0, s>>>(a); break;
+    case 2: fill_kernel<B, 2><<<grid, 128, 0, s>>>(a); break;
+    case 3: fill_kernel<B, 3><<<grid, 128, 0, s>>>(a); break;
+    case 4: fill_kernel<B, 4><<<grid, 128, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------- diagnostics
@@ -182,6 +202,7 @@ namespace kl {
 cudaError_t fill_ghosts_launch(int esize, const kl_grid &g, void *u, void *v, void *w, void *nu,
                                cudaStream_t s)
 {
+    if (g.g < 1 || g.g > 4) return cudaErrorInvalidValue;
     FillArgs a;
     size_t off = (size_t)g.origin * esize;
     a.f[0] = (char *)u + off;
@@ -193,20 +214,21 @@ cudaError_t fill_ghosts_launch(int esize, const kl_grid &g, void *u, void *v, vo
     a.nx = g.nx;
     a.ny = g.ny;
     a.nz = g.nz;
-    a.g = g.g;
     a.zbc = g.zbc;
-    a.px = g.nx + 2LL * g.g;
-    a.py = g.ny + 2LL * g.g;
-    a.n_zp = 2LL * g.g * a.px * a.py;
-    a.n_yr = (long long)g.nz * 2 * g.g * a.px;
-    a.n_xp = (long long)g.nz * g.ny * 2 * g.g;
-    a.total = a.n_zp + a.n_yr + a.n_xp;
-    long long blocks = (a.total + 255) / 256;
-    if (blocks > 4096) blocks = 4096;
-    if (esize == 8) fill_kernel<unsigned long long><<<(unsigned)blocks, 256, 0, s>>>(a);
-    else if (esize == 4) fill_kernel<unsigned int><<<(unsigned)blocks, 256, 0, s>>>(a);
-    else fill_kernel<unsigned short><<<(unsigned)blocks, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    a.px = g.nx + 2 * g.g;
+    a.py = g.ny + 2 * g.g;
+    a.gxp = (a.px + 127) / 128;
+    a.gxx = (2 * g.g * g.ny + 127) / 128;
+    long long b0 = (long long)a.gxp * 2 * g.g * a.py;
+    long long b1 = b0 + (long long)a.gxp * 2 * g.g * g.nz;
+    long long bt = b1 + (long long)a.gxx * g.nz;
+    if (bt > 0x7fffffffLL) return cudaErrorInvalidValue;
+    a.b0 = (int)b0;
+    a.b1 = (int)b1;
+    unsigned grid = (unsigned)bt;
+    if (esize == 8) return fill_dispatch<unsigned long long>(g.g, grid, a, s);
+    if (esize == 4) return fill_dispatch<unsigned int>(g.g, grid, a, s);
+    return fill_dispatch<unsigned short>(g.g, grid, a, s);
 }
 
 int diag_blocks(int nsm) { return nsm * 4; }

@@ -659,14 +659,16 @@ kl_tendency(const kl_args a, const __grid_constant__ kl_tmap tm_u,
 // Same plane ring as zmarch (tile 64 x KL_TYS, KL_MBY warps, each warp KL_MPY
 // consecutive rows); every face flux is formed once and diffusion is folded
 // into it:
-//  * lane l of a warp owns the column pair (x0 + l, x0 + l + 32); the pair is
-//    one packed value (f32x2 for f32 compute, two doubles for f64), so every
-//    arithmetic step serves two points;
-//  * x: a lane forms the flux on one face of each of its columns and gets the
-//    other face from its neighbour lane by a shuffle; the one face per row
-//    that lies past the warp's 64 columns is formed for all rows of the warp
-//    in a single side pass (lane e: field e / MPY, row e % MPY);
-//  * y: the MPY + 1 faces of a thread's consecutive rows are formed once;
+//  * lane l of a warp owns the two adjacent columns c0 = x0 + 2l, c1 = c0 + 1
+//    as one packed value (f32x2 for f32 compute, two doubles for f64); an
+//    aligned pair is one 8-byte (f32) shared load that lands in the packed
+//    register, odd offsets are formed from two aligned pairs, and results are
+//    stored with one vector store per field;
+//  * x: a lane forms the faces of both its columns on one side and gets the
+//    face on the other side of the pair from its neighbour lane by a shuffle;
+//    the one face per row beyond the warp's 64 columns is formed for all rows
+//    of the warp in one side pass (lane e: field e / MPY, row e % MPY);
+//  * y: a thread's consecutive rows share their faces (two live per field);
 //  * z: the top face of level k is carried as the bottom face of level k+1;
 //  * constant-nu diffusion: the diffusive flux nu (a_{m+1} - a_m) / d of a face
 //    is added to the advective flux of the same face, using the difference
@@ -687,10 +689,10 @@ __device__ __forceinline__ V vsub(V a, V b) { return vmk(a.lo - b.lo, a.hi - b.h
 __device__ __forceinline__ V vmul(V a, V b) { return vmk(a.lo * b.lo, a.hi * b.hi); }
 __device__ __forceinline__ V vfma(V a, V b, V c) { return vmk(fma(a.lo, b.lo, c.lo), fma(a.hi, b.hi, c.hi)); }
 __device__ __forceinline__ V vabs(V a) { return vmk(fabs(a.lo), fabs(a.hi)); }
-__device__ __forceinline__ V vshfl(V a, int src)
-{
-    return vmk(__shfl_sync(0xffffffffu, a.lo, src), __shfl_sync(0xffffffffu, a.hi, src));
-}
+// aligned pair of consecutive elements at p (16-byte aligned)
+__device__ __forceinline__ V vld(const T *p) { double2 d = *(const double2 *)p; return vmk(d.x, d.y); }
+__device__ __forceinline__ void vst(T *p, V a) { *(double2 *)p = make_double2(a.lo, a.hi); }
+__device__ __forceinline__ V vldg(const T *p) { return vld(p); }
 #else
 struct V { unsigned long long b; };
 __device__ __forceinline__ V vmk(float a, float c)
@@ -721,19 +723,35 @@ __device__ __forceinline__ V vfma(V a, V b, V c)
     return r;
 }
 __device__ __forceinline__ V vabs(V a) { V r; r.b = a.b & 0x7fffffff7fffffffull; return r; }
-__device__ __forceinline__ V vshfl(V a, int src)
+#if KL_DTYPE == 1
+__device__ __forceinline__ V vld(const T *p) { V r; r.b = *(const unsigned long long *)p; return r; }
+__device__ __forceinline__ void vst(T *p, V a) { *(unsigned long long *)p = a.b; }
+#else
+// two 16-bit values in one 32-bit word, widened to f32
+__device__ __forceinline__ V vld(const T *p)
 {
-    V r;
-    r.b = __shfl_sync(0xffffffffu, a.b, src);
-    return r;
+    unsigned w = *(const unsigned *)p;
+    kl_u16 lo = (kl_u16)(w & 0xffffu), hi = (kl_u16)(w >> 16);
+    return vmk(lds(&lo), lds(&hi));
+}
+__device__ __forceinline__ void vst(T *p, V a)
+{
+    kl_u16 lo, hi;
+    st(&lo, vlo(a));
+    st(&hi, vhi(a));
+    *(unsigned *)p = (unsigned)lo | ((unsigned)hi << 16);
 }
 #endif
+__device__ __forceinline__ V vldg(const T *p) { return vld(p); }
+#endif
 __device__ __forceinline__ V vsplat(C a) { return vmk(a, a); }
+// (hi of a, lo of b): the pair starting one element after a's
+__device__ __forceinline__ V vcross(V a, V b) { return vmk(vhi(a), vlo(b)); }
+
+struct kl_vk { V c37, cm8, c10, cm5; };
 
 // packed face flux with the diffusive part folded in:
 //   G = F + kd * d1,  F as flux5 / flux2 (scaled by 1/KL_FS), d1 = a2 - a3
-struct kl_vk { V c37, cm8, c10, cm5; };
-
 __device__ __forceinline__ V kl_vflux(const kl_vk &K, V Us, V a0, V a1, V a2, V a3, V a4, V a5, V kd)
 {
     V d1 = vsub(a2, a3);
@@ -754,7 +772,7 @@ __device__ __forceinline__ V kl_vflux(const kl_vk &K, V Us, V a0, V a1, V a2, V 
     return f;
 }
 
-// scalar twin of kl_vflux for the side pass
+// scalar twin for the side pass
 __device__ __forceinline__ C kl_sflux(C Us, C a0, C a1, C a2, C a3, C a4, C a5, C kd)
 {
     C d1 = a2 - a3;
@@ -781,14 +799,17 @@ __device__ __forceinline__ C kl_sflux(C Us, C a0, C a1, C a2, C a3, C a4, C a5, 
 
 #define KL_OFF(x, row) ((((row) + KL_H) * KL_PITCH + (x)) * (int)sizeof(T))
 
+// aligned pair of field F on plane k+DK at columns (lx + DX, lx + DX + 1),
+// tile row `row`; DX even (lx is even), offsets checked at compile time
 template <int F, int DK, int DX>
-__device__ __forceinline__ V kl_pair(const char *const *pl, int lx, int row)
+__device__ __forceinline__ V kl_pr(const char *const *pl, int lx, int row)
 {
     static_assert(DK >= -KL_R && DK <= KL_R, "plane outside the staged window");
-    static_assert(DX >= -KL_H && DX <= KL_H, "x offset outside the halo");
+    static_assert(DX % 2 == 0, "pairs start on even columns");
+    // lx ranges over [LPAD, LPAD + 62]: the pair must stay inside [0, PITCH)
+    static_assert(DX >= -KL_LPAD && KL_LPAD + 62 + DX + 1 < KL_PITCH, "x offset outside the box");
     static_assert(F >= 0 && F < 3, "field index");
-    const char *b = pl[DK + KL_R] + F * KL_PLANE_BYTES;
-    return vmk(lds((const T *)(b + KL_OFF(lx + DX, row))), lds((const T *)(b + KL_OFF(lx + 32 + DX, row))));
+    return vld((const T *)(pl[DK + KL_R] + F * KL_PLANE_BYTES + KL_OFF(lx + DX, row)));
 }
 
 extern "C" __global__ void __launch_bounds__(32 * KL_MBY, KL_MMINB)
@@ -798,6 +819,10 @@ kl_tendency(const kl_args a, const __grid_constant__ kl_tmap tm_u,
 {
     static_assert(KL_MBX == 32 && KL_MPX == 2, "zpack tiles are 64 columns wide");
     static_assert(3 * KL_MPY <= 32, "side pass needs 3 x rows <= 32 lanes");
+    // reach of the pairs and the side pass: 4 columns left and right of the
+    // tile for the 5th-order scheme, 2 left and 1 right otherwise
+    static_assert(KL_LPAD % 2 == 0 && KL_LPAD >= (KL_ADV == 5 ? 4 : 2), "left pad too small");
+    static_assert(KL_PITCH >= KL_LPAD + 64 + (KL_ADV == 5 ? 3 : 1), "right pad too small");
     extern __shared__ unsigned char kl_smem_raw[];
     unsigned char *ring = (unsigned char *)(((unsigned long long)kl_smem_raw + 127) & ~127ull);
     unsigned long long *bars = (unsigned long long *)(ring + KL_NS * KL_SLOT_BYTES);
@@ -835,14 +860,15 @@ kl_tendency(const kl_args a, const __grid_constant__ kl_tmap tm_u,
 
     // coefficients (f32 kernels read the f32 copies; no f64 arithmetic)
     const C dxi = KL_CO(a, 0), dyi = KL_CO(a, 1), nu = KL_CO(a, 4);
-    const C cx = KL_FS * dxi, cy = KL_FS * dyi;
-    const C kdx = nu * dxi / KL_FS, kdy = nu * dyi / KL_FS;
+    const C kdx = nu * dxi / KL_FS;
     kl_vk K;
     K.c37 = vsplat(C(37)); K.cm8 = vsplat(C(-8)); K.c10 = vsplat(C(10)); K.cm5 = vsplat(C(-5));
-    const V vkdx = vsplat(kdx), vkdy = vsplat(kdy), vcx = vsplat(cx), vcy = vsplat(cy);
+    const V vkdx = vsplat(kdx), vkdy = vsplat(nu * dyi / KL_FS);
+    const V vcx = vsplat(KL_FS * dxi), vcy = vsplat(KL_FS * dyi);
 
     const int r0 = warp * KL_MPY;                       // first row of this thread (tile local)
-    const int lx = KL_LPAD + lane;                      // local x of the low column
+    const int lx = KL_LPAD + 2 * lane;                  // local x of column c0 (even)
+    const int c0 = tx0 + 2 * lane;                      // global interior column of c0
 
     V zb[KL_MPY][3];
     bool timed_out = false;
@@ -869,23 +895,20 @@ kl_tendency(const kl_args a, const __grid_constant__ kl_tmap tm_u,
 #pragma unroll
         for (int d = -KL_R; d <= KL_R; ++d)
             pl[d + KL_R] = (const char *)(ring + ((k + d - p_first) % KL_NS) * KL_SLOT_BYTES);
-        // packed pair of field f (0 u, 1 v, 2 w) on plane k+dk, columns lx+dx
-        // and lx+32+dx, tile row `row` (offsets checked at compile time)
-#define KL_P(f, dk, dx, row) kl_pair<f, dk, dx>(pl, lx, row)
+#define KL_Q(f, dk, dx, row) kl_pr<f, dk, dx>(pl, lx, row)
 
         const kl_zmetric Z = kl_make_z(a, k);
-        const C czu = KL_FS * Z.dzi, czw = KL_FS * Z.dzhi;
-        const C kzu_top = nu * Z.dzhi_up / KL_FS;         // u, v top face zh_{k+1}
-        const C kzw_top = nu * Z.dzi / KL_FS;             // w top face z_k
-        const V vkzu_top = vsplat(kzu_top), vkzw_top = vsplat(kzw_top);
+        const V vczu = vsplat(KL_FS * Z.dzi), vczw = vsplat(KL_FS * Z.dzhi);
+        const V vkzu_top = vsplat(nu * Z.dzhi_up / KL_FS);   // u, v top face zh_{k+1}
+        const V vkzw_top = vsplat(nu * Z.dzi / KL_FS);       // w top face z_k
 
-        // ---- side pass: the x face past the warp's columns, for every row
+        // ---- side pass: the x face beyond the warp's columns, every row
         C extra;
         {
             int e = lane < 3 * KL_MPY ? lane : 0;
             int f = e / KL_MPY, row = r0 + e % KL_MPY;
-            // u: face at centre x0-1 (window x0-3 .. x0+2); v, w: face at edge x0+64
-            // (window x0+61 .. x0+66)
+            // u: face at centre x0-1 (values x0-3 .. x0+2, Us = a2 + a3);
+            // v, w: face at edge x0+64 (values x0+61 .. x0+66, Us = two u's)
             int xs = f == 0 ? KL_LPAD - 3 : KL_LPAD + 61;
             const char *base = pl[KL_R] + f * KL_PLANE_BYTES;
             C a2 = lds((const T *)(base + KL_OFF(xs + 2, row)));
@@ -898,100 +921,127 @@ kl_tendency(const kl_args a, const __grid_constant__ kl_tmap tm_u,
 #else
             C a0 = C(0), a1 = C(0), a4 = C(0), a5 = C(0);
 #endif
-            C us;
-            if (f == 0) {
-                us = a2 + a3;                                   // u(x0-1) + u(x0)
-            } else {
-                // u at x0+64 on rows j-1, j (v) or planes k-1, k (w)
-                const char *ub = pl[KL_R];
-                const char *ub2 = f == 1 ? pl[KL_R] : pl[KL_R - 1];
-                int row2 = f == 1 ? row - 1 : row;
-                us = lds((const T *)(ub2 + KL_OFF(KL_LPAD + 64, row2))) +
-                     lds((const T *)(ub + KL_OFF(KL_LPAD + 64, row)));
-            }
+            // branch-free choice of the two velocities that form Us
+            const char *p1 = f == 0 ? base + KL_OFF(xs + 2, row)
+                           : (f == 1 ? pl[KL_R] + KL_OFF(KL_LPAD + 64, row - 1)
+                                     : pl[KL_R - 1] + KL_OFF(KL_LPAD + 64, row));
+            const char *p2 = f == 0 ? base + KL_OFF(xs + 3, row) : pl[KL_R] + KL_OFF(KL_LPAD + 64, row);
+            C us = lds((const T *)p1) + lds((const T *)p2);
             extra = kl_sflux(us, a0, a1, a2, a3, a4, a5, kdx);
         }
 
-        // ---- y faces of this thread's rows (shared by consecutive rows)
-        V fuy[KL_MPY + 1], fvy[KL_MPY + 1], fwy[KL_MPY + 1];
-#pragma unroll
-        for (int m = 0; m <= KL_MPY; ++m) {
-            const int yr = r0 + m;                         // edge yh_{yr} (u, w); centre y_{yr-1} (v)
-            fuy[m] = kl_vflux(K, vadd(KL_P(1, 0, -1, yr), KL_P(1, 0, 0, yr)), KL_A5(KL_P(0, 0, 0, yr - 3)), KL_A5(KL_P(0, 0, 0, yr - 2)), KL_P(0, 0, 0, yr - 1),
-                              KL_P(0, 0, 0, yr), KL_A5(KL_P(0, 0, 0, yr + 1)), KL_A5(KL_P(0, 0, 0, yr + 2)), vkdy);
-            fvy[m] = kl_vflux(K, vadd(KL_P(1, 0, 0, yr - 1), KL_P(1, 0, 0, yr)), KL_A5(KL_P(1, 0, 0, yr - 3)), KL_A5(KL_P(1, 0, 0, yr - 2)), KL_P(1, 0, 0, yr - 1),
-                              KL_P(1, 0, 0, yr), KL_A5(KL_P(1, 0, 0, yr + 1)), KL_A5(KL_P(1, 0, 0, yr + 2)), vkdy);
-            fwy[m] = kl_vflux(K, vadd(KL_P(1, -1, 0, yr), KL_P(1, 0, 0, yr)), KL_A5(KL_P(2, 0, 0, yr - 3)), KL_A5(KL_P(2, 0, 0, yr - 2)), KL_P(2, 0, 0, yr - 1),
-                              KL_P(2, 0, 0, yr), KL_A5(KL_P(2, 0, 0, yr + 1)), KL_A5(KL_P(2, 0, 0, yr + 2)), vkdy);
+        // ---- y faces: bottom face of the first row; rows then roll upwards
+        V fuy_b, fvy_b, fwy_b;
+        {
+            const int yr = r0;
+            fuy_b = kl_vflux(K, vadd(vcross(KL_Q(1, 0, -2, yr), KL_Q(1, 0, 0, yr)), KL_Q(1, 0, 0, yr)),
+                             KL_A5(KL_Q(0, 0, 0, yr - 3)), KL_A5(KL_Q(0, 0, 0, yr - 2)), KL_Q(0, 0, 0, yr - 1),
+                             KL_Q(0, 0, 0, yr), KL_A5(KL_Q(0, 0, 0, yr + 1)), KL_A5(KL_Q(0, 0, 0, yr + 2)), vkdy);
+            fvy_b = kl_vflux(K, vadd(KL_Q(1, 0, 0, yr - 1), KL_Q(1, 0, 0, yr)),
+                             KL_A5(KL_Q(1, 0, 0, yr - 3)), KL_A5(KL_Q(1, 0, 0, yr - 2)), KL_Q(1, 0, 0, yr - 1),
+                             KL_Q(1, 0, 0, yr), KL_A5(KL_Q(1, 0, 0, yr + 1)), KL_A5(KL_Q(1, 0, 0, yr + 2)), vkdy);
+            fwy_b = kl_vflux(K, vadd(KL_Q(1, -1, 0, yr), KL_Q(1, 0, 0, yr)),
+                             KL_A5(KL_Q(2, 0, 0, yr - 3)), KL_A5(KL_Q(2, 0, 0, yr - 2)), KL_Q(2, 0, 0, yr - 1),
+                             KL_Q(2, 0, 0, yr), KL_A5(KL_Q(2, 0, 0, yr + 1)), KL_A5(KL_Q(2, 0, 0, yr + 2)), vkdy);
         }
 
 #pragma unroll
         for (int r = 0; r < KL_MPY; ++r) {
             const int yr = r0 + r;
-            // ---- x faces: u right face (centre), v and w left faces (edge)
-            V fux = kl_vflux(K, vadd(KL_P(0, 0, 0, yr), KL_P(0, 0, 1, yr)), KL_A5(KL_P(0, 0, -2, yr)), KL_A5(KL_P(0, 0, -1, yr)), KL_P(0, 0, 0, yr),
-                             KL_P(0, 0, 1, yr), KL_A5(KL_P(0, 0, 2, yr)), KL_A5(KL_P(0, 0, 3, yr)), vkdx);
-            V fvx = kl_vflux(K, vadd(KL_P(0, 0, 0, yr - 1), KL_P(0, 0, 0, yr)), KL_A5(KL_P(1, 0, -3, yr)), KL_A5(KL_P(1, 0, -2, yr)), KL_P(1, 0, -1, yr),
-                             KL_P(1, 0, 0, yr), KL_A5(KL_P(1, 0, 1, yr)), KL_A5(KL_P(1, 0, 2, yr)), vkdx);
-            V fwx = kl_vflux(K, vadd(KL_P(0, -1, 0, yr), KL_P(0, 0, 0, yr)), KL_A5(KL_P(2, 0, -3, yr)), KL_A5(KL_P(2, 0, -2, yr)), KL_P(2, 0, -1, yr),
-                             KL_P(2, 0, 0, yr), KL_A5(KL_P(2, 0, 1, yr)), KL_A5(KL_P(2, 0, 2, yr)), vkdx);
-            // neighbour faces
-            V ul = vshfl(fux, (lane + 31) & 31);            // (lane-1).(lo, hi)
-            V vr = vshfl(fvx, (lane + 1) & 31);              // (lane+1).(lo, hi)
-            V wr = vshfl(fwx, (lane + 1) & 31);
+            // ---- x faces of both columns: u right faces (centres), v, w left
+            // faces (edges); pairs at even offsets, odd offsets by vcross
+            V u_m2 = KL_A5(KL_Q(0, 0, -2, yr)), u_0 = KL_Q(0, 0, 0, yr), u_2 = KL_Q(0, 0, 2, yr);
+            V fux = kl_vflux(K, vadd(u_0, vcross(u_0, u_2)),
+                             KL_A5(u_m2), KL_A5(vcross(u_m2, u_0)), u_0,
+                             vcross(u_0, u_2), KL_A5(u_2), KL_A5(vcross(u_2, KL_Q(0, 0, 4, yr))), vkdx);
+            V v_m4 = KL_A5(KL_Q(1, 0, -4, yr)), v_m2 = KL_Q(1, 0, -2, yr), v_0 = KL_Q(1, 0, 0, yr),
+              v_2 = KL_Q(1, 0, 2, yr);
+            V fvx = kl_vflux(K, vadd(KL_Q(0, 0, 0, yr - 1), u_0),
+                             KL_A5(vcross(v_m4, v_m2)), KL_A5(v_m2), vcross(v_m2, v_0),
+                             v_0, KL_A5(vcross(v_0, v_2)), KL_A5(v_2), vkdx);
+            V w_m4 = KL_A5(KL_Q(2, 0, -4, yr)), w_m2 = KL_Q(2, 0, -2, yr), w_0 = KL_Q(2, 0, 0, yr),
+              w_2 = KL_Q(2, 0, 2, yr);
+            V fwx = kl_vflux(K, vadd(KL_Q(0, -1, 0, yr), u_0),
+                             KL_A5(vcross(w_m4, w_m2)), KL_A5(w_m2), vcross(w_m2, w_0),
+                             w_0, KL_A5(vcross(w_0, w_2)), KL_A5(w_2), vkdx);
+            // faces on the other side: u left = (lane-1 hi, own lo);
+            // v, w right = (own hi, lane+1 lo); warp edges from the side pass
+            C ul_hi = __shfl_sync(0xffffffffu, vhi(fux), (lane + 31) & 31);
+            C vr_lo = __shfl_sync(0xffffffffu, vlo(fvx), (lane + 1) & 31);
+            C wr_lo = __shfl_sync(0xffffffffu, vlo(fwx), (lane + 1) & 31);
             C eu = __shfl_sync(0xffffffffu, extra, r);
             C ev = __shfl_sync(0xffffffffu, extra, KL_MPY + r);
             C ew = __shfl_sync(0xffffffffu, extra, 2 * KL_MPY + r);
-            if (lane == 0) ul = vmk(eu, vlo(ul));           // (face x0-1, face x0+31)
-            if (lane == 31) {                                // (face x0+32, face x0+64)
-                vr = vmk(vhi(vr), ev);
-                wr = vmk(vhi(wr), ew);
-            }
+            V ul = vmk(lane == 0 ? eu : ul_hi, vlo(fux));
+            V vr = vmk(vhi(fvx), lane == 31 ? ev : vr_lo);
+            V wr = vmk(vhi(fwx), lane == 31 ? ew : wr_lo);
+
+            // ---- top y faces of this row
+            const int yt = yr + 1;
+            V fuy_t = kl_vflux(K, vadd(vcross(KL_Q(1, 0, -2, yt), KL_Q(1, 0, 0, yt)), KL_Q(1, 0, 0, yt)),
+                               KL_A5(KL_Q(0, 0, 0, yt - 3)), KL_A5(KL_Q(0, 0, 0, yt - 2)), KL_Q(0, 0, 0, yt - 1),
+                               KL_Q(0, 0, 0, yt), KL_A5(KL_Q(0, 0, 0, yt + 1)), KL_A5(KL_Q(0, 0, 0, yt + 2)), vkdy);
+            V fvy_t = kl_vflux(K, vadd(KL_Q(1, 0, 0, yt - 1), KL_Q(1, 0, 0, yt)),
+                               KL_A5(KL_Q(1, 0, 0, yt - 3)), KL_A5(KL_Q(1, 0, 0, yt - 2)), KL_Q(1, 0, 0, yt - 1),
+                               KL_Q(1, 0, 0, yt), KL_A5(KL_Q(1, 0, 0, yt + 1)), KL_A5(KL_Q(1, 0, 0, yt + 2)), vkdy);
+            V fwy_t = kl_vflux(K, vadd(KL_Q(1, -1, 0, yt), KL_Q(1, 0, 0, yt)),
+                               KL_A5(KL_Q(2, 0, 0, yt - 3)), KL_A5(KL_Q(2, 0, 0, yt - 2)), KL_Q(2, 0, 0, yt - 1),
+                               KL_Q(2, 0, 0, yt), KL_A5(KL_Q(2, 0, 0, yt + 1)), KL_A5(KL_Q(2, 0, 0, yt + 2)), vkdy);
+
             // ---- z faces: bottom carried, top formed here
-            V fz_u, fz_v, fz_w;
-            fz_u = kl_vflux(K, vadd(KL_P(2, 1, -1, yr), KL_P(2, 1, 0, yr)), KL_A5(KL_P(0, -2, 0, yr)), KL_A5(KL_P(0, -1, 0, yr)), KL_P(0, 0, 0, yr),
-                            KL_P(0, 1, 0, yr), KL_A5(KL_P(0, 2, 0, yr)), KL_A5(KL_P(0, 3, 0, yr)), vkzu_top);
-            fz_v = kl_vflux(K, vadd(KL_P(2, 1, 0, yr - 1), KL_P(2, 1, 0, yr)), KL_A5(KL_P(1, -2, 0, yr)), KL_A5(KL_P(1, -1, 0, yr)), KL_P(1, 0, 0, yr),
-                            KL_P(1, 1, 0, yr), KL_A5(KL_P(1, 2, 0, yr)), KL_A5(KL_P(1, 3, 0, yr)), vkzu_top);
-            fz_w = kl_vflux(K, vadd(KL_P(2, 0, 0, yr), KL_P(2, 1, 0, yr)), KL_A5(KL_P(2, -2, 0, yr)), KL_A5(KL_P(2, -1, 0, yr)), KL_P(2, 0, 0, yr),
-                            KL_P(2, 1, 0, yr), KL_A5(KL_P(2, 2, 0, yr)), KL_A5(KL_P(2, 3, 0, yr)), vkzw_top);
+            V fz_u = kl_vflux(K, vadd(vcross(KL_Q(2, 1, -2, yr), KL_Q(2, 1, 0, yr)), KL_Q(2, 1, 0, yr)),
+                              KL_A5(KL_Q(0, -2, 0, yr)), KL_A5(KL_Q(0, -1, 0, yr)), u_0,
+                              KL_Q(0, 1, 0, yr), KL_A5(KL_Q(0, 2, 0, yr)), KL_A5(KL_Q(0, 3, 0, yr)), vkzu_top);
+            V fz_v = kl_vflux(K, vadd(KL_Q(2, 1, 0, yr - 1), KL_Q(2, 1, 0, yr)),
+                              KL_A5(KL_Q(1, -2, 0, yr)), KL_A5(KL_Q(1, -1, 0, yr)), v_0,
+                              KL_Q(1, 1, 0, yr), KL_A5(KL_Q(1, 2, 0, yr)), KL_A5(KL_Q(1, 3, 0, yr)), vkzu_top);
+            V fz_w = kl_vflux(K, vadd(w_0, KL_Q(2, 1, 0, yr)),
+                              KL_A5(KL_Q(2, -2, 0, yr)), KL_A5(KL_Q(2, -1, 0, yr)), w_0,
+                              KL_Q(2, 1, 0, yr), KL_A5(KL_Q(2, 2, 0, yr)), KL_A5(KL_Q(2, 3, 0, yr)), vkzw_top);
             if (k == kb) {
                 // bottom faces of the first level: u, v at zh_k, w at z_{k-1}
                 const V kzu_b = vsplat(nu * Z.dzhi / KL_FS), kzw_b = vsplat(nu * Z.dzi_dn / KL_FS);
-                zb[r][0] = kl_vflux(K, vadd(KL_P(2, 0, -1, yr), KL_P(2, 0, 0, yr)), KL_A5(KL_P(0, -3, 0, yr)), KL_A5(KL_P(0, -2, 0, yr)), KL_P(0, -1, 0, yr),
-                                    KL_P(0, 0, 0, yr), KL_A5(KL_P(0, 1, 0, yr)), KL_A5(KL_P(0, 2, 0, yr)), kzu_b);
-                zb[r][1] = kl_vflux(K, vadd(KL_P(2, 0, 0, yr - 1), KL_P(2, 0, 0, yr)), KL_A5(KL_P(1, -3, 0, yr)), KL_A5(KL_P(1, -2, 0, yr)), KL_P(1, -1, 0, yr),
-                                    KL_P(1, 0, 0, yr), KL_A5(KL_P(1, 1, 0, yr)), KL_A5(KL_P(1, 2, 0, yr)), kzu_b);
-                zb[r][2] = kl_vflux(K, vadd(KL_P(2, -1, 0, yr), KL_P(2, 0, 0, yr)), KL_A5(KL_P(2, -3, 0, yr)), KL_A5(KL_P(2, -2, 0, yr)), KL_P(2, -1, 0, yr),
-                                    KL_P(2, 0, 0, yr), KL_A5(KL_P(2, 1, 0, yr)), KL_A5(KL_P(2, 2, 0, yr)), kzw_b);
+                zb[r][0] = kl_vflux(K, vadd(vcross(KL_Q(2, 0, -2, yr), w_0), w_0),
+                                    KL_A5(KL_Q(0, -3, 0, yr)), KL_A5(KL_Q(0, -2, 0, yr)), KL_Q(0, -1, 0, yr),
+                                    u_0, KL_A5(KL_Q(0, 1, 0, yr)), KL_A5(KL_Q(0, 2, 0, yr)), kzu_b);
+                zb[r][1] = kl_vflux(K, vadd(KL_Q(2, 0, 0, yr - 1), w_0),
+                                    KL_A5(KL_Q(1, -3, 0, yr)), KL_A5(KL_Q(1, -2, 0, yr)), KL_Q(1, -1, 0, yr),
+                                    v_0, KL_A5(KL_Q(1, 1, 0, yr)), KL_A5(KL_Q(1, 2, 0, yr)), kzu_b);
+                zb[r][2] = kl_vflux(K, vadd(KL_Q(2, -1, 0, yr), w_0),
+                                    KL_A5(KL_Q(2, -3, 0, yr)), KL_A5(KL_Q(2, -2, 0, yr)), KL_Q(2, -1, 0, yr),
+                                    w_0, KL_A5(KL_Q(2, 1, 0, yr)), KL_A5(KL_Q(2, 2, 0, yr)), kzw_b);
             }
             // ---- tendencies
-            V tu = vfma(vsub(ul, fux), vcx, vfma(vsub(fuy[r], fuy[r + 1]), vcy,
-                                                 vmul(vsub(zb[r][0], fz_u), vsplat(czu))));
-            V tv = vfma(vsub(fvx, vr), vcx, vfma(vsub(fvy[r], fvy[r + 1]), vcy,
-                                                 vmul(vsub(zb[r][1], fz_v), vsplat(czu))));
-            V tw = vfma(vsub(fwx, wr), vcx, vfma(vsub(fwy[r], fwy[r + 1]), vcy,
-                                                 vmul(vsub(zb[r][2], fz_w), vsplat(czw))));
+            V tu = vfma(vsub(ul, fux), vcx, vfma(vsub(fuy_b, fuy_t), vcy, vmul(vsub(zb[r][0], fz_u), vczu)));
+            V tv = vfma(vsub(fvx, vr), vcx, vfma(vsub(fvy_b, fvy_t), vcy, vmul(vsub(zb[r][1], fz_v), vczu)));
+            V tw = vfma(vsub(fwx, wr), vcx, vfma(vsub(fwy_b, fwy_t), vcy, vmul(vsub(zb[r][2], fz_w), vczw)));
             zb[r][0] = fz_u;
             zb[r][1] = fz_v;
             zb[r][2] = fz_w;
+            fuy_b = fuy_t;
+            fvy_b = fvy_t;
+            fwy_b = fwy_t;
+            if (KL_ZBC == 1 && k == 0) tw = vsplat(C(0));
             const int j = ty0 + yr;
             if (j < ny) {
-                const bool wall = KL_ZBC == 1 && k == 0;
-                const long long o = (long long)(tx0 + lane) + (long long)j * a.sj + (long long)k * a.sk;
-                if (tx0 + lane < nx) {
+                const long long o = (long long)c0 + (long long)j * a.sj + (long long)k * a.sk;
+                if (c0 + 1 < nx) {
+#if KL_ACC
+                    tu = vadd(tu, vldg(a.ut + o));
+                    tv = vadd(tv, vldg(a.vt + o));
+                    tw = vadd(tw, vldg(a.wt + o));
+#endif
+                    vst(a.ut + o, tu);
+                    vst(a.vt + o, tv);
+                    vst(a.wt + o, tw);
+                } else if (c0 < nx) {
                     out(a.ut + o, vlo(tu));
                     out(a.vt + o, vlo(tv));
-                    out(a.wt + o, wall ? C(0) : vlo(tw));
-                }
-                if (tx0 + lane + 32 < nx) {
-                    out(a.ut + o + 32, vhi(tu));
-                    out(a.vt + o + 32, vhi(tv));
-                    out(a.wt + o + 32, wall ? C(0) : vhi(tw));
+                    out(a.wt + o, vlo(tw));
                 }
             }
         }
-#undef KL_P
+#undef KL_Q
         __syncthreads();
         if (tid == 0 && p_next <= p_last) issue(p_next++);
     }

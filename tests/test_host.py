@@ -131,7 +131,7 @@ def test_wisdom_rules(tmp_path):
         rec("GPU A", "10.3", 1, (256, 256, 256), "direct:bx=32,by=2"),  # newer duplicate
     ])
     sel = lambda dev, cc, zbc, n: kl.kl_wisdom_select(p, dev, cc[0], cc[1], zbc, *n)
-    # rule 1, newest duplicate wins
+    # rule 1, equal times: the newest duplicate wins
     assert sel("GPU A", (10, 3), 1, (256, 256, 256)) == ("direct:bx=32,by=2", 1)
     # rule 2: same device, nearest size
     assert sel("GPU A", (10, 3), 1, (500, 500, 250)) == ("direct:bx=64", 2)
@@ -145,6 +145,14 @@ def test_wisdom_rules(tmp_path):
     # rule 5: nothing for this zbc ... and a missing file
     assert sel("GPU Z", (12, 0), 2, (60, 60, 60)) == ("default", 5)
     assert kl.kl_wisdom_select(str(tmp_path / "none"), "x", 1, 0, 0, 1, 1, 1) == ("default", 5)
+
+
+def test_wisdom_duplicates_fastest_session_wins(tmp_path):
+    p = str(tmp_path / "w.wisdom")
+    _write(p, [rec("G", "10.3", 0, (64, 64, 64), "direct:bx=16").replace("time_us=1.0", "time_us=9.0"),
+               rec("G", "10.3", 0, (64, 64, 64), "direct:bx=32").replace("time_us=1.0", "time_us=3.0"),
+               rec("G", "10.3", 0, (64, 64, 64), "direct:bx=64").replace("time_us=1.0", "time_us=5.0")])
+    assert kl.kl_wisdom_select(p, "G", 10, 3, 0, 64, 64, 64) == ("direct:bx=32", 1)
 
 
 def test_wisdom_distance_tie_takes_first_record(tmp_path):
