@@ -157,9 +157,9 @@ kl_status load_compiled(kl_ctx *ctx, const kl_op &op, const Config &cfg, const s
 }
 
 kl_status get_kernel(kl_ctx *ctx, const kl_op &op, const Config &cfg, int zbc, int zuni,
-                     Kernel **out)
+                     Kernel **out, bool batch)
 {
-    std::string key = compile_defines(op, cfg, zbc, zuni);
+    std::string key = compile_defines(op, cfg, zbc, zuni) + (batch ? " -DKL_BATCH=1" : "");
     auto it = ctx->kernels.find(key);
     if (it != ctx->kernels.end()) {
         *out = &it->second;
@@ -232,7 +232,7 @@ kl_status get_profile(kl_ctx *ctx, const kl_grid &g, Profile **out)
 
 // ------------------------------------------------------------ launch
 
-static kl_status check_op(const kl_op *op)
+kl_status check_op(const kl_op *op)
 {
     if (!op) return fail(KL_ERR_INVALID_ARG, "op is NULL");
     if (op->adv != 0 && op->adv != 2 && op->adv != 5)
@@ -245,7 +245,7 @@ static kl_status check_op(const kl_op *op)
     return KL_OK;
 }
 
-static kl_status check_fields(const kl_op &op, const kl_fields *f)
+kl_status check_fields(const kl_op &op, const kl_fields *f)
 {
     if (!f) return fail(KL_ERR_INVALID_ARG, "fields is NULL");
     if (!f->u || !f->v || !f->w || !f->ut || !f->vt || !f->wt)
@@ -327,29 +327,22 @@ static kl_status get_tmap(kl_ctx *ctx, const kl_op &op, const kl_grid &g, const 
     return KL_OK;
 }
 
-kl_status launch_config(kl_ctx *ctx, const kl_op &op, const Config &cfg, const kl_grid &g,
-                        const kl_fields &f, cudaStream_t s)
+kl_status make_kargs(kl_ctx *ctx, const kl_op &op, const Config &cfg, const kl_grid &g,
+                     const kl_fields &f, KArgs *ap, CUtensorMap maps[4])
 {
     std::string err;
     if (!config_check(op, cfg, &err)) return fail(KL_ERR_INVALID_ARG, "configuration: " + err);
     Geom geo;
     kl_status st = check_grid(&g, halo_of(op), &geo);
     if (st) return st;
-    int zuni = g.zh ? 0 : 1;
+    if (!config_fits(op, cfg, g, &f, &err)) return fail(KL_ERR_INVALID_ARG, "configuration: " + err);
     Profile *prof = nullptr;
-    if (!zuni) {
+    if (g.zh) {
         st = get_profile(ctx, g, &prof);
         if (st) return st;
     }
-    Kernel *k = nullptr;
-    auto t0 = std::chrono::steady_clock::now();
-    bool miss = ctx->kernels.find(compile_defines(op, cfg, g.zbc, zuni)) == ctx->kernels.end();
-    st = get_kernel(ctx, op, cfg, g.zbc, zuni, &k);
-    if (st) return st;
-    if (!miss) ctx->cache_hits++;
-
     int es = esize_of(op.dtype);
-    KArgs a;
+    KArgs &a = *ap;
     memset(&a, 0, sizeof a);
     const char *base[7] = {(const char *)f.u, (const char *)f.v, (const char *)f.w,
                            (const char *)f.nu, (const char *)f.ut, (const char *)f.vt,
@@ -381,42 +374,99 @@ kl_status launch_config(kl_ctx *ctx, const kl_op &op, const Config &cfg, const k
     a.tile_y0 = geo.y0;
     a.tile_z0 = geo.z0;
     fill_coefs(a, g);
-
-    if (!config_fits(op, cfg, g, &f, &err)) return fail(KL_ERR_INVALID_ARG, "configuration: " + err);
-    if (!space_size(cfg.family)) return fail(KL_ERR_INVALID_ARG, "unknown family");
-    CUresult r;
     if (cfg.family == 0) {
         a.nbx = (g.nx + cfg.bx * cfg.tx - 1) / (cfg.bx * cfg.tx);
         a.nby = (g.ny + cfg.by * cfg.ty - 1) / (cfg.by * cfg.ty);
         a.nbz = (g.nz + cfg.bz * cfg.tz - 1) / (cfg.bz * cfg.tz);
+    } else {
+        ZGeom z = zmarch_geometry(op, cfg);
+        a.kchunk = cfg.kc;
+        a.nbx = (g.nx + z.txs - 1) / z.txs;
+        a.nby = (g.ny + z.tys - 1) / z.tys;
+        a.nbz = (g.nz + cfg.kc - 1) / cfg.kc;
+        const void *fp[4] = {f.u, f.v, f.w, op.diff == 2 ? f.nu : f.u};
+        for (int q = 0; q < 4; ++q) {
+            st = get_tmap(ctx, op, g, z, fp[q], &maps[q]);
+            if (st) return st;
+        }
+    }
+    return KL_OK;
+}
+
+kl_status launch_config(kl_ctx *ctx, const kl_op &op, const Config &cfg, const kl_grid &g,
+                        const kl_fields &f, cudaStream_t s)
+{
+    KArgs a;
+    CUtensorMap maps[4];
+    kl_status st = make_kargs(ctx, op, cfg, g, f, &a, maps);
+    if (st) return st;
+    if (!space_size(cfg.family)) return fail(KL_ERR_INVALID_ARG, "unknown family");
+    int zuni = g.zh ? 0 : 1;
+    Kernel *k = nullptr;
+    auto t0 = std::chrono::steady_clock::now();
+    bool miss = ctx->kernels.find(compile_defines(op, cfg, g.zbc, zuni)) == ctx->kernels.end();
+    st = get_kernel(ctx, op, cfg, g.zbc, zuni, &k);
+    if (st) return st;
+    if (!miss) ctx->cache_hits++;
+
+    CUresult r;
+    if (cfg.family == 0) {
         long long nb = a.nbx * a.nby * a.nbz;
         if (nb > 0x7fffffffLL) return fail(KL_ERR_UNSUPPORTED, "grid too large");
         void *params[] = {&a};
         r = ctx->drv.LaunchKernel(k->fn, (unsigned)nb, 1, 1, cfg.bx, cfg.by, cfg.bz, 0,
                                   (CUstream)s, params, nullptr);
     } else {
-        ZGeom z = zmarch_geometry(op, cfg);
-        CUtensorMap maps[4];
-        const void *fp[4] = {f.u, f.v, f.w, op.diff == 2 ? f.nu : f.u};
-        for (int q = 0; q < 4; ++q) {
-            st = get_tmap(ctx, op, g, z, fp[q], &maps[q]);
-            if (st) return st;
-        }
-        a.kchunk = cfg.kc;
-        unsigned gxn = (unsigned)((g.nx + z.txs - 1) / z.txs);
-        unsigned gyn = (unsigned)((g.ny + z.tys - 1) / z.tys);
-        unsigned gzn = (unsigned)((g.nz + cfg.kc - 1) / cfg.kc);
-        if (gyn > 65535 || gzn > 65535) return fail(KL_ERR_UNSUPPORTED, "grid too large");
+        if (a.nby > 65535 || a.nbz > 65535) return fail(KL_ERR_UNSUPPORTED, "grid too large");
         void *params[] = {&a, &maps[0], &maps[1], &maps[2], &maps[3]};
-        r = ctx->drv.LaunchKernel(k->fn, gxn, gyn, gzn, cfg.mbx, cfg.mby, 1, (unsigned)k->smem,
-                                  (CUstream)s, params, nullptr);
+        r = ctx->drv.LaunchKernel(k->fn, (unsigned)a.nbx, (unsigned)a.nby, (unsigned)a.nbz,
+                                  cfg.mbx, cfg.mby, 1, (unsigned)k->smem, (CUstream)s, params,
+                                  nullptr);
     }
     if (r != CUDA_SUCCESS) return cu_fail(r, "cuLaunchKernel");
-    if (miss) {
-        ctx->t_launch_ms += ms_since(t0);
-    }
+    if (miss) ctx->t_launch_ms += ms_since(t0);
     ctx->launches++;
     ctx->last_config = config_string(cfg);
+    return KL_OK;
+}
+
+kl_status select_config(kl_ctx *ctx, const kl_op &op, const kl_grid &g, Config *cfg)
+{
+    char key[160];
+    snprintf(key, sizeof key, "%d/%d/%d/%d/%d/%d/%d/%d", op.adv, op.diff, op.dtype,
+             op.accumulate, g.zbc, g.nx, g.ny, g.nz);
+    auto it = ctx->selection.find(key);
+    std::string text;
+    if (it != ctx->selection.end()) {
+        text = it->second;
+    } else {
+        auto t0 = std::chrono::steady_clock::now();
+        std::vector<WisdomRecord> recs;
+        std::string err;
+        int rule = 5;
+        text = "default";
+        if (!ctx->wisdom_dir.empty()) {
+            std::string path = ctx->wisdom_dir + "/" + wisdom_file_name(op);
+            if (wisdom_read(path, &recs, &err))
+                rule = wisdom_select(recs, ctx->name, ctx->cc_major, ctx->cc_minor, g.zbc, g.nx,
+                                     g.ny, g.nz, &text);
+            else
+                ctx->last_rule_text = err;
+        }
+        // a record whose configuration is invalid here falls back to the default
+        Config c;
+        if (!config_parse(text, &c, &err) || !config_check(op, c, &err) ||
+            !config_fits(op, c, g, nullptr, &err)) {
+            ctx->last_rule_text = "wisdom config rejected (" + err + "); default used";
+            text = "default";
+            rule = 5;
+        }
+        ctx->selection[key] = text;
+        ctx->selection_rule[key] = rule;
+        ctx->t_wisdom_ms += ms_since(t0);
+    }
+    std::string err;
+    if (!config_parse(text, cfg, &err)) return fail(KL_ERR_WISDOM_PARSE, err);
     return KL_OK;
 }
 
@@ -521,45 +571,6 @@ kl_status kl_fill_ghosts(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, void *
     return KL_OK;
 }
 
-static kl_status select_config(kl_ctx *ctx, const kl_op &op, const kl_grid &g, Config *cfg)
-{
-    char key[160];
-    snprintf(key, sizeof key, "%d/%d/%d/%d/%d/%d/%d/%d", op.adv, op.diff, op.dtype,
-             op.accumulate, g.zbc, g.nx, g.ny, g.nz);
-    auto it = ctx->selection.find(key);
-    std::string text;
-    if (it != ctx->selection.end()) {
-        text = it->second;
-    } else {
-        auto t0 = std::chrono::steady_clock::now();
-        std::vector<WisdomRecord> recs;
-        std::string err;
-        int rule = 5;
-        text = "default";
-        if (!ctx->wisdom_dir.empty()) {
-            std::string path = ctx->wisdom_dir + "/" + wisdom_file_name(op);
-            if (wisdom_read(path, &recs, &err))
-                rule = wisdom_select(recs, ctx->name, ctx->cc_major, ctx->cc_minor, g.zbc, g.nx,
-                                     g.ny, g.nz, &text);
-            else
-                ctx->last_rule_text = err;
-        }
-        // a record whose configuration is invalid here falls back to the default
-        Config c;
-        if (!config_parse(text, &c, &err) || !config_check(op, c, &err) ||
-            !config_fits(op, c, g, nullptr, &err)) {
-            ctx->last_rule_text = "wisdom config rejected (" + err + "); default used";
-            text = "default";
-            rule = 5;
-        }
-        ctx->selection[key] = text;
-        ctx->selection_rule[key] = rule;
-        ctx->t_wisdom_ms += ms_since(t0);
-    }
-    std::string err;
-    if (!config_parse(text, cfg, &err)) return fail(KL_ERR_WISDOM_PARSE, err);
-    return KL_OK;
-}
 
 kl_status kl_capture_if_requested(kl_ctx *ctx, const kl_op *op, const kl_grid *grid,
                                   const kl_fields *fields, void *stream);
@@ -643,11 +654,12 @@ kl_status kl_stats(kl_ctx *ctx, char *buf, size_t n)
                      "{\"device\":\"%s\",\"cc\":\"%d.%d\",\"sms\":%d,\"launches\":%lld,"
                      "\"cache_hits\":%lld,\"cache_misses\":%lld,\"modules\":%zu,"
                      "\"stage_ms\":{\"wisdom\":%.3f,\"nvrtc\":%.3f,\"module_load\":%.3f,"
-                     "\"launch\":%.3f},\"last_config\":\"%s\",\"rules\":{%s},\"note\":\"%s\"}",
+                     "\"launch\":%.3f},\"last_config\":\"%s\",\"rules\":{%s},\"note\":\"%s\","
+                     "\"tables\":%zu}",
                      ctx->name.c_str(), ctx->cc_major, ctx->cc_minor, ctx->nsm, ctx->launches,
                      ctx->cache_hits, ctx->cache_misses, ctx->kernels.size(), ctx->t_wisdom_ms,
                      ctx->t_nvrtc_ms, ctx->t_load_ms, ctx->t_launch_ms, ctx->last_config.c_str(),
-                     rules.c_str(), ctx->last_rule_text.c_str());
+                     rules.c_str(), ctx->last_rule_text.c_str(), ctx->tables.size());
     if (m < 0 || (size_t)m >= n) return fail(KL_ERR_INVALID_ARG, "stats buffer too small");
     return KL_OK;
 }
@@ -698,11 +710,14 @@ kl_status kl_compile_only(const kl_op *op, const char *config, int32_t zbc, int3
     kl_status st = check_op(op);
     if (st) return st;
     Config c;
-    std::string err;
-    if (!config || !config_parse(config, &c, &err) || !config_check(*op, c, &err))
+    std::string err, text = config ? config : "";
+    bool batch = text.rfind("batch+", 0) == 0;     // "batch+<config>": the batched variant
+    if (batch) text = text.substr(6);
+    if (!config || !config_parse(text, &c, &err) || !config_check(*op, c, &err))
         return fail(KL_ERR_INVALID_ARG, "configuration: " + err);
     Compiled out;
-    st = nvrtc_compile(compile_defines(*op, c, zbc, zuni), true, &out);
+    st = nvrtc_compile(compile_defines(*op, c, zbc, zuni) + (batch ? " -DKL_BATCH=1" : ""), true,
+                       &out);
     if (log && n) {
         std::string s = st ? g_last_error : out.log;
         size_t m = std::min(n - 1, s.size());

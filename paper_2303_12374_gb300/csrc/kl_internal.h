@@ -172,7 +172,13 @@ namespace kl {
 kl_status launch_config(kl_ctx *ctx, const kl_op &op, const Config &cfg, const kl_grid &g,
                         const kl_fields &f, cudaStream_t s);
 kl_status get_kernel(kl_ctx *ctx, const kl_op &op, const Config &cfg, int zbc, int zuni,
-                     Kernel **out);
+                     Kernel **out, bool batch = false);
+// kernel arguments and TMA descriptors of one launch (validated)
+kl_status make_kargs(kl_ctx *ctx, const kl_op &op, const Config &cfg, const kl_grid &g,
+                     const kl_fields &f, KArgs *a, CUtensorMap maps[4]);
+kl_status select_config(kl_ctx *ctx, const kl_op &op, const kl_grid &g, Config *cfg);
+kl_status check_op(const kl_op *op);
+kl_status check_fields(const kl_op &op, const kl_fields *f);
 kl_status get_profile(kl_ctx *ctx, const kl_grid &g, Profile **out);
 // can configuration cfg run on this grid's memory layout and pointers?
 bool config_fits(const kl_op &op, const Config &cfg, const kl_grid &g, const kl_fields *f,

@@ -34,6 +34,9 @@
 #ifndef KL_DTYPE
 #error "KL_DTYPE must be defined"
 #endif
+#ifndef KL_BATCH
+#define KL_BATCH 0    // 1: one launch over many grids through a device tile table
+#endif
 
 typedef unsigned short kl_u16;
 
@@ -396,11 +399,10 @@ __device__ __forceinline__ void kl_direct_tile(const kl_args &a, const kl_coef &
     }
 }
 
-extern "C" __global__ void __launch_bounds__(KL_BX * KL_BY * KL_BZ, KL_MINB)
-kl_tendency(const kl_args a)
+__device__ __forceinline__ void kl_direct_block(const kl_args &a, long long b)
 {
     // unravel the 1D block index; the first letter of the order varies fastest
-    long long b = blockIdx.x, bx, by, bz;
+    long long bx, by, bz;
     const long long nbx = a.nbx, nby = a.nby, nbz = a.nbz;
     (void)nbx; (void)nby; (void)nbz;
 #if KL_PERM == 0
@@ -428,6 +430,23 @@ kl_tendency(const kl_args a)
     else
         kl_direct_tile<false>(a, K, i0, j0, k0);
 }
+
+#if KL_BATCH
+// many grids in one launch: block b runs block blocks[b].y of grid blocks[b].x
+extern "C" __global__ void __launch_bounds__(KL_BX * KL_BY * KL_BZ, KL_MINB)
+kl_tendency(const kl_args *argv, const int4 *blocks)
+{
+    const int4 d = blocks[blockIdx.x];
+    const kl_args a = argv[d.x];
+    kl_direct_block(a, d.y);
+}
+#else
+extern "C" __global__ void __launch_bounds__(KL_BX * KL_BY * KL_BZ, KL_MINB)
+kl_tendency(const kl_args a)
+{
+    kl_direct_block(a, blockIdx.x);
+}
+#endif
 #endif  // KL_FAMILY == 0
 
 #if KL_FAMILY >= 1
@@ -504,6 +523,14 @@ __device__ __forceinline__ bool kl_mbar_wait(unsigned bar, unsigned parity)
     return false;
 }
 
+// a descriptor read from global memory (batched launches) is ordered after
+// the host's copy of it for the tensor-map proxy by this fence
+__device__ __forceinline__ void kl_tmap_acquire(const kl_tmap *m)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;"
+                 ::"l"((unsigned long long)m) : "memory");
+}
+
 __device__ __forceinline__ void kl_tma_load3(unsigned dst, const kl_tmap *map, int x, int y, int z,
                                              unsigned bar)
 {
@@ -537,22 +564,19 @@ struct kl_acc_smem {
     template <int a, int b, int c> __device__ __forceinline__ C N() const { return at<a, b, c>(3); }
 };
 
-extern "C" __global__ void __launch_bounds__(KL_MBX * KL_MBY, KL_MMINB)
-kl_tendency(const kl_args a, const __grid_constant__ kl_tmap tm_u,
-            const __grid_constant__ kl_tmap tm_v, const __grid_constant__ kl_tmap tm_w,
-            const __grid_constant__ kl_tmap tm_n)
+__device__ __forceinline__ void kl_zmarch_body(const kl_args &a, const kl_tmap *const *maps,
+                                               int bxi, int byi, int bzi)
 {
     extern __shared__ unsigned char kl_smem_raw[];
     unsigned char *ring = (unsigned char *)(((unsigned long long)kl_smem_raw + 127) & ~127ull);
     unsigned long long *bars = (unsigned long long *)(ring + KL_NS * KL_SLOT_BYTES);
     const int tid = threadIdx.x + threadIdx.y * KL_MBX;
     const int nx = (int)a.nx, ny = (int)a.ny, nz = (int)a.nz;
-    const int kb = blockIdx.z * (int)a.kchunk;
+    const int kb = bzi * (int)a.kchunk;
     const int ke = min(kb + (int)a.kchunk, nz);
-    const int tx0 = blockIdx.x * KL_TXS, ty0 = blockIdx.y * KL_TYS;
+    const int tx0 = bxi * KL_TXS, ty0 = byi * KL_TYS;
     const int gx = (int)a.tile_x0 + tx0 - KL_LPAD, gy = (int)a.tile_y0 + ty0 - KL_H;
     const int gz0 = (int)a.tile_z0;
-    const kl_tmap *maps[4] = {&tm_u, &tm_v, &tm_w, &tm_n};
 
     if (tid == 0) {
         for (int s = 0; s < KL_NS; ++s) kl_mbar_init(kl_smem_addr(&bars[s]), 1);
@@ -651,6 +675,31 @@ kl_tendency(const kl_args a, const __grid_constant__ kl_tmap tm_u,
         __syncthreads();
     }
 }
+
+#if KL_BATCH
+// many grids in one launch: block b runs tile (y, z, w) of grid x of blocks[b];
+// TMA descriptors of grid g at maps[4g .. 4g+3] (global memory, 64-B aligned)
+extern "C" __global__ void __launch_bounds__(KL_MBX * KL_MBY, KL_MMINB)
+kl_tendency(const kl_args *argv, const int4 *blocks, const kl_tmap *tmaps)
+{
+    const int4 d = blocks[blockIdx.x];
+    const kl_args a = argv[d.x];
+    const kl_tmap *maps[4] = {&tmaps[4 * d.x], &tmaps[4 * d.x + 1], &tmaps[4 * d.x + 2],
+                              &tmaps[4 * d.x + 3]};
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        for (int f = 0; f < KL_NF; ++f) kl_tmap_acquire(maps[f]);
+    kl_zmarch_body(a, maps, d.y, d.z, d.w);
+}
+#else
+extern "C" __global__ void __launch_bounds__(KL_MBX * KL_MBY, KL_MMINB)
+kl_tendency(const kl_args a, const __grid_constant__ kl_tmap tm_u,
+            const __grid_constant__ kl_tmap tm_v, const __grid_constant__ kl_tmap tm_w,
+            const __grid_constant__ kl_tmap tm_n)
+{
+    const kl_tmap *maps[4] = {&tm_u, &tm_v, &tm_w, &tm_n};
+    kl_zmarch_body(a, maps, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+#endif
 #endif  // KL_FAMILY == 1
 
 #if KL_FAMILY == 2
@@ -812,10 +861,8 @@ __device__ __forceinline__ V kl_pr(const char *const *pl, int lx, int row)
     return vld((const T *)(pl[DK + KL_R] + F * KL_PLANE_BYTES + KL_OFF(lx + DX, row)));
 }
 
-extern "C" __global__ void __launch_bounds__(32 * KL_MBY, KL_MMINB)
-kl_tendency(const kl_args a, const __grid_constant__ kl_tmap tm_u,
-            const __grid_constant__ kl_tmap tm_v, const __grid_constant__ kl_tmap tm_w,
-            const __grid_constant__ kl_tmap tm_n)
+__device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *const *maps,
+                                              int bxi, int byi, int bzi)
 {
     static_assert(KL_MBX == 32 && KL_MPX == 2, "zpack tiles are 64 columns wide");
     static_assert(3 * KL_MPY <= 32, "side pass needs 3 x rows <= 32 lanes");
@@ -829,13 +876,11 @@ kl_tendency(const kl_args a, const __grid_constant__ kl_tmap tm_u,
     const int lane = threadIdx.x, warp = threadIdx.y;
     const int tid = lane + 32 * warp;
     const int nx = (int)a.nx, ny = (int)a.ny, nz = (int)a.nz;
-    const int kb = blockIdx.z * (int)a.kchunk;
+    const int kb = bzi * (int)a.kchunk;
     const int ke = min(kb + (int)a.kchunk, nz);
-    const int tx0 = blockIdx.x * 64, ty0 = blockIdx.y * KL_TYS;
+    const int tx0 = bxi * 64, ty0 = byi * KL_TYS;
     const int gx = (int)a.tile_x0 + tx0 - KL_LPAD, gy = (int)a.tile_y0 + ty0 - KL_H;
     const int gz0 = (int)a.tile_z0;
-    const kl_tmap *maps[3] = {&tm_u, &tm_v, &tm_w};
-    (void)tm_n;
 
     if (tid == 0) {
         for (int s = 0; s < KL_NS; ++s) kl_mbar_init(kl_smem_addr(&bars[s]), 1);
@@ -1057,4 +1102,27 @@ kl_tendency(const kl_args a, const __grid_constant__ kl_tmap tm_u,
         __syncthreads();
     }
 }
+
+#if KL_BATCH
+extern "C" __global__ void __launch_bounds__(32 * KL_MBY, KL_MMINB)
+kl_tendency(const kl_args *argv, const int4 *blocks, const kl_tmap *tmaps)
+{
+    const int4 d = blocks[blockIdx.x];
+    const kl_args a = argv[d.x];
+    const kl_tmap *maps[3] = {&tmaps[4 * d.x], &tmaps[4 * d.x + 1], &tmaps[4 * d.x + 2]};
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        for (int f = 0; f < 3; ++f) kl_tmap_acquire(maps[f]);
+    kl_zpack_body(a, maps, d.y, d.z, d.w);
+}
+#else
+extern "C" __global__ void __launch_bounds__(32 * KL_MBY, KL_MMINB)
+kl_tendency(const kl_args a, const __grid_constant__ kl_tmap tm_u,
+            const __grid_constant__ kl_tmap tm_v, const __grid_constant__ kl_tmap tm_w,
+            const __grid_constant__ kl_tmap tm_n)
+{
+    (void)tm_n;
+    const kl_tmap *maps[3] = {&tm_u, &tm_v, &tm_w};
+    kl_zpack_body(a, maps, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+#endif
 #endif  // KL_FAMILY == 2

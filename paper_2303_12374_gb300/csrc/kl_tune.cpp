@@ -823,8 +823,118 @@ kl_status kl_tune(kl_ctx *ctx, const char *capture_path, const char *opts, const
 kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_grid *grids,
                             const kl_fields *fields, void *stream)
 {
-    (void)ctx; (void)op; (void)n; (void)grids; (void)fields; (void)stream;
-    return fail(KL_ERR_UNSUPPORTED, "kl_launch_batched: not built yet");
+    if (!ctx || !grids || !fields) return fail(KL_ERR_INVALID_ARG, "NULL argument");
+    if (n < 1) return fail(KL_ERR_INVALID_ARG, "batch needs at least one grid");
+    kl_status st = check_op(op);
+    if (st) return st;
+    // per grid: the configuration of its nearest tuned size (Sec. 4.5 rules)
+    struct Item {
+        Config cfg;
+        KArgs a;
+        CUtensorMap maps[4];
+    };
+    std::vector<Item> items((size_t)n);
+    std::map<std::string, std::vector<int>> groups;       // compile key -> grids
+    for (int i = 0; i < n; ++i) {
+        st = check_fields(*op, &fields[i]);
+        if (st) return fail(st, "grid " + std::to_string(i) + ": " + kl_last_error());
+        st = check_grid(&grids[i], halo_of(*op), nullptr);
+        if (st) return fail(st, "grid " + std::to_string(i) + ": " + kl_last_error());
+        Config cfg;
+        st = select_config(ctx, *op, grids[i], &cfg);
+        if (st) return st;
+        std::string err;
+        if (!config_fits(*op, cfg, grids[i], &fields[i], &err)) cfg = Config();
+        items[i].cfg = cfg;
+        st = make_kargs(ctx, *op, cfg, grids[i], fields[i], &items[i].a, items[i].maps);
+        if (st) return fail(st, "grid " + std::to_string(i) + ": " + kl_last_error());
+        int zuni = grids[i].zh ? 0 : 1;
+        groups[compile_defines(*op, cfg, grids[i].zbc, zuni)].push_back(i);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    for (auto &gp : groups) {
+        const std::vector<int> &ids = gp.second;
+        const Config &cfg = items[ids[0]].cfg;
+        const kl_grid &g0 = grids[ids[0]];
+        // host image of the table: [descriptors | argument blocks | tile list]
+        std::vector<int> tiles;                 // 4 ints per block
+        for (size_t q = 0; q < ids.size(); ++q) {
+            const KArgs &a = items[ids[q]].a;
+            if (cfg.family == 0) {
+                long long nb = a.nbx * a.nby * a.nbz;
+                for (long long b = 0; b < nb; ++b) {
+                    tiles.push_back((int)q);
+                    tiles.push_back((int)b);
+                    tiles.push_back(0);
+                    tiles.push_back(0);
+                }
+            } else {
+                for (int bz = 0; bz < (int)a.nbz; ++bz)
+                    for (int by = 0; by < (int)a.nby; ++by)
+                        for (int bx = 0; bx < (int)a.nbx; ++bx) {
+                            tiles.push_back((int)q);
+                            tiles.push_back(bx);
+                            tiles.push_back(by);
+                            tiles.push_back(bz);
+                        }
+            }
+        }
+        size_t nblocks = tiles.size() / 4;
+        if (nblocks == 0 || nblocks > 0x7fffffffULL) return fail(KL_ERR_UNSUPPORTED, "batch too large");
+        size_t off_maps = 0, sz_maps = ids.size() * 4 * sizeof(CUtensorMap);
+        size_t off_args = (sz_maps + 63) / 64 * 64, sz_args = ids.size() * sizeof(KArgs);
+        size_t off_tiles = (off_args + sz_args + 63) / 64 * 64;
+        size_t total = off_tiles + tiles.size() * sizeof(int);
+        std::vector<char> img(total, 0);
+        for (size_t q = 0; q < ids.size(); ++q) {
+            memcpy(img.data() + off_maps + q * 4 * sizeof(CUtensorMap), items[ids[q]].maps,
+                   4 * sizeof(CUtensorMap));
+            memcpy(img.data() + off_args + q * sizeof(KArgs), &items[ids[q]].a, sizeof(KArgs));
+        }
+        memcpy(img.data() + off_tiles, tiles.data(), tiles.size() * sizeof(int));
+        // cached per table content: a time loop re-launching the same batch
+        // uploads its table once
+        uint64_t h = 1469598103934665603ull;
+        for (char c : gp.first) h = (h ^ (unsigned char)c) * 1099511628211ull;
+        for (char c : img) h = (h ^ (unsigned char)c) * 1099511628211ull;
+        std::string tkey = "batch:" + std::to_string(h) + ":" + std::to_string(total);
+        auto it = ctx->tables.find(tkey);
+        void *dev = nullptr;
+        if (it != ctx->tables.end()) {
+            dev = it->second.first;
+        } else {
+            if (ctx->tables.size() > 64) {              // bound the cache
+                cudaStreamSynchronize(s);
+                for (auto &t : ctx->tables) cudaFree(t.second.first);
+                ctx->tables.clear();
+            }
+            if (cudaMalloc(&dev, total) != cudaSuccess) return fail(KL_ERR_OOM, "batch table allocation");
+            cudaError_t e = cudaMemcpy(dev, img.data(), total, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                cudaFree(dev);
+                return cuda_fail(e, "batch table upload");
+            }
+            ctx->tables[tkey] = {dev, total};
+        }
+        Kernel *k = nullptr;
+        st = get_kernel(ctx, *op, cfg, g0.zbc, g0.zh ? 0 : 1, &k, true);
+        if (st) return st;
+        char *base = (char *)dev;
+        void *argv = base + off_args, *tl = base + off_tiles, *tm = base + off_maps;
+        CUresult r;
+        if (cfg.family == 0) {
+            void *params[] = {&argv, &tl};
+            r = ctx->drv.LaunchKernel(k->fn, (unsigned)nblocks, 1, 1, cfg.bx, cfg.by, cfg.bz, 0,
+                                      (CUstream)s, params, nullptr);
+        } else {
+            void *params[] = {&argv, &tl, &tm};
+            r = ctx->drv.LaunchKernel(k->fn, (unsigned)nblocks, 1, 1, cfg.mbx, cfg.mby, 1,
+                                      (unsigned)k->smem, (CUstream)s, params, nullptr);
+        }
+        if (r != CUDA_SUCCESS) return cu_fail(r, "cuLaunchKernel (batch)");
+        ctx->launches++;
+    }
+    return KL_OK;
 }
 
 }  // extern "C"
