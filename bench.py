@@ -195,6 +195,116 @@ def cpu_baseline(seconds_target):
                       f"single thread, {dt:.1f} s incl. ghost padding)"}, dt
 
 
+def precision_sweep(ctx, f, device, stream, reps):
+    """Tuned and default kernel time per storage type on the same 256^3 fields."""
+    import torch
+    from paper_2303_12374_gb300 import kl
+    from paper_2303_12374_gb300.problem import Problem
+    out = {}
+    for name in ("f64", "f32", "bf16", "f16"):
+        p = Problem(NX, NY, NZ, g=G, dtype=name, walls=True, dz=1.0 / NZ, nu=NU, device=device)
+        ins = [p.upload(f[k]) for k in ("u", "v", "w")]
+        outs = [p.empty() for _ in range(3)]
+        op = kl.Op(5, 1, p.dtype, 0)
+        es = {0: 8, 1: 4, 2: 2, 3: 2}[p.dtype]
+        row = {"bytes_per_point": 6 * es}
+        n = reps if name != "f64" else max(3, reps // 20)
+        for label, cfg in (("tuned", None), ("default", "default")):
+            _, k_ms = time_steps(ctx, p, ins, outs, op, cfg, n, 2, stream)
+            row[label] = {"kernel_us": k_ms * 1e3, "gpts": NX * NY * NZ / (k_ms * 1e-3) / 1e9,
+                          "hbm_gbs": 6 * es * NX * NY * NZ / (k_ms * 1e-3) / 1e9}
+            if cfg is None:
+                row[label]["config"] = json.loads(kl.kl_stats(ctx))["last_config"]
+        row["speedup"] = row["default"]["kernel_us"] / row["tuned"]["kernel_us"]
+        out[name] = row
+        del ins, outs
+        torch.cuda.empty_cache()
+    return out
+
+
+def batched_run(ctx, device, stream, reps=20):
+    """64 uneven grids: one batched call (tuned size classes) vs 64 default launches."""
+    import torch
+    from paper_2303_12374_gb300 import kl, synth
+    from paper_2303_12374_gb300.problem import Problem
+    spec = synth.WORKLOADS["batch64_uneven"]
+    sizes = synth.batch_sizes(synth.seed_of(spec["index"]), spec["count"])
+    probs = []
+    for q, (nx, ny, nz) in enumerate(sizes):
+        f = synth.velocity_fields(nx, ny, nz, seed=synth.seed_of(spec["index"]) * 1000 + q,
+                                  walls=True)
+        p = Problem(nx, ny, nz, g=G, dtype="f32", walls=True, dz=1.0 / nz, nu=NU, device=device)
+        bufs = [p.upload(f[k]) for k in ("u", "v", "w")]
+        outs = [p.empty() for _ in range(3)]
+        fl = kl.Fields(*[b.data_ptr() for b in bufs], None, *[o.data_ptr() for o in outs])
+        probs.append((p, bufs, outs, fl))
+    pts = sum(nx * ny * nz for nx, ny, nz in sizes)
+    op = kl.Op(5, 1, 1, 0)
+    grids = [pr[0].grid for pr in probs]
+    fields = [pr[3] for pr in probs]
+    sp = stream.cuda_stream
+    with torch.cuda.stream(stream):
+        for p, bufs, outs, fl in probs:
+            kl.kl_fill_ghosts(ctx, p.dtype, p.grid, *[b.data_ptr() for b in bufs], None, sp)
+
+        def batched():
+            kl.kl_launch_batched(ctx, op, grids, fields, sp)
+
+        def separate():
+            for p, bufs, outs, fl in probs:
+                kl.kl_launch_with_config(ctx, op, "default", p.grid, fl, sp)
+
+        res = {}
+        for label, fn in (("batched_tuned", batched), ("separate_default", separate)):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / reps
+            res[label] = {"ms": ms, "gpts": pts / (ms * 1e-3) / 1e9,
+                          "hbm_gbs": 24 * pts / (ms * 1e-3) / 1e9}
+    res["grids"] = len(sizes)
+    res["points"] = pts
+    res["speedup"] = res["separate_default"]["ms"] / res["batched_tuned"]["ms"]
+    return res
+
+
+def launch_overhead(local, wisdom, device, calls=1000):
+    """Sec. 5.6: the four stages of a first launch and the cost of a cached launch."""
+    import torch
+    from paper_2303_12374_gb300 import kl
+    from paper_2303_12374_gb300.problem import Problem
+    ctx = kl.kl_create(local, wisdom)
+    try:
+        n = 32
+        p = Problem(n, n, n, g=G, dtype="f32", walls=True, dz=1.0 / n, nu=NU, device=device)
+        bufs = [p.empty() for _ in range(3)]
+        outs = [p.empty() for _ in range(3)]
+        fl = kl.Fields(*[b.data_ptr() for b in bufs], None, *[o.data_ptr() for o in outs])
+        op = kl.Op(5, 1, p.dtype, 0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        kl.kl_launch(ctx, op, p.grid, fl)
+        first_ms = (time.perf_counter() - t0) * 1e3
+        stages = json.loads(kl.kl_stats(ctx))["stage_ms"]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(calls):
+            kl.kl_launch(ctx, op, p.grid, fl)
+        host_us = (time.perf_counter() - t0) / calls * 1e6
+        torch.cuda.synchronize()
+        return {"first_launch_ms": first_ms, "stage_ms": stages,
+                "cached_launch_host_us": host_us,
+                "note": "host time per kl_launch call through the ctypes binding, 32^3 grid"}
+    finally:
+        kl.kl_destroy(ctx)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", 0))
     if rank != 0:
@@ -284,16 +394,9 @@ def main():
             "kernel_hbm_gbs": alg_bytes / (d_kern * 1e-3) / 1e9}
         extras["tuned_config"] = {"config": tuned_cfg, "kernel_us": kern_ms * 1e3,
                                   "speedup_vs_default": d_kern / kern_ms}
-        if args.dtype == "f32":
-            p64, _, ins64, outs64 = setup("f64", device)
-            op64 = kl.Op(5, 1, 0, 0)
-            k3 = max(10, args.steps // 50)
-            t64, k64 = time_steps(ctx, p64, ins64, outs64, op64, None, k3, 3, stream)
-            extras["f64_tuned"] = {"config": json.loads(kl.kl_stats(ctx))["last_config"],
-                                   "value": pts * k3 / (t64 * 1e-3) / 1e9,
-                                   "kernel_us": k64 * 1e3,
-                                   "kernel_hbm_gbs": 48 * pts / (k64 * 1e-3) / 1e9}
-            del ins64, outs64
+        extras["precision"] = precision_sweep(ctx, f, device, stream, max(20, args.steps // 20))
+        extras["batched"] = batched_run(ctx, device, stream)
+        extras["launch_overhead"] = launch_overhead(local, wisdom, device)
 
     # --- end to end through the public API with pinned host buffers
     e2e = None

@@ -410,6 +410,7 @@ kl_status launch_config(kl_ctx *ctx, const kl_op &op, const Config &cfg, const k
     if (!miss) ctx->cache_hits++;
 
     CUresult r;
+    auto t_launch = std::chrono::steady_clock::now();
     if (cfg.family == 0) {
         long long nb = a.nbx * a.nby * a.nbz;
         if (nb > 0x7fffffffLL) return fail(KL_ERR_UNSUPPORTED, "grid too large");
@@ -424,7 +425,8 @@ kl_status launch_config(kl_ctx *ctx, const kl_op &op, const Config &cfg, const k
                                   nullptr);
     }
     if (r != CUDA_SUCCESS) return cu_fail(r, "cuLaunchKernel");
-    if (miss) ctx->t_launch_ms += ms_since(t0);
+    if (miss) ctx->t_launch_ms += ms_since(t_launch);
+    (void)t0;
     ctx->launches++;
     ctx->last_config = config_string(cfg);
     return KL_OK;

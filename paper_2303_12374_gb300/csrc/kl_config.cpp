@@ -30,8 +30,8 @@ std::string config_string(const Config &c)
         snprintf(b, sizeof b, "zmarch:bx=%d,by=%d,px=%d,py=%d,kc=%d,ns=%d,minb=%d", c.mbx, c.mby,
                  c.mpx, c.mpy, c.kc, c.ns, c.mminb);
     } else {
-        snprintf(b, sizeof b, "zpack:w=%d,ly=%d,kc=%d,ns=%d,minb=%d", c.mby, c.mpy, c.kc, c.ns,
-                 c.mminb);
+        snprintf(b, sizeof b, "zpack:w=%d,ly=%d,kc=%d,ns=%d,minb=%d,yx=%d,pk=%d", c.mby, c.mpy,
+                 c.kc, c.ns, c.mminb, c.yx, c.pk);
     }
     return b;
 }
@@ -104,6 +104,8 @@ bool config_parse(const std::string &text, Config *c, std::string *err)
             else if (k == "minb") dst = &c->minb;
         } else if (c->family == 2) {
             if (k == "w") dst = &c->mby; else if (k == "ly") dst = &c->mpy;
+            else if (k == "yx") dst = &c->yx;
+            else if (k == "pk") dst = &c->pk;
             else if (k == "kc") dst = &c->kc; else if (k == "ns") dst = &c->ns;
             else if (k == "minb") dst = &c->mminb;
         } else {
@@ -150,7 +152,11 @@ size_t zmarch_smem_bytes(const kl_op &op, const Config &c)
 {
     ZGeom z = zmarch_geometry(op, c);
     // ring + 128 B of alignment slack + one 8-byte mbarrier per slot
-    return z.plane_bytes * z.nf * c.ns + 256;
+    size_t bytes = z.plane_bytes * z.nf * c.ns + 256;
+    // zpack y-face exchange: 3 fields x warps x 32 lanes x one packed pair
+    if (c.family == 2 && c.yx)
+        bytes += 3 * (size_t)c.mby * 32 * (op.dtype == KL_F64 ? 16 : 8) + 16;
+    return bytes;
 }
 
 static bool in(int v, std::initializer_list<int> set)
@@ -199,6 +205,10 @@ bool config_check(const kl_op &op, const Config &c, std::string *err)
             *err = "zpack parameter outside the space (w 1..16, ly 1..8)";
             return false;
         }
+        if (c.family == 2 && ((c.yx != 0 && c.yx != 1) || (c.pk != 0 && c.pk != 1))) {
+            *err = "yx and pk must be 0 or 1";
+            return false;
+        }
         if (c.family == 2 && op.diff == 2) {
             *err = "zpack supports diff = 0 or 1";
             return false;
@@ -245,7 +255,7 @@ int64_t space_size(int family)
 {
     if (family == 0) return 5LL * 5 * 5 * 27 * 8 * 8 * 6 * 6;
     if (family == 1) return 3LL * 5 * 3 * 3 * 7 * 4 * 4;
-    if (family == 2) return 5LL * 4 * 7 * 4 * 4;
+    if (family == 2) return 5LL * 4 * 7 * 4 * 4 * 2;
     return 0;
 }
 
@@ -278,6 +288,7 @@ bool space_config(int family, int64_t idx, Config *c)
         c->kc = kKC[take(7)];
         c->ns = kNS[take(4)];
         c->mminb = 1 + take(4);
+        c->yx = take(2);
     } else {
         c->mbx = kMBX[take(3)];
         c->mby = kMBY[take(5)];
@@ -492,8 +503,9 @@ std::string compile_defines(const kl_op &op, const Config &c, int zbc, int zuni)
     } else {
         snprintf(b + n, sizeof b - n,
                  " -DKL_MBX=%d -DKL_MBY=%d -DKL_MPX=%d -DKL_MPY=%d -DKL_KC=%d -DKL_NS=%d"
-                 " -DKL_MMINB=%d",
-                 c.mbx, c.mby, c.mpx, c.mpy, c.kc, c.ns, c.mminb);
+                 " -DKL_MMINB=%d -DKL_YX=%d -DKL_PK=%d",
+                 c.mbx, c.mby, c.mpx, c.mpy, c.kc, c.ns, c.mminb, c.family == 2 ? c.yx : 0,
+                 c.family == 2 ? c.pk : 1);
     }
     return b;
 }

@@ -37,6 +37,8 @@ struct Config {
     int kc = 32;               // z levels per CTA
     int ns = 8;                // plane ring slots (>= 7 + prefetch)
     int mminb = 1;             // min blocks per SM
+    int yx = 0;                // zpack: exchange y faces between warps (shared memory)
+    int pk = 1;                // zpack: packed f32x2 arithmetic (f32 compute)
 };
 
 std::string config_string(const Config &c);

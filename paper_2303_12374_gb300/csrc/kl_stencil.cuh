@@ -34,6 +34,12 @@
 #ifndef KL_DTYPE
 #error "KL_DTYPE must be defined"
 #endif
+#ifndef KL_PK
+#define KL_PK 1       // zpack: packed f32x2 arithmetic for f32 compute
+#endif
+#ifndef KL_YX
+#define KL_YX 0       // zpack: exchange y faces between warps through shared memory
+#endif
 #ifndef KL_BATCH
 #define KL_BATCH 0    // 1: one launch over many grids through a device tile table
 #endif
@@ -728,19 +734,39 @@ kl_tendency(const kl_args a, const __grid_constant__ kl_tmap tm_u,
 #error "zpack supports diff = 0 or 1"
 #endif
 
-#if KL_DTYPE == 0
-struct V { double lo, hi; };
-__device__ __forceinline__ V vmk(double a, double b) { V r; r.lo = a; r.hi = b; return r; }
-__device__ __forceinline__ double vlo(V a) { return a.lo; }
-__device__ __forceinline__ double vhi(V a) { return a.hi; }
+#if KL_DTYPE == 0 || KL_PK == 0
+// two independent scalars (f64, or f32 with packed arithmetic switched off)
+struct V { C lo, hi; };
+__device__ __forceinline__ V vmk(C a, C b) { V r; r.lo = a; r.hi = b; return r; }
+__device__ __forceinline__ C vlo(V a) { return a.lo; }
+__device__ __forceinline__ C vhi(V a) { return a.hi; }
 __device__ __forceinline__ V vadd(V a, V b) { return vmk(a.lo + b.lo, a.hi + b.hi); }
 __device__ __forceinline__ V vsub(V a, V b) { return vmk(a.lo - b.lo, a.hi - b.hi); }
 __device__ __forceinline__ V vmul(V a, V b) { return vmk(a.lo * b.lo, a.hi * b.hi); }
 __device__ __forceinline__ V vfma(V a, V b, V c) { return vmk(fma(a.lo, b.lo, c.lo), fma(a.hi, b.hi, c.hi)); }
 __device__ __forceinline__ V vabs(V a) { return vmk(fabs(a.lo), fabs(a.hi)); }
+#if KL_DTYPE == 0
 // aligned pair of consecutive elements at p (16-byte aligned)
 __device__ __forceinline__ V vld(const T *p) { double2 d = *(const double2 *)p; return vmk(d.x, d.y); }
 __device__ __forceinline__ void vst(T *p, V a) { *(double2 *)p = make_double2(a.lo, a.hi); }
+#elif KL_DTYPE == 1
+__device__ __forceinline__ V vld(const T *p) { float2 d = *(const float2 *)p; return vmk(d.x, d.y); }
+__device__ __forceinline__ void vst(T *p, V a) { *(float2 *)p = make_float2(a.lo, a.hi); }
+#else
+__device__ __forceinline__ V vld(const T *p)
+{
+    unsigned w = *(const unsigned *)p;
+    kl_u16 lo = (kl_u16)(w & 0xffffu), hi = (kl_u16)(w >> 16);
+    return vmk(lds(&lo), lds(&hi));
+}
+__device__ __forceinline__ void vst(T *p, V a)
+{
+    kl_u16 lo, hi;
+    st(&lo, a.lo);
+    st(&hi, a.hi);
+    *(unsigned *)p = (unsigned)lo | ((unsigned)hi << 16);
+}
+#endif
 __device__ __forceinline__ V vldg(const T *p) { return vld(p); }
 #else
 struct V { unsigned long long b; };
@@ -873,6 +899,10 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
     extern __shared__ unsigned char kl_smem_raw[];
     unsigned char *ring = (unsigned char *)(((unsigned long long)kl_smem_raw + 127) & ~127ull);
     unsigned long long *bars = (unsigned long long *)(ring + KL_NS * KL_SLOT_BYTES);
+#if KL_YX
+    // y-face exchange buffer after the barriers: [3 fields][warps][32 lanes]
+    V *xbuf = (V *)(((unsigned long long)(bars + KL_NS) + 15) & ~15ull);
+#endif
     const int lane = threadIdx.x, warp = threadIdx.y;
     const int tid = lane + 32 * warp;
     const int nx = (int)a.nx, ny = (int)a.ny, nz = (int)a.nz;
@@ -975,7 +1005,48 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
             extra = kl_sflux(us, a0, a1, a2, a3, a4, a5, kdx);
         }
 
-        // ---- y faces: bottom face of the first row; rows then roll upwards
+        // ---- y faces
+#if KL_YX
+        // every thread forms the bottom faces of its rows; the top face of
+        // its last row is the bottom face of the warp above, exchanged
+        // through shared memory (the last warp forms the tile's top face)
+        V fyb[KL_MPY][3], fyt_last[3];
+#pragma unroll
+        for (int r = 0; r < KL_MPY; ++r) {
+            const int yr = r0 + r;
+            fyb[r][0] = kl_vflux(K, vadd(vcross(KL_Q(1, 0, -2, yr), KL_Q(1, 0, 0, yr)), KL_Q(1, 0, 0, yr)),
+                                 KL_A5(KL_Q(0, 0, 0, yr - 3)), KL_A5(KL_Q(0, 0, 0, yr - 2)), KL_Q(0, 0, 0, yr - 1),
+                                 KL_Q(0, 0, 0, yr), KL_A5(KL_Q(0, 0, 0, yr + 1)), KL_A5(KL_Q(0, 0, 0, yr + 2)), vkdy);
+            fyb[r][1] = kl_vflux(K, vadd(KL_Q(1, 0, 0, yr - 1), KL_Q(1, 0, 0, yr)),
+                                 KL_A5(KL_Q(1, 0, 0, yr - 3)), KL_A5(KL_Q(1, 0, 0, yr - 2)), KL_Q(1, 0, 0, yr - 1),
+                                 KL_Q(1, 0, 0, yr), KL_A5(KL_Q(1, 0, 0, yr + 1)), KL_A5(KL_Q(1, 0, 0, yr + 2)), vkdy);
+            fyb[r][2] = kl_vflux(K, vadd(KL_Q(1, -1, 0, yr), KL_Q(1, 0, 0, yr)),
+                                 KL_A5(KL_Q(2, 0, 0, yr - 3)), KL_A5(KL_Q(2, 0, 0, yr - 2)), KL_Q(2, 0, 0, yr - 1),
+                                 KL_Q(2, 0, 0, yr), KL_A5(KL_Q(2, 0, 0, yr + 1)), KL_A5(KL_Q(2, 0, 0, yr + 2)), vkdy);
+        }
+#pragma unroll
+        for (int f = 0; f < 3; ++f) xbuf[(f * KL_MBY + warp) * 32 + lane] = fyb[0][f];
+        if (warp == KL_MBY - 1) {
+            const int yt = r0 + KL_MPY;
+            fyt_last[0] = kl_vflux(K, vadd(vcross(KL_Q(1, 0, -2, yt), KL_Q(1, 0, 0, yt)), KL_Q(1, 0, 0, yt)),
+                                   KL_A5(KL_Q(0, 0, 0, yt - 3)), KL_A5(KL_Q(0, 0, 0, yt - 2)), KL_Q(0, 0, 0, yt - 1),
+                                   KL_Q(0, 0, 0, yt), KL_A5(KL_Q(0, 0, 0, yt + 1)), KL_A5(KL_Q(0, 0, 0, yt + 2)), vkdy);
+            fyt_last[1] = kl_vflux(K, vadd(KL_Q(1, 0, 0, yt - 1), KL_Q(1, 0, 0, yt)),
+                                   KL_A5(KL_Q(1, 0, 0, yt - 3)), KL_A5(KL_Q(1, 0, 0, yt - 2)), KL_Q(1, 0, 0, yt - 1),
+                                   KL_Q(1, 0, 0, yt), KL_A5(KL_Q(1, 0, 0, yt + 1)), KL_A5(KL_Q(1, 0, 0, yt + 2)), vkdy);
+            fyt_last[2] = kl_vflux(K, vadd(KL_Q(1, -1, 0, yt), KL_Q(1, 0, 0, yt)),
+                                   KL_A5(KL_Q(2, 0, 0, yt - 3)), KL_A5(KL_Q(2, 0, 0, yt - 2)), KL_Q(2, 0, 0, yt - 1),
+                                   KL_Q(2, 0, 0, yt), KL_A5(KL_Q(2, 0, 0, yt + 1)), KL_A5(KL_Q(2, 0, 0, yt + 2)), vkdy);
+        } else {
+            fyt_last[0] = fyt_last[1] = fyt_last[2] = vsplat(C(0));
+        }
+        __syncthreads();
+        if (warp != KL_MBY - 1) {
+#pragma unroll
+            for (int f = 0; f < 3; ++f) fyt_last[f] = xbuf[(f * KL_MBY + warp + 1) * 32 + lane];
+        }
+        V fuy_b = fyb[0][0], fvy_b = fyb[0][1], fwy_b = fyb[0][2];
+#else
         V fuy_b, fvy_b, fwy_b;
         {
             const int yr = r0;
@@ -989,6 +1060,7 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
                              KL_A5(KL_Q(2, 0, 0, yr - 3)), KL_A5(KL_Q(2, 0, 0, yr - 2)), KL_Q(2, 0, 0, yr - 1),
                              KL_Q(2, 0, 0, yr), KL_A5(KL_Q(2, 0, 0, yr + 1)), KL_A5(KL_Q(2, 0, 0, yr + 2)), vkdy);
         }
+#endif
 
 #pragma unroll
         for (int r = 0; r < KL_MPY; ++r) {
@@ -1022,6 +1094,18 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
             V wr = vmk(vhi(fwx), lane == 31 ? ew : wr_lo);
 
             // ---- top y faces of this row
+#if KL_YX
+            V fuy_t, fvy_t, fwy_t;
+            if (r + 1 < KL_MPY) {
+                fuy_t = fyb[r + 1 < KL_MPY ? r + 1 : 0][0];
+                fvy_t = fyb[r + 1 < KL_MPY ? r + 1 : 0][1];
+                fwy_t = fyb[r + 1 < KL_MPY ? r + 1 : 0][2];
+            } else {
+                fuy_t = fyt_last[0];
+                fvy_t = fyt_last[1];
+                fwy_t = fyt_last[2];
+            }
+#else
             const int yt = yr + 1;
             V fuy_t = kl_vflux(K, vadd(vcross(KL_Q(1, 0, -2, yt), KL_Q(1, 0, 0, yt)), KL_Q(1, 0, 0, yt)),
                                KL_A5(KL_Q(0, 0, 0, yt - 3)), KL_A5(KL_Q(0, 0, 0, yt - 2)), KL_Q(0, 0, 0, yt - 1),
@@ -1032,6 +1116,7 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
             V fwy_t = kl_vflux(K, vadd(KL_Q(1, -1, 0, yt), KL_Q(1, 0, 0, yt)),
                                KL_A5(KL_Q(2, 0, 0, yt - 3)), KL_A5(KL_Q(2, 0, 0, yt - 2)), KL_Q(2, 0, 0, yt - 1),
                                KL_Q(2, 0, 0, yt), KL_A5(KL_Q(2, 0, 0, yt + 1)), KL_A5(KL_Q(2, 0, 0, yt + 2)), vkdy);
+#endif
 
             // ---- z faces: bottom carried, top formed here
             V fz_u = kl_vflux(K, vadd(vcross(KL_Q(2, 1, -2, yr), KL_Q(2, 1, 0, yr)), KL_Q(2, 1, 0, yr)),

@@ -450,7 +450,7 @@ static bool valid_for(const kl_op &op, const kl_grid &g, int family, int64_t idx
 static std::vector<int> radices(int family)
 {
     if (family == 0) return {5, 5, 5, 3, 3, 3, 2, 2, 2, 2, 2, 2, 6, 6};
-    if (family == 2) return {5, 4, 7, 4, 4};
+    if (family == 2) return {5, 4, 7, 4, 4, 2};
     return {3, 5, 3, 3, 7, 4, 4};
 }
 
@@ -623,13 +623,13 @@ kl_status kl_tune(kl_ctx *ctx, const char *capture_path, const char *opts, const
                     {1, 2, 3, 4, 5, 6}};
         else if (c.family == 2)
             vals = {{1, 2, 4, 8, 16}, {1, 2, 4, 8}, {4, 8, 16, 32, 64, 128, 256}, {8, 9, 10, 12},
-                    {1, 2, 3, 4}};
+                    {1, 2, 3, 4}, {0, 1}};
         else
             vals = {{32, 64, 128}, {1, 2, 4, 8, 16}, {1, 2, 4}, {1, 2, 4}, {4, 8, 16, 32, 64, 128, 256},
                     {8, 9, 10, 12}, {1, 2, 3, 4}};
         std::vector<int> cur = c.family == 0
             ? std::vector<int>{c.bx, c.by, c.bz, c.tx, c.ty, c.tz, c.ux, c.uy, c.uz, c.cx, c.cy, c.cz, c.perm, c.minb}
-            : c.family == 2 ? std::vector<int>{c.mby, c.mpy, c.kc, c.ns, c.mminb}
+            : c.family == 2 ? std::vector<int>{c.mby, c.mpy, c.kc, c.ns, c.mminb, c.yx}
                             : std::vector<int>{c.mbx, c.mby, c.mpx, c.mpy, c.kc, c.ns, c.mminb};
         int64_t y = 0;
         for (size_t p = r.size(); p-- > 0;) {

@@ -26,6 +26,8 @@ CONFIGS_DIRECT = [
     "zpack:w=8,ly=2,kc=8,ns=8,minb=1",
     "zpack:w=4,ly=4,kc=16,ns=9,minb=1",
     "zpack:w=2,ly=1,kc=4,ns=12,minb=2",
+    "zpack:w=8,ly=1,kc=8,ns=8,minb=2,yx=1",
+    "zpack:w=4,ly=2,kc=16,ns=9,minb=1,yx=1",
 ]
 
 
