@@ -143,11 +143,15 @@ __device__ __forceinline__ void out(T *p, C v)
 //                     + |Us|*(10(a2-a3) - 5(a1-a4) + (a0-a5))
 //   2nd order:   4 F = Us*(a2+a3)
 
+// I6 keeps a2 and a3 unrounded until they are scaled by 37 (fused into the
+// last two steps): rounding the pair sum a2 + a3 first would multiply its
+// error by 37, making the face value's rounding error ~2.8 units instead of
+// ~1.9, and the flux differences amplify that error by 1/(k dx).
 __device__ __forceinline__ C flux5(C Us, C a0, C a1, C a2, C a3, C a4, C a5)
 {
-    C s1 = a2 + a3, s2 = a1 + a4, s3 = a0 + a5;
+    C s2 = a1 + a4, s3 = a0 + a5;
     C d1 = a2 - a3, d2 = a1 - a4, d3 = a0 - a5;
-    C i6 = fma(C(37), s1, fma(C(-8), s2, s3));
+    C i6 = fma(C(37), a2, fma(C(37), a3, fma(C(-8), s2, s3)));
     C d6 = fma(C(10), d1, fma(C(-5), d2, d3));
     return fma(Us, i6, fabs(Us) * d6);
 }
@@ -823,7 +827,7 @@ __device__ __forceinline__ V vsplat(C a) { return vmk(a, a); }
 // (hi of a, lo of b): the pair starting one element after a's
 __device__ __forceinline__ V vcross(V a, V b) { return vmk(vhi(a), vlo(b)); }
 
-struct kl_vk { V c37, cm8, c10, cm5; };
+struct kl_vk { V c37, cm8, c10, cm5, cm10, c5; };
 
 // packed face flux with the diffusive part folded in:
 //   G = F + kd * d1,  F as flux5 / flux2 (scaled by 1/KL_FS), d1 = a2 - a3
@@ -831,9 +835,10 @@ __device__ __forceinline__ V kl_vflux(const kl_vk &K, V Us, V a0, V a1, V a2, V 
 {
     V d1 = vsub(a2, a3);
 #if KL_ADV == 5
-    V s1 = vadd(a2, a3), s2 = vadd(a1, a4), s3 = vadd(a0, a5);
+    // a2, a3 stay unrounded until scaled by 37 (see flux5)
+    V s2 = vadd(a1, a4), s3 = vadd(a0, a5);
     V d2 = vsub(a1, a4), d3 = vsub(a0, a5);
-    V i6 = vfma(K.c37, s1, vfma(K.cm8, s2, s3));
+    V i6 = vfma(K.c37, a2, vfma(K.c37, a3, vfma(K.cm8, s2, s3)));
     V d6 = vfma(K.c10, d1, vfma(K.cm5, d2, d3));
     V f = vfma(Us, i6, vmul(vabs(Us), d6));
 #elif KL_ADV == 2
@@ -938,6 +943,7 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
     const C kdx = nu * dxi / KL_FS;
     kl_vk K;
     K.c37 = vsplat(C(37)); K.cm8 = vsplat(C(-8)); K.c10 = vsplat(C(10)); K.cm5 = vsplat(C(-5));
+    K.cm10 = vsplat(C(-10)); K.c5 = vsplat(C(5));
     const V vkdx = vsplat(kdx), vkdy = vsplat(nu * dyi / KL_FS);
     const V vcx = vsplat(KL_FS * dxi), vcy = vsplat(KL_FS * dyi);
 
@@ -949,23 +955,17 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
     bool timed_out = false;
     int p_waited = p_first - 1;
 
-    for (int k = kb; k < ke; ++k) {
-        {
-            int p = k + KL_R;
-            if (k == kb) {
-                for (int q = p_first; q < p; ++q) {
-                    unsigned b2 = kl_smem_addr(&bars[(q - p_first) % KL_NS]);
-                    bool ok2 = kl_mbar_wait(b2, ((q - p_first) / KL_NS) & 1);
-                    if (__syncthreads_or(!ok2)) { timed_out = true; break; }
-                    p_waited = q;
-                }
-                if (timed_out) break;
-            }
-            unsigned bar = kl_smem_addr(&bars[(p - p_first) % KL_NS]);
-            bool ok = kl_mbar_wait(bar, ((p - p_first) / KL_NS) & 1);
-            if (__syncthreads_or(!ok)) { timed_out = true; break; }
-            p_waited = p;
-        }
+    // planes of the first level; afterwards each level ends with the wait for
+    // the next level's newest plane and one barrier that both releases the
+    // slot of plane k-R and makes the time-out decision uniform
+    {
+        bool ok = true;
+        for (int q = p_first; q <= kb + KL_R && ok; ++q)
+            ok = kl_mbar_wait(kl_smem_addr(&bars[(q - p_first) % KL_NS]), ((q - p_first) / KL_NS) & 1);
+        timed_out = __syncthreads_or(!ok);
+        if (!timed_out) p_waited = kb + KL_R;
+    }
+    for (int k = kb; k < ke && !timed_out; ++k) {
         const char *pl[2 * KL_R + 1];
 #pragma unroll
         for (int d = -KL_R; d <= KL_R; ++d)
@@ -1172,7 +1172,16 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
             }
         }
 #undef KL_Q
-        __syncthreads();
+        bool ok = true;
+        if (k + 1 < ke) {
+            const int p = k + 1 + KL_R;
+            ok = kl_mbar_wait(kl_smem_addr(&bars[(p - p_first) % KL_NS]), ((p - p_first) / KL_NS) & 1);
+        }
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            break;
+        }
+        if (k + 1 < ke) p_waited = k + 1 + KL_R;
         if (tid == 0 && p_next <= p_last) issue(p_next++);
     }
 

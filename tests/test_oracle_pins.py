@@ -263,6 +263,19 @@ def test_momentum_conservation_walls_dz_weighted(oracle_mod, adv, diff):
         assert abs(t.sum()) > 1e-9 * np.abs(t).sum()
 
 
+@pytest.mark.parametrize("adv,diff", [(5, 1), (2, 1), (5, 2), (0, 1)])
+def test_momentum_conservation_periodic_stretched(oracle_mod, adv, diff):
+    """Periodic z on a non-uniform grid: the flux differences telescope for any
+    spacing, so sum ut dz_k, sum vt dz_k and sum wt dzh_k vanish to rounding
+    (the metric each component's divergence divides by is the right one)."""
+    f = _fields(n=(10, 8, 12), walls=False, stretch=2.0, nu0=1e-3)
+    dz, dzh = oracle_mod.zprofile(12, 3, False, f["zh"])
+    ut, vt, wt = run(oracle_mod, f, adv=adv, diff=diff, walls=False, nu_field=f["nu"])
+    for t, wgt in ((ut, dz), (vt, dz), (wt, dzh)):
+        tw = t * wgt[3:15][:, None, None]
+        assert abs(tw.sum()) <= 1e-13 * np.abs(tw).sum()
+
+
 def divergence_free(n=(16, 16, 16), seed=3):
     """C-grid velocity = discrete curl of random edge potentials (div = 0 to rounding)."""
     nx, ny, nz = n
