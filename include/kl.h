@@ -138,6 +138,25 @@ kl_status kl_fill_ghosts(kl_ctx *ctx, int32_t dtype, const kl_grid *grid,
 kl_status kl_launch(kl_ctx *ctx, const kl_op *op, const kl_grid *grid,
                     const kl_fields *fields, void *stream);
 
+/*
+ * The ghost fill that the configuration kl_launch selects for (op, grid)
+ * reads: as kl_fill_ghosts, except that for a configuration of the zpack
+ * family, which forms the periodic x halo of its tiles from interior columns
+ * itself, the x ghosts of interior rows of interior levels are not written
+ * (left as they were); y rows and z planes, their x ghosts included, are.
+ * Same checks as kl_launch; nothing is launched when they fail.
+ */
+kl_status kl_fill_ghosts_op(kl_ctx *ctx, const kl_op *op, const kl_grid *grid,
+                            const kl_fields *fields, void *stream);
+
+/*
+ * One step of the hot path: kl_fill_ghosts_op then kl_launch, both on
+ * `stream`, with one configuration selection.  The tendencies equal those of
+ * kl_fill_ghosts + kl_launch.  The input fields must be writable (ghosts).
+ */
+kl_status kl_step(kl_ctx *ctx, const kl_op *op, const kl_grid *grid, const kl_fields *fields,
+                  void *stream);
+
 /* As kl_launch with an explicit configuration string (see kl_config_help);
  * "default" is the untuned default configuration. */
 kl_status kl_launch_with_config(kl_ctx *ctx, const kl_op *op, const char *config,

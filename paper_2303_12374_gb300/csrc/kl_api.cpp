@@ -295,12 +295,13 @@ bool config_fits(const kl_op &op, const Config &cfg, const kl_grid &g, const kl_
 }
 
 // TMA descriptor of one field for the zmarch box; cached by pointer and layout
+// (box_x elements wide, z.rows rows, one plane)
 static kl_status get_tmap(kl_ctx *ctx, const kl_op &op, const kl_grid &g, const ZGeom &z,
-                          const void *ptr, CUtensorMap *out)
+                          int box_x, const void *ptr, CUtensorMap *out)
 {
     char key[256];
     snprintf(key, sizeof key, "%p/%d/%lld/%lld/%lld/%d/%d", ptr, op.dtype, (long long)g.sj,
-             (long long)g.sk, (long long)g.extent, z.pitch, z.rows);
+             (long long)g.sk, (long long)g.extent, box_x, z.rows);
     auto it = ctx->tmaps.find(key);
     if (it != ctx->tmaps.end()) {
         *out = it->second;
@@ -312,7 +313,7 @@ static kl_status get_tmap(kl_ctx *ctx, const kl_op &op, const kl_grid &g, const 
                                                   : CU_TENSOR_MAP_DATA_TYPE_UINT16;
     cuuint64_t dims[3] = {(cuuint64_t)g.sj, (cuuint64_t)(g.sk / g.sj), (cuuint64_t)(g.extent / g.sk)};
     cuuint64_t strides[2] = {(cuuint64_t)(g.sj * es), (cuuint64_t)(g.sk * es)};
-    cuuint32_t box[3] = {(cuuint32_t)z.pitch, (cuuint32_t)z.rows, 1};
+    cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)z.rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUtensorMap m;
     CUresult r = ctx->drv.TensorMapEncodeTiled(&m, dt, 3, const_cast<void *>(ptr), dims, strides, box,
@@ -328,7 +329,7 @@ static kl_status get_tmap(kl_ctx *ctx, const kl_op &op, const kl_grid &g, const 
 }
 
 kl_status make_kargs(kl_ctx *ctx, const kl_op &op, const Config &cfg, const kl_grid &g,
-                     const kl_fields &f, KArgs *ap, CUtensorMap maps[4])
+                     const kl_fields &f, KArgs *ap, CUtensorMap maps[KL_NMAPS])
 {
     std::string err;
     if (!config_check(op, cfg, &err)) return fail(KL_ERR_INVALID_ARG, "configuration: " + err);
@@ -384,9 +385,11 @@ kl_status make_kargs(kl_ctx *ctx, const kl_op &op, const Config &cfg, const kl_g
         a.nbx = (g.nx + z.txs - 1) / z.txs;
         a.nby = (g.ny + z.tys - 1) / z.tys;
         a.nbz = (g.nz + cfg.kc - 1) / cfg.kc;
-        const void *fp[4] = {f.u, f.v, f.w, op.diff == 2 ? f.nu : f.u};
-        for (int q = 0; q < 4; ++q) {
-            st = get_tmap(ctx, op, g, z, fp[q], &maps[q]);
+        const void *fp[KL_NMAPS] = {f.u, f.v, f.w, op.diff == 2 ? f.nu : f.u, f.u, f.v, f.w};
+        for (int q = 0; q < KL_NMAPS; ++q) {
+            // zpack's x-wrap strips are 32 bytes wide; zmarch never reads maps 4..6
+            int bx = q >= 4 && cfg.family == 2 ? 32 / es : z.pitch;
+            st = get_tmap(ctx, op, g, z, bx, fp[q], &maps[q]);
             if (st) return st;
         }
     }
@@ -397,7 +400,7 @@ kl_status launch_config(kl_ctx *ctx, const kl_op &op, const Config &cfg, const k
                         const kl_fields &f, cudaStream_t s)
 {
     KArgs a;
-    CUtensorMap maps[4];
+    CUtensorMap maps[KL_NMAPS];
     kl_status st = make_kargs(ctx, op, cfg, g, f, &a, maps);
     if (st) return st;
     if (!space_size(cfg.family)) return fail(KL_ERR_INVALID_ARG, "unknown family");
@@ -419,9 +422,10 @@ kl_status launch_config(kl_ctx *ctx, const kl_op &op, const Config &cfg, const k
                                   (CUstream)s, params, nullptr);
     } else {
         if (a.nby > 65535 || a.nbz > 65535) return fail(KL_ERR_UNSUPPORTED, "grid too large");
-        void *params[] = {&a, &maps[0], &maps[1], &maps[2], &maps[3]};
+        // zmarch takes the first four descriptors, zpack all seven
+        void *params[] = {&a, &maps[0], &maps[1], &maps[2], &maps[3], &maps[4], &maps[5], &maps[6]};
         r = ctx->drv.LaunchKernel(k->fn, (unsigned)a.nbx, (unsigned)a.nby, (unsigned)a.nbz,
-                                  cfg.mbx, cfg.mby, 1, (unsigned)k->smem, (CUstream)s, params,
+                                  cfg.mbx, zmarch_block_y(cfg), 1, (unsigned)k->smem, (CUstream)s, params,
                                   nullptr);
     }
     if (r != CUDA_SUCCESS) return cu_fail(r, "cuLaunchKernel");
@@ -594,6 +598,51 @@ kl_status kl_launch(kl_ctx *ctx, const kl_op *op, const kl_grid *grid, const kl_
     Config cfg;
     st = select_config(ctx, *op, *grid, &cfg);
     if (st) return st;
+    return launch_config(ctx, *op, cfg, *grid, *fields, (cudaStream_t)stream);
+}
+
+// checks, configuration selection and the ghost fill that configuration
+// needs (the zpack family wraps x itself: no x ghosts of interior rows)
+static kl_status fill_for_op(kl_ctx *ctx, const kl_op *op, const kl_grid *grid,
+                             const kl_fields *fields, void *stream, Config *cfg)
+{
+    if (!ctx) return fail(KL_ERR_INVALID_ARG, "ctx is NULL");
+    kl_status st = check_op(op);
+    if (st) return st;
+    st = check_fields(*op, fields);
+    if (st) return st;
+    st = check_grid(grid, halo_of(*op), nullptr);
+    if (st) return st;
+    if (grid->g > 4) return fail(KL_ERR_UNSUPPORTED, "ghost fill supports g <= 4");
+    st = select_config(ctx, *op, *grid, cfg);
+    if (st) return st;
+    // the zpack kernel forms the x halo itself on grids with nx >= 64 + H
+    const bool x_ghosts = !(cfg->family == 2 && grid->nx >= 64 + halo_of(*op));
+    cudaError_t e = fill_ghosts_launch(esize_of(op->dtype), *grid, (void *)fields->u,
+                                       (void *)fields->v, (void *)fields->w, (void *)fields->nu,
+                                       (cudaStream_t)stream, x_ghosts);
+    if (e != cudaSuccess) return cuda_fail(e, "fill ghosts launch");
+    ctx->launches++;
+    return KL_OK;
+}
+
+kl_status kl_fill_ghosts_op(kl_ctx *ctx, const kl_op *op, const kl_grid *grid,
+                            const kl_fields *fields, void *stream)
+{
+    Config cfg;
+    return fill_for_op(ctx, op, grid, fields, stream, &cfg);
+}
+
+kl_status kl_step(kl_ctx *ctx, const kl_op *op, const kl_grid *grid, const kl_fields *fields,
+                  void *stream)
+{
+    Config cfg;
+    kl_status st = fill_for_op(ctx, op, grid, fields, stream, &cfg);
+    if (st) return st;
+    if (env_lists("KERNEL_LAUNCHER_CAPTURE", "tendency")) {
+        st = kl_capture_if_requested(ctx, op, grid, fields, stream);
+        if (st) return st;
+    }
     return launch_config(ctx, *op, cfg, *grid, *fields, (cudaStream_t)stream);
 }
 

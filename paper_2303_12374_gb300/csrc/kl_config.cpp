@@ -30,8 +30,8 @@ std::string config_string(const Config &c)
         snprintf(b, sizeof b, "zmarch:bx=%d,by=%d,px=%d,py=%d,kc=%d,ns=%d,minb=%d", c.mbx, c.mby,
                  c.mpx, c.mpy, c.kc, c.ns, c.mminb);
     } else {
-        snprintf(b, sizeof b, "zpack:w=%d,ly=%d,kc=%d,ns=%d,minb=%d,yx=%d,pk=%d", c.mby, c.mpy,
-                 c.kc, c.ns, c.mminb, c.yx, c.pk);
+        snprintf(b, sizeof b, "zpack:w=%d,ly=%d,kc=%d,ns=%d,minb=%d,yx=%d,pk=%d,cs=%d", c.mby,
+                 c.mpy, c.kc, c.ns, c.mminb, c.yx, c.pk, c.cs);
     }
     return b;
 }
@@ -106,6 +106,7 @@ bool config_parse(const std::string &text, Config *c, std::string *err)
             if (k == "w") dst = &c->mby; else if (k == "ly") dst = &c->mpy;
             else if (k == "yx") dst = &c->yx;
             else if (k == "pk") dst = &c->pk;
+            else if (k == "cs") dst = &c->cs;
             else if (k == "kc") dst = &c->kc; else if (k == "ns") dst = &c->ns;
             else if (k == "minb") dst = &c->mminb;
         } else {
@@ -153,6 +154,8 @@ size_t zmarch_smem_bytes(const kl_op &op, const Config &c)
     ZGeom z = zmarch_geometry(op, c);
     // ring + 128 B of alignment slack + one 8-byte mbarrier per slot
     size_t bytes = z.plane_bytes * z.nf * c.ns + 256;
+    // zpack x-wrap strips: 3 fields x rows x 32 bytes per slot (128-B multiples)
+    if (c.family == 2) bytes += 3 * (size_t)((z.rows * 32 + 127) / 128 * 128) * c.ns;
     // zpack y-face exchange: 3 fields x warps x 32 lanes x one packed pair
     if (c.family == 2 && c.yx)
         bytes += 3 * (size_t)c.mby * 32 * (op.dtype == KL_F64 ? 16 : 8) + 16;
@@ -205,8 +208,13 @@ bool config_check(const kl_op &op, const Config &c, std::string *err)
             *err = "zpack parameter outside the space (w 1..16, ly 1..8)";
             return false;
         }
-        if (c.family == 2 && ((c.yx != 0 && c.yx != 1) || (c.pk != 0 && c.pk != 1))) {
-            *err = "yx and pk must be 0 or 1";
+        if (c.family == 2 &&
+            ((c.yx != 0 && c.yx != 1) || (c.pk != 0 && c.pk != 1) || (c.cs != 0 && c.cs != 1))) {
+            *err = "yx, pk and cs must be 0 or 1";
+            return false;
+        }
+        if (c.family == 2 && c.cs && c.yx) {
+            *err = "cs=1 forms every y face in its own warp group (yx must be 0)";
             return false;
         }
         if (c.family == 2 && op.diff == 2) {
@@ -218,8 +226,12 @@ bool config_check(const kl_op &op, const Config &c, std::string *err)
             *err = "z-march parameter outside the space";
             return false;
         }
-        if (c.mbx * c.mby > 1024) {
+        if (c.mbx * zmarch_block_y(c) > 1024) {
             *err = "more than 1024 threads per block";
+            return false;
+        }
+        if (c.mminb * c.mbx * zmarch_block_y(c) > 2048) {
+            *err = "minb x threads per block exceeds 2048 threads per SM";
             return false;
         }
         int reach = halo_of(op);
@@ -255,7 +267,7 @@ int64_t space_size(int family)
 {
     if (family == 0) return 5LL * 5 * 5 * 27 * 8 * 8 * 6 * 6;
     if (family == 1) return 3LL * 5 * 3 * 3 * 7 * 4 * 4;
-    if (family == 2) return 5LL * 4 * 7 * 4 * 4 * 2;
+    if (family == 2) return 5LL * 4 * 7 * 4 * 4 * 2 * 2;
     return 0;
 }
 
@@ -289,6 +301,7 @@ bool space_config(int family, int64_t idx, Config *c)
         c->ns = kNS[take(4)];
         c->mminb = 1 + take(4);
         c->yx = take(2);
+        c->cs = take(2);
     } else {
         c->mbx = kMBX[take(3)];
         c->mby = kMBY[take(5)];
@@ -503,9 +516,9 @@ std::string compile_defines(const kl_op &op, const Config &c, int zbc, int zuni)
     } else {
         snprintf(b + n, sizeof b - n,
                  " -DKL_MBX=%d -DKL_MBY=%d -DKL_MPX=%d -DKL_MPY=%d -DKL_KC=%d -DKL_NS=%d"
-                 " -DKL_MMINB=%d -DKL_YX=%d -DKL_PK=%d",
+                 " -DKL_MMINB=%d -DKL_YX=%d -DKL_PK=%d -DKL_CS=%d",
                  c.mbx, c.mby, c.mpx, c.mpy, c.kc, c.ns, c.mminb, c.family == 2 ? c.yx : 0,
-                 c.family == 2 ? c.pk : 1);
+                 c.family == 2 ? c.pk : 1, c.family == 2 ? c.cs : 0);
     }
     return b;
 }

@@ -12,82 +12,99 @@ namespace {
 
 // ------------------------------------------------------------ ghost fill
 //
-// Ghost points form three disjoint groups, one per blockIdx.z: the 2g full z
-// planes (x and y ghosts included), the 2g y rows of every interior level (x
-// ghosts included), and the 2g x points of every interior row.  Each ghost maps
-// straight to an interior source point, axis by axis, so one launch fills
-// faces, edges and corners with no ordering between them.  The copy moves raw
-// bits; the odd (w) mirror flips the sign bit, which negates exactly in every
-// format.  blockIdx.x / blockIdx.y index x and the row inside a group, so no
-// thread divides by a run-time extent.
+// Ghost points form three disjoint groups laid end to end in one linear cell
+// index: the 2g full z planes (x and y ghosts included), the 2g y rows of
+// every interior level (x ghosts included), and the 2g x points of every
+// interior row.  Each ghost maps straight to an interior source point, axis by
+// axis, so one launch fills faces, edges and corners with no ordering between
+// them (no source is ever a ghost).  The copy moves raw bits; the odd (w)
+// mirror flips the sign bit, which negates exactly in every format.
+//
+// A block covers FILL_U x 256 consecutive cells; each thread issues the loads
+// of its FILL_U cells (all fields) before any store, so a thread keeps up to
+// 4 x FILL_U loads in flight, and consecutive lanes touch consecutive cells.
+
+constexpr int FILL_T = 256, FILL_U = 4;
 
 struct FillArgs {
     char *f[4];              // u, v, w, nu at interior (0,0,0); nu may be NULL
     long long sj, sk;
     int nx, ny, nz, zbc;
-    int px, py;              // padded row length / rows per plane
-    int gxp, gxx;            // blocks per padded row, per row of x ghosts
-    int b0, b1;              // first block of the y-row group, of the x group
+    unsigned px, py;         // padded row length, padded rows per plane
+    unsigned n0, n1, n2;     // cell index ends of the z-plane, y-row and x groups
 };
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-template <typename B, int G>
-__device__ __forceinline__ void fill_one(const FillArgs &a, int i, int j, int k)
+template <int G>
+__device__ __forceinline__ void fill_decode(const FillArgs &a, unsigned q, int &i, int &j, int &k)
 {
-    const B sign_bit = (B)1 << (sizeof(B) * 8 - 1);
-    int si = wrapi(i, a.nx), sj = wrapi(j, a.ny);
-    long long dst = i + j * a.sj + k * a.sk;
-    int ske;
-    if (a.zbc == 0) ske = wrapi(k, a.nz);
-    else ske = k < 0 ? -1 - k : (k >= a.nz ? 2 * a.nz - 1 - k : k);
-    long long srce = si + sj * a.sj + (long long)ske * a.sk;
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        if (f == 2 || !a.f[f]) continue;
-        B *p = (B *)a.f[f];
-        p[dst] = p[srce];
-    }
-    B *pw = (B *)a.f[2];
-    if (a.zbc == 0) {
-        pw[dst] = pw[srce];
-    } else if (k == a.nz) {
-        pw[dst] = (B)0;
-    } else {
-        int sko = k < 0 ? -k : (k > a.nz ? 2 * a.nz - k : k);
-        B v = pw[si + sj * a.sj + (long long)sko * a.sk];
-        pw[dst] = (k < 0 || k > a.nz) ? (B)(v ^ sign_bit) : v;
+    if (q < a.n0) {                        // full z planes: px points x py rows x 2G planes
+        unsigned r = q / a.px, p = r / a.py;
+        i = (int)(q - r * a.px) - G;
+        j = (int)(r - p * a.py) - G;
+        k = p < (unsigned)G ? (int)p - G : a.nz + ((int)p - G);
+    } else if (q < a.n1) {                 // y rows: px points x 2G rows x nz levels
+        unsigned t = q - a.n0, r = t / a.px, kk = r / (2 * G), qq = r - kk * (2 * G);
+        i = (int)(t - r * a.px) - G;
+        j = qq < (unsigned)G ? (int)qq - G : a.ny + ((int)qq - G);
+        k = (int)kk;
+    } else {                               // x ghosts: 2G points x ny rows x nz levels
+        unsigned t = q - a.n1, r = t / (2 * G), qq = t - r * (2 * G), kk = r / (unsigned)a.ny;
+        i = qq < (unsigned)G ? (int)qq - G : a.nx + ((int)qq - G);
+        j = (int)(r - kk * (unsigned)a.ny);
+        k = (int)kk;
     }
 }
 
 template <typename B, int G>
-__global__ void __launch_bounds__(128) fill_kernel(FillArgs a)
+__global__ void __launch_bounds__(FILL_T) fill_kernel(FillArgs a)
 {
-    // blocks [0, b0): z planes; [b0, b1): y rows; [b1, end): x ghosts
-    int b = blockIdx.x;
-    if (b < a.b0) {                        // full z planes: row r of 2G * py rows
-        int r = b / a.gxp, bx = b - r * a.gxp;
-        int i = bx * 128 + threadIdx.x - G;
-        if (i >= a.nx + G) return;
-        int p = r / a.py, j = r - p * a.py - G;
-        int k = p < G ? p - G : a.nz + (p - G);
-        fill_one<B, G>(a, i, j, k);
-    } else if (b < a.b1) {                 // y rows of interior levels
-        b -= a.b0;
-        int r = b / a.gxp, bx = b - r * a.gxp;
-        int i = bx * 128 + threadIdx.x - G;
-        if (i >= a.nx + G) return;
-        int k = r / (2 * G), q = r - k * (2 * G);
-        int j = q < G ? q - G : a.ny + (q - G);
-        fill_one<B, G>(a, i, j, k);
-    } else {                               // x ghosts of interior rows
-        b -= a.b1;
-        int k = b / a.gxx, bx = b - k * a.gxx;
-        int t = bx * 128 + threadIdx.x;
-        if (t >= 2 * G * a.ny) return;
-        int j = t / (2 * G), q = t - j * (2 * G);
-        int i = q < G ? q - G : a.nx + (q - G);
-        fill_one<B, G>(a, i, j, k);
+    const B sign_bit = (B)1 << (sizeof(B) * 8 - 1);
+    long long dst[FILL_U], src[FILL_U], srcw[FILL_U];
+    bool live[FILL_U], wzero[FILL_U], wneg[FILL_U];
+    const unsigned base = blockIdx.x * (unsigned)(FILL_T * FILL_U) + threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < FILL_U; ++c) {
+        const unsigned q = base + c * FILL_T;
+        live[c] = q < a.n2;
+        int i = 0, j = 0, k = 0;
+        if (live[c]) fill_decode<G>(a, q, i, j, k);
+        const int si = wrapi(i, a.nx), sj = wrapi(j, a.ny);
+        int ske, sko;
+        if (a.zbc == 0) {
+            ske = sko = wrapi(k, a.nz);
+        } else {
+            ske = k < 0 ? -1 - k : (k >= a.nz ? 2 * a.nz - 1 - k : k);
+            sko = k < 0 ? -k : (k > a.nz ? 2 * a.nz - k : k);
+        }
+        dst[c] = i + j * a.sj + k * a.sk;
+        src[c] = si + sj * a.sj + (long long)ske * a.sk;
+        srcw[c] = si + sj * a.sj + (long long)sko * a.sk;
+        wzero[c] = a.zbc != 0 && k == a.nz;
+        wneg[c] = a.zbc != 0 && (k < 0 || k > a.nz);
+    }
+    B val[FILL_U][4];
+#pragma unroll
+    for (int c = 0; c < FILL_U; ++c) {
+        if (!live[c]) continue;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            if (f != 2 && !a.f[f]) continue;
+            const B *p = (const B *)a.f[f];
+            if (f != 2) val[c][f] = p[src[c]];
+            else if (!wzero[c]) val[c][f] = p[srcw[c]];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < FILL_U; ++c) {
+        if (!live[c]) continue;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            if (f != 2 && !a.f[f]) continue;
+            B v = f != 2 ? val[c][f] : (wzero[c] ? (B)0 : (wneg[c] ? (B)(val[c][f] ^ sign_bit) : val[c][f]));
+            ((B *)a.f[f])[dst[c]] = v;
+        }
     }
 }
 
@@ -95,10 +112,10 @@ template <typename B>
 static cudaError_t fill_dispatch(int g, unsigned grid, const FillArgs &a, cudaStream_t s)
 {
     switch (g) {
-    case 1: fill_kernel<B, 1><<<grid, 128, 0, s>>>(a); break;
-    case 2: fill_kernel<B, 2><<<grid, 128, 0, s>>>(a); break;
-    case 3: fill_kernel<B, 3><<<grid, 128, 0, s>>>(a); break;
-    case 4: fill_kernel<B, 4><<<grid, 128, 0, s>>>(a); break;
+    case 1: fill_kernel<B, 1><<<grid, FILL_T, 0, s>>>(a); break;
+    case 2: fill_kernel<B, 2><<<grid, FILL_T, 0, s>>>(a); break;
+    case 3: fill_kernel<B, 3><<<grid, FILL_T, 0, s>>>(a); break;
+    case 4: fill_kernel<B, 4><<<grid, FILL_T, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -200,7 +217,7 @@ __global__ void __launch_bounds__(256) diag_final(const double *partial, int nb,
 namespace kl {
 
 cudaError_t fill_ghosts_launch(int esize, const kl_grid &g, void *u, void *v, void *w, void *nu,
-                               cudaStream_t s)
+                               cudaStream_t s, bool x_ghosts)
 {
     if (g.g < 1 || g.g > 4) return cudaErrorInvalidValue;
     FillArgs a;
@@ -215,17 +232,18 @@ cudaError_t fill_ghosts_launch(int esize, const kl_grid &g, void *u, void *v, vo
     a.ny = g.ny;
     a.nz = g.nz;
     a.zbc = g.zbc;
-    a.px = g.nx + 2 * g.g;
-    a.py = g.ny + 2 * g.g;
-    a.gxp = (a.px + 127) / 128;
-    a.gxx = (2 * g.g * g.ny + 127) / 128;
-    long long b0 = (long long)a.gxp * 2 * g.g * a.py;
-    long long b1 = b0 + (long long)a.gxp * 2 * g.g * g.nz;
-    long long bt = b1 + (long long)a.gxx * g.nz;
-    if (bt > 0x7fffffffLL) return cudaErrorInvalidValue;
-    a.b0 = (int)b0;
-    a.b1 = (int)b1;
-    unsigned grid = (unsigned)bt;
+    long long px = g.nx + 2LL * g.g, py = g.ny + 2LL * g.g;
+    long long n0 = px * py * 2 * g.g;
+    long long n1 = n0 + px * 2 * g.g * g.nz;
+    long long n2 = x_ghosts ? n1 + 2LL * g.g * g.ny * g.nz : n1;
+    // 32-bit cell indices, and the last block's FILL_U x FILL_T cells too
+    if (n2 + FILL_T * FILL_U > 0x7fffffffLL) return cudaErrorInvalidValue;
+    a.px = (unsigned)px;
+    a.py = (unsigned)py;
+    a.n0 = (unsigned)n0;
+    a.n1 = (unsigned)n1;
+    a.n2 = (unsigned)n2;
+    unsigned grid = (unsigned)((n2 + FILL_T * FILL_U - 1) / (FILL_T * FILL_U));
     if (esize == 8) return fill_dispatch<unsigned long long>(g.g, grid, a, s);
     if (esize == 4) return fill_dispatch<unsigned int>(g.g, grid, a, s);
     return fill_dispatch<unsigned short>(g.g, grid, a, s);

@@ -39,7 +39,15 @@ struct Config {
     int mminb = 1;             // min blocks per SM
     int yx = 0;                // zpack: exchange y faces between warps (shared memory)
     int pk = 1;                // zpack: packed f32x2 arithmetic (f32 compute)
+    int cs = 0;                // zpack: one warp group per tendency component (3 x w warps)
 };
+
+// TMA descriptors per launch: u, v, w, nu with the plane box, then u, v, w
+// with the 32-byte x-wrap strip box (zpack)
+constexpr int KL_NMAPS = 7;
+
+// threads of a z-march block along y (zpack with cs=1: three warp groups)
+inline int zmarch_block_y(const Config &c) { return c.mby * (c.family == 2 && c.cs ? 3 : 1); }
 
 std::string config_string(const Config &c);
 bool config_parse(const std::string &s, Config *c, std::string *err);
@@ -177,7 +185,7 @@ kl_status get_kernel(kl_ctx *ctx, const kl_op &op, const Config &cfg, int zbc, i
                      Kernel **out, bool batch = false);
 // kernel arguments and TMA descriptors of one launch (validated)
 kl_status make_kargs(kl_ctx *ctx, const kl_op &op, const Config &cfg, const kl_grid &g,
-                     const kl_fields &f, KArgs *a, CUtensorMap maps[4]);
+                     const kl_fields &f, KArgs *a, CUtensorMap maps[KL_NMAPS]);
 kl_status select_config(kl_ctx *ctx, const kl_op &op, const kl_grid &g, Config *cfg);
 kl_status check_op(const kl_op *op);
 kl_status check_fields(const kl_op &op, const kl_fields *f);
@@ -186,8 +194,10 @@ kl_status get_profile(kl_ctx *ctx, const kl_grid &g, Profile **out);
 bool config_fits(const kl_op &op, const Config &cfg, const kl_grid &g, const kl_fields *f,
                  std::string *why);
 // device kernels of kl_device.cu
+// x_ghosts false: leave the x ghosts of interior rows of interior levels as
+// they are (fill the y rows and z planes only)
 cudaError_t fill_ghosts_launch(int esize, const kl_grid &g, void *u, void *v, void *w,
-                               void *nu, cudaStream_t s);
+                               void *nu, cudaStream_t s, bool x_ghosts = true);
 cudaError_t diag_launch(int dtype, const kl_grid &g, int level, const void *t,
                         const double *ref, const double *wz, double *scratch, int nblocks,
                         double *dout, cudaStream_t s);

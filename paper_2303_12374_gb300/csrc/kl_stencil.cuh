@@ -40,6 +40,12 @@
 #ifndef KL_YX
 #define KL_YX 0       // zpack: exchange y faces between warps through shared memory
 #endif
+#ifndef KL_CS
+#define KL_CS 0       // zpack: one warp group per tendency component
+#endif
+#if KL_CS && KL_YX
+#error "KL_CS forms every y face in its own warp group; KL_YX must be 0"
+#endif
 #ifndef KL_BATCH
 #define KL_BATCH 0    // 1: one launch over many grids through a device tile table
 #endif
@@ -688,14 +694,14 @@ __device__ __forceinline__ void kl_zmarch_body(const kl_args &a, const kl_tmap *
 
 #if KL_BATCH
 // many grids in one launch: block b runs tile (y, z, w) of grid x of blocks[b];
-// TMA descriptors of grid g at maps[4g .. 4g+3] (global memory, 64-B aligned)
+// TMA descriptors of grid g at maps[7g .. 7g+3] (global memory, 64-B aligned)
 extern "C" __global__ void __launch_bounds__(KL_MBX * KL_MBY, KL_MMINB)
 kl_tendency(const kl_args *argv, const int4 *blocks, const kl_tmap *tmaps)
 {
     const int4 d = blocks[blockIdx.x];
     const kl_args a = argv[d.x];
-    const kl_tmap *maps[4] = {&tmaps[4 * d.x], &tmaps[4 * d.x + 1], &tmaps[4 * d.x + 2],
-                              &tmaps[4 * d.x + 3]};
+    const kl_tmap *maps[4] = {&tmaps[7 * d.x], &tmaps[7 * d.x + 1], &tmaps[7 * d.x + 2],
+                              &tmaps[7 * d.x + 3]};
     if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int f = 0; f < KL_NF; ++f) kl_tmap_acquire(maps[f]);
     kl_zmarch_body(a, maps, d.y, d.z, d.w);
@@ -748,7 +754,6 @@ __device__ __forceinline__ V vadd(V a, V b) { return vmk(a.lo + b.lo, a.hi + b.h
 __device__ __forceinline__ V vsub(V a, V b) { return vmk(a.lo - b.lo, a.hi - b.hi); }
 __device__ __forceinline__ V vmul(V a, V b) { return vmk(a.lo * b.lo, a.hi * b.hi); }
 __device__ __forceinline__ V vfma(V a, V b, V c) { return vmk(fma(a.lo, b.lo, c.lo), fma(a.hi, b.hi, c.hi)); }
-__device__ __forceinline__ V vabs(V a) { return vmk(fabs(a.lo), fabs(a.hi)); }
 #if KL_DTYPE == 0
 // aligned pair of consecutive elements at p (16-byte aligned)
 __device__ __forceinline__ V vld(const T *p) { double2 d = *(const double2 *)p; return vmk(d.x, d.y); }
@@ -801,7 +806,6 @@ __device__ __forceinline__ V vfma(V a, V b, V c)
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.b) : "l"(a.b), "l"(b.b), "l"(c.b));
     return r;
 }
-__device__ __forceinline__ V vabs(V a) { V r; r.b = a.b & 0x7fffffff7fffffffull; return r; }
 #if KL_DTYPE == 1
 __device__ __forceinline__ V vld(const T *p) { V r; r.b = *(const unsigned long long *)p; return r; }
 __device__ __forceinline__ void vst(T *p, V a) { *(unsigned long long *)p = a.b; }
@@ -840,7 +844,9 @@ __device__ __forceinline__ V kl_vflux(const kl_vk &K, V Us, V a0, V a1, V a2, V 
     V d2 = vsub(a1, a4), d3 = vsub(a0, a5);
     V i6 = vfma(K.c37, a2, vfma(K.c37, a3, vfma(K.cm8, s2, s3)));
     V d6 = vfma(K.c10, d1, vfma(K.cm5, d2, d3));
-    V f = vfma(Us, i6, vmul(vabs(Us), d6));
+    // |U| d6 as two scalar products: the absolute value folds into the
+    // multiply as an operand modifier instead of two integer masks
+    V f = vfma(Us, i6, vmk(fabs(vlo(Us)) * vlo(d6), fabs(vhi(Us)) * vhi(d6)));
 #elif KL_ADV == 2
     V f = vmul(Us, vadd(a2, a3));
 #else
@@ -892,6 +898,145 @@ __device__ __forceinline__ V kl_pr(const char *const *pl, int lx, int row)
     return vld((const T *)(pl[DK + KL_R] + F * KL_PLANE_BYTES + KL_OFF(lx + DX, row)));
 }
 
+#if KL_CS
+// ---- component split (cs=1): the block holds three groups of KL_MBY warps
+// over the same tile; group CP forms every face flux of tendency component CP
+// (0: u, 1: v, 2: w) with the same expressions, in the same order, as the
+// all-component path, so both give identical results.  A thread carries one
+// component's z faces instead of three, which leaves room for three times the
+// warps per tile.
+#define KL_P(f, dk, dx, row) kl_pr<(f), (dk), (dx)>(pl, lx, (row))
+
+// y face of component CP at the bottom edge of tile row yr
+template <int CP>
+__device__ __forceinline__ V kl_cs_yface(const kl_vk &K, const char *const *pl, int lx, int yr, V kd)
+{
+    V us;
+    if constexpr (CP == 0) us = vadd(vcross(KL_P(1, 0, -2, yr), KL_P(1, 0, 0, yr)), KL_P(1, 0, 0, yr));
+    else if constexpr (CP == 1) us = vadd(KL_P(1, 0, 0, yr - 1), KL_P(1, 0, 0, yr));
+    else us = vadd(KL_P(1, -1, 0, yr), KL_P(1, 0, 0, yr));
+    return kl_vflux(K, us, KL_A5(KL_P(CP, 0, 0, yr - 3)), KL_A5(KL_P(CP, 0, 0, yr - 2)),
+                    KL_P(CP, 0, 0, yr - 1), KL_P(CP, 0, 0, yr), KL_A5(KL_P(CP, 0, 0, yr + 1)),
+                    KL_A5(KL_P(CP, 0, 0, yr + 2)), kd);
+}
+
+// z face of component CP below plane DK (DK = 1: top face of the level, 0: bottom)
+template <int CP, int DK>
+__device__ __forceinline__ V kl_cs_zface(const kl_vk &K, const char *const *pl, int lx, int yr, V kd)
+{
+    V us;
+    if constexpr (CP == 0) us = vadd(vcross(KL_P(2, DK, -2, yr), KL_P(2, DK, 0, yr)), KL_P(2, DK, 0, yr));
+    else if constexpr (CP == 1) us = vadd(KL_P(2, DK, 0, yr - 1), KL_P(2, DK, 0, yr));
+    else us = vadd(KL_P(2, DK - 1, 0, yr), KL_P(2, DK, 0, yr));
+    return kl_vflux(K, us, KL_A5(KL_P(CP, DK - 3, 0, yr)), KL_A5(KL_P(CP, DK - 2, 0, yr)),
+                    KL_P(CP, DK - 1, 0, yr), KL_P(CP, DK, 0, yr), KL_A5(KL_P(CP, DK + 1, 0, yr)),
+                    KL_A5(KL_P(CP, DK + 2, 0, yr)), kd);
+}
+
+template <int CP>
+__device__ __forceinline__ void kl_cs_level(const kl_args &a, const kl_vk &K, const char *const *pl,
+                                            const kl_zmetric &Z, int lane, int lx, int r0, int c0,
+                                            int ty0, int k, int kb, C nu, C kdx, V vkdx, V vkdy,
+                                            V vcx, V vcy, V (&zb)[KL_MPY])
+{
+    const V vcz = vsplat(KL_FS * (CP == 2 ? Z.dzhi : Z.dzi));
+    const V vkz_top = vsplat(nu * (CP == 2 ? Z.dzi : Z.dzhi_up) / KL_FS);
+
+    // side pass: lane e < KL_MPY forms the x face beyond the warp's columns of row r0 + e
+    C extra;
+    {
+        const int row = r0 + (lane < KL_MPY ? lane : 0);
+        const int xs = CP == 0 ? KL_LPAD - 3 : KL_LPAD + 61;
+        const char *base = pl[KL_R] + CP * KL_PLANE_BYTES;
+        C a2 = lds((const T *)(base + KL_OFF(xs + 2, row)));
+        C a3 = lds((const T *)(base + KL_OFF(xs + 3, row)));
+#if KL_ADV == 5
+        C a0 = lds((const T *)(base + KL_OFF(xs, row)));
+        C a1 = lds((const T *)(base + KL_OFF(xs + 1, row)));
+        C a4 = lds((const T *)(base + KL_OFF(xs + 4, row)));
+        C a5 = lds((const T *)(base + KL_OFF(xs + 5, row)));
+#else
+        C a0 = C(0), a1 = C(0), a4 = C(0), a5 = C(0);
+#endif
+        C us;
+        if constexpr (CP == 0)
+            us = a2 + a3;
+        else if constexpr (CP == 1)
+            us = lds((const T *)(pl[KL_R] + KL_OFF(KL_LPAD + 64, row - 1))) +
+                 lds((const T *)(pl[KL_R] + KL_OFF(KL_LPAD + 64, row)));
+        else
+            us = lds((const T *)(pl[KL_R - 1] + KL_OFF(KL_LPAD + 64, row))) +
+                 lds((const T *)(pl[KL_R] + KL_OFF(KL_LPAD + 64, row)));
+        extra = kl_sflux(us, a0, a1, a2, a3, a4, a5, kdx);
+    }
+
+    V fy_b = kl_cs_yface<CP>(K, pl, lx, r0, vkdy);
+    T *const dst = CP == 0 ? a.ut : CP == 1 ? a.vt : a.wt;
+#pragma unroll
+    for (int r = 0; r < KL_MPY; ++r) {
+        const int yr = r0 + r;
+        // x faces of both columns; the face on the far side of the pair comes
+        // from the neighbour lane, or from the side pass at the warp's edge
+        const C e = __shfl_sync(0xffffffffu, extra, r);
+        V tx;
+        if constexpr (CP == 0) {
+            V u_m2 = KL_A5(KL_P(0, 0, -2, yr)), u_0 = KL_P(0, 0, 0, yr), u_2 = KL_P(0, 0, 2, yr);
+            V fx = kl_vflux(K, vadd(u_0, vcross(u_0, u_2)), KL_A5(u_m2), KL_A5(vcross(u_m2, u_0)), u_0,
+                            vcross(u_0, u_2), KL_A5(u_2), KL_A5(vcross(u_2, KL_P(0, 0, 4, yr))), vkdx);
+            C hi = __shfl_sync(0xffffffffu, vhi(fx), (lane + 31) & 31);
+            tx = vsub(vmk(lane == 0 ? e : hi, vlo(fx)), fx);
+        } else {
+            V m4 = KL_A5(KL_P(CP, 0, -4, yr)), m2 = KL_P(CP, 0, -2, yr), p0 = KL_P(CP, 0, 0, yr),
+              p2 = KL_P(CP, 0, 2, yr);
+            V us = CP == 1 ? vadd(KL_P(0, 0, 0, yr - 1), KL_P(0, 0, 0, yr))
+                           : vadd(KL_P(0, -1, 0, yr), KL_P(0, 0, 0, yr));
+            V fx = kl_vflux(K, us, KL_A5(vcross(m4, m2)), KL_A5(m2), vcross(m2, p0), p0,
+                            KL_A5(vcross(p0, p2)), KL_A5(p2), vkdx);
+            C lo = __shfl_sync(0xffffffffu, vlo(fx), (lane + 1) & 31);
+            tx = vsub(fx, vmk(vhi(fx), lane == 31 ? e : lo));
+        }
+        const V fy_t = kl_cs_yface<CP>(K, pl, lx, yr + 1, vkdy);
+        const V fz = kl_cs_zface<CP, 1>(K, pl, lx, yr, vkz_top);
+        if (k == kb)
+            zb[r] = kl_cs_zface<CP, 0>(K, pl, lx, yr,
+                                       vsplat(nu * (CP == 2 ? Z.dzi_dn : Z.dzhi) / KL_FS));
+        V t = vfma(tx, vcx, vfma(vsub(fy_b, fy_t), vcy, vmul(vsub(zb[r], fz), vcz)));
+        zb[r] = fz;
+        fy_b = fy_t;
+        if (CP == 2 && KL_ZBC == 1 && k == 0) t = vsplat(C(0));
+        const int j = ty0 + yr;
+        if (j < (int)a.ny) {
+            const long long o = (long long)c0 + (long long)j * a.sj + (long long)k * a.sk;
+            if (c0 + 1 < (int)a.nx) {
+#if KL_ACC
+                t = vadd(t, vldg(dst + o));
+#endif
+                vst(dst + o, t);
+            } else if (c0 < (int)a.nx) {
+                out(dst + o, vlo(t));
+            }
+        }
+    }
+}
+#undef KL_P
+#endif  // KL_CS
+
+// ---- periodic x inside the kernel.  On a grid with nx >= 64 + H, the one
+// tile whose reach [tx0 - H, tx0 + 64 + H) crosses x = 0 (or x = nx) loads,
+// with each plane, a strip of 32 bytes x KL_ROWS rows per field that holds the
+// interior columns its halo wraps to; once the plane has landed each thread
+// copies its share of those values over the halo columns (between its wait
+// and the level's barrier).  The kernel then reads no x ghost column of
+// memory: the y and z ghosts must be filled, the x ghosts of interior rows
+// need not be.  Narrower grids read the filled x ghosts.
+#define KL_XW_W (32 / (int)sizeof(T))                        // strip width, elements
+#define KL_STRIP_BOX (KL_ROWS * 32)                          // bytes one strip box lands
+#define KL_STRIP_BYTES KL_RUP(KL_STRIP_BOX, 128)
+#define KL_ZSLOT (3 * KL_PLANE_BYTES + 3 * KL_STRIP_BYTES)   // zpack ring slot
+#define KL_NT (32 * KL_MBY * (KL_CS ? 3 : 1))                // threads per block
+#define KL_XW_Q ((3 * KL_ROWS * KL_H + KL_NT - 1) / KL_NT)   // halo values per thread
+static_assert(KL_AL - 1 + KL_H - 1 < KL_XW_W, "a strip must hold the wrapped columns");
+
 __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *const *maps,
                                               int bxi, int byi, int bzi)
 {
@@ -903,13 +1048,14 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
     static_assert(KL_PITCH >= KL_LPAD + 64 + (KL_ADV == 5 ? 3 : 1), "right pad too small");
     extern __shared__ unsigned char kl_smem_raw[];
     unsigned char *ring = (unsigned char *)(((unsigned long long)kl_smem_raw + 127) & ~127ull);
-    unsigned long long *bars = (unsigned long long *)(ring + KL_NS * KL_SLOT_BYTES);
+    unsigned long long *bars = (unsigned long long *)(ring + KL_NS * KL_ZSLOT);
 #if KL_YX
     // y-face exchange buffer after the barriers: [3 fields][warps][32 lanes]
     V *xbuf = (V *)(((unsigned long long)(bars + KL_NS) + 15) & ~15ull);
 #endif
-    const int lane = threadIdx.x, warp = threadIdx.y;
-    const int tid = lane + 32 * warp;
+    const int lane = threadIdx.x;
+    const int warp = KL_CS ? (int)threadIdx.y % KL_MBY : (int)threadIdx.y;
+    const int tid = lane + 32 * (int)threadIdx.y;
     const int nx = (int)a.nx, ny = (int)a.ny, nz = (int)a.nz;
     const int kb = bzi * (int)a.kchunk;
     const int ke = min(kb + (int)a.kchunk, nz);
@@ -923,20 +1069,53 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
+    // x wrap (see above): which side this tile wraps, never both
+    const bool xw_on = nx >= 64 + KL_H;
+    const bool need_l = xw_on && tx0 == 0, need_r = xw_on && tx0 + 64 + KL_H > nx;
+    const bool xwrap = need_l || need_r;
+    const int xs0 = need_l ? (nx - KL_H) / KL_AL * KL_AL : 0;   // first strip column
     auto issue = [&](int p) {
         int slot = (p - (kb - KL_R)) % KL_NS;
         unsigned bar = kl_smem_addr(&bars[slot]);
-        kl_mbar_expect(bar, 3 * KL_BOX_BYTES);
-        unsigned dst = kl_smem_addr(ring + slot * KL_SLOT_BYTES);
+        kl_mbar_expect(bar, 3 * KL_BOX_BYTES + (xwrap ? 3 * KL_STRIP_BOX : 0));
+        unsigned dst = kl_smem_addr(ring + slot * KL_ZSLOT);
 #pragma unroll
         for (int f = 0; f < 3; ++f)
             kl_tma_load3(dst + f * KL_PLANE_BYTES, maps[f], gx, gy, gz0 + p, bar);
+        if (xwrap) {
+            // the halo columns of this slot were last written through the
+            // generic proxy; order that before the asynchronous writes
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+#pragma unroll
+            for (int f = 0; f < 3; ++f)
+                kl_tma_load3(dst + 3 * KL_PLANE_BYTES + f * KL_STRIP_BYTES, maps[4 + f],
+                             (int)a.tile_x0 + xs0, gy, gz0 + p, bar);
+        }
     };
     const int p_first = kb - KL_R;
     const int p_last = ke - 1 + KL_R;
     int p_next = p_first;
     if (tid == 0)
         for (; p_next < p_first + KL_NS && p_next <= p_last; ++p_next) issue(p_next);
+    // this thread's share of the halo values: byte offsets in a slot of the
+    // strip source and the halo destination (-1: none)
+    int xw_src[KL_XW_Q], xw_dst[KL_XW_Q];
+#pragma unroll
+    for (int t = 0; t < KL_XW_Q; ++t) {
+        const int q = tid + t * KL_NT;
+        const int f = q / (KL_ROWS * KL_H), rr = (q / KL_H) % KL_ROWS, c = q % KL_H;
+        const int col = need_l ? nx - KL_H + c : c;             // wrapped-to column
+        const bool ok = xwrap && q < 3 * KL_ROWS * KL_H && !(need_r && nx - tx0 + c >= 64 + KL_H);
+        const int lc = need_l ? KL_LPAD - KL_H + c : KL_LPAD + (nx - tx0) + c;
+        xw_src[t] = ok ? 3 * KL_PLANE_BYTES + f * KL_STRIP_BYTES + (rr * KL_XW_W + col - xs0) * (int)sizeof(T) : -1;
+        xw_dst[t] = ok ? f * KL_PLANE_BYTES + (rr * KL_PITCH + lc) * (int)sizeof(T) : -1;
+    }
+    auto xw_copy = [&](unsigned char *slot) {
+#pragma unroll
+        for (int t = 0; t < KL_XW_Q; ++t)
+            if (xw_src[t] >= 0) *(T *)(slot + xw_dst[t]) = *(const T *)(slot + xw_src[t]);
+    };
+    auto slot_of = [&](int p) { return ring + ((p - p_first) % KL_NS) * KL_ZSLOT; };
 
     // coefficients (f32 kernels read the f32 copies; no f64 arithmetic)
     const C dxi = KL_CO(a, 0), dyi = KL_CO(a, 1), nu = KL_CO(a, 4);
@@ -951,7 +1130,12 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
     const int lx = KL_LPAD + 2 * lane;                  // local x of column c0 (even)
     const int c0 = tx0 + 2 * lane;                      // global interior column of c0
 
+#if KL_CS
+    const int grp = (int)threadIdx.y / KL_MBY;           // tendency component of this warp
+    V zb[KL_MPY];
+#else
     V zb[KL_MPY][3];
+#endif
     bool timed_out = false;
     int p_waited = p_first - 1;
 
@@ -960,8 +1144,10 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
     // slot of plane k-R and makes the time-out decision uniform
     {
         bool ok = true;
-        for (int q = p_first; q <= kb + KL_R && ok; ++q)
+        for (int q = p_first; q <= kb + KL_R && ok; ++q) {
             ok = kl_mbar_wait(kl_smem_addr(&bars[(q - p_first) % KL_NS]), ((q - p_first) / KL_NS) & 1);
+            if (ok && xwrap) xw_copy(slot_of(q));
+        }
         timed_out = __syncthreads_or(!ok);
         if (!timed_out) p_waited = kb + KL_R;
     }
@@ -969,10 +1155,18 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
         const char *pl[2 * KL_R + 1];
 #pragma unroll
         for (int d = -KL_R; d <= KL_R; ++d)
-            pl[d + KL_R] = (const char *)(ring + ((k + d - p_first) % KL_NS) * KL_SLOT_BYTES);
+            pl[d + KL_R] = (const char *)(ring + ((k + d - p_first) % KL_NS) * KL_ZSLOT);
 #define KL_Q(f, dk, dx, row) kl_pr<f, dk, dx>(pl, lx, row)
 
         const kl_zmetric Z = kl_make_z(a, k);
+#if KL_CS
+        if (grp == 0)
+            kl_cs_level<0>(a, K, pl, Z, lane, lx, r0, c0, ty0, k, kb, nu, kdx, vkdx, vkdy, vcx, vcy, zb);
+        else if (grp == 1)
+            kl_cs_level<1>(a, K, pl, Z, lane, lx, r0, c0, ty0, k, kb, nu, kdx, vkdx, vkdy, vcx, vcy, zb);
+        else
+            kl_cs_level<2>(a, K, pl, Z, lane, lx, r0, c0, ty0, k, kb, nu, kdx, vkdx, vkdy, vcx, vcy, zb);
+#else
         const V vczu = vsplat(KL_FS * Z.dzi), vczw = vsplat(KL_FS * Z.dzhi);
         const V vkzu_top = vsplat(nu * Z.dzhi_up / KL_FS);   // u, v top face zh_{k+1}
         const V vkzw_top = vsplat(nu * Z.dzi / KL_FS);       // w top face z_k
@@ -1171,11 +1365,13 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
                 }
             }
         }
+#endif  // KL_CS
 #undef KL_Q
         bool ok = true;
         if (k + 1 < ke) {
             const int p = k + 1 + KL_R;
             ok = kl_mbar_wait(kl_smem_addr(&bars[(p - p_first) % KL_NS]), ((p - p_first) / KL_NS) & 1);
+            if (ok && xwrap) xw_copy(slot_of(p));
         }
         if (__syncthreads_or(!ok)) {
             timed_out = true;
@@ -1198,24 +1394,27 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
 }
 
 #if KL_BATCH
-extern "C" __global__ void __launch_bounds__(32 * KL_MBY, KL_MMINB)
+extern "C" __global__ void __launch_bounds__(32 * KL_MBY * (KL_CS ? 3 : 1), KL_MMINB)
 kl_tendency(const kl_args *argv, const int4 *blocks, const kl_tmap *tmaps)
 {
     const int4 d = blocks[blockIdx.x];
     const kl_args a = argv[d.x];
-    const kl_tmap *maps[3] = {&tmaps[4 * d.x], &tmaps[4 * d.x + 1], &tmaps[4 * d.x + 2]};
+    const kl_tmap *maps[7];
+    for (int f = 0; f < 7; ++f) maps[f] = &tmaps[7 * d.x + f];
     if (threadIdx.x == 0 && threadIdx.y == 0)
-        for (int f = 0; f < 3; ++f) kl_tmap_acquire(maps[f]);
+        for (int f = 0; f < 7; ++f)
+            if (f != 3) kl_tmap_acquire(maps[f]);
     kl_zpack_body(a, maps, d.y, d.z, d.w);
 }
 #else
-extern "C" __global__ void __launch_bounds__(32 * KL_MBY, KL_MMINB)
+extern "C" __global__ void __launch_bounds__(32 * KL_MBY * (KL_CS ? 3 : 1), KL_MMINB)
 kl_tendency(const kl_args a, const __grid_constant__ kl_tmap tm_u,
             const __grid_constant__ kl_tmap tm_v, const __grid_constant__ kl_tmap tm_w,
-            const __grid_constant__ kl_tmap tm_n)
+            const __grid_constant__ kl_tmap tm_n, const __grid_constant__ kl_tmap tm_su,
+            const __grid_constant__ kl_tmap tm_sv, const __grid_constant__ kl_tmap tm_sw)
 {
-    (void)tm_n;
-    const kl_tmap *maps[3] = {&tm_u, &tm_v, &tm_w};
+    // tm_su .. tm_sw: the same fields with the 32-byte x-wrap strip box
+    const kl_tmap *maps[7] = {&tm_u, &tm_v, &tm_w, &tm_n, &tm_su, &tm_sv, &tm_sw};
     kl_zpack_body(a, maps, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 #endif

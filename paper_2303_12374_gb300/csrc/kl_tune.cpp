@@ -450,7 +450,7 @@ static bool valid_for(const kl_op &op, const kl_grid &g, int family, int64_t idx
 static std::vector<int> radices(int family)
 {
     if (family == 0) return {5, 5, 5, 3, 3, 3, 2, 2, 2, 2, 2, 2, 6, 6};
-    if (family == 2) return {5, 4, 7, 4, 4, 2};
+    if (family == 2) return {5, 4, 7, 4, 4, 2, 2};
     return {3, 5, 3, 3, 7, 4, 4};
 }
 
@@ -623,13 +623,13 @@ kl_status kl_tune(kl_ctx *ctx, const char *capture_path, const char *opts, const
                     {1, 2, 3, 4, 5, 6}};
         else if (c.family == 2)
             vals = {{1, 2, 4, 8, 16}, {1, 2, 4, 8}, {4, 8, 16, 32, 64, 128, 256}, {8, 9, 10, 12},
-                    {1, 2, 3, 4}, {0, 1}};
+                    {1, 2, 3, 4}, {0, 1}, {0, 1}};
         else
             vals = {{32, 64, 128}, {1, 2, 4, 8, 16}, {1, 2, 4}, {1, 2, 4}, {4, 8, 16, 32, 64, 128, 256},
                     {8, 9, 10, 12}, {1, 2, 3, 4}};
         std::vector<int> cur = c.family == 0
             ? std::vector<int>{c.bx, c.by, c.bz, c.tx, c.ty, c.tz, c.ux, c.uy, c.uz, c.cx, c.cy, c.cz, c.perm, c.minb}
-            : c.family == 2 ? std::vector<int>{c.mby, c.mpy, c.kc, c.ns, c.mminb, c.yx}
+            : c.family == 2 ? std::vector<int>{c.mby, c.mpy, c.kc, c.ns, c.mminb, c.yx, c.cs}
                             : std::vector<int>{c.mbx, c.mby, c.mpx, c.mpy, c.kc, c.ns, c.mminb};
         int64_t y = 0;
         for (size_t p = r.size(); p-- > 0;) {
@@ -831,7 +831,7 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
     struct Item {
         Config cfg;
         KArgs a;
-        CUtensorMap maps[4];
+        CUtensorMap maps[KL_NMAPS];
     };
     std::vector<Item> items((size_t)n);
     std::map<std::string, std::vector<int>> groups;       // compile key -> grids
@@ -881,14 +881,14 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
         }
         size_t nblocks = tiles.size() / 4;
         if (nblocks == 0 || nblocks > 0x7fffffffULL) return fail(KL_ERR_UNSUPPORTED, "batch too large");
-        size_t off_maps = 0, sz_maps = ids.size() * 4 * sizeof(CUtensorMap);
+        size_t off_maps = 0, sz_maps = ids.size() * KL_NMAPS * sizeof(CUtensorMap);
         size_t off_args = (sz_maps + 63) / 64 * 64, sz_args = ids.size() * sizeof(KArgs);
         size_t off_tiles = (off_args + sz_args + 63) / 64 * 64;
         size_t total = off_tiles + tiles.size() * sizeof(int);
         std::vector<char> img(total, 0);
         for (size_t q = 0; q < ids.size(); ++q) {
-            memcpy(img.data() + off_maps + q * 4 * sizeof(CUtensorMap), items[ids[q]].maps,
-                   4 * sizeof(CUtensorMap));
+            memcpy(img.data() + off_maps + q * KL_NMAPS * sizeof(CUtensorMap), items[ids[q]].maps,
+                   KL_NMAPS * sizeof(CUtensorMap));
             memcpy(img.data() + off_args + q * sizeof(KArgs), &items[ids[q]].a, sizeof(KArgs));
         }
         memcpy(img.data() + off_tiles, tiles.data(), tiles.size() * sizeof(int));
@@ -928,7 +928,7 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
                                       (CUstream)s, params, nullptr);
         } else {
             void *params[] = {&argv, &tl, &tm};
-            r = ctx->drv.LaunchKernel(k->fn, (unsigned)nblocks, 1, 1, cfg.mbx, cfg.mby, 1,
+            r = ctx->drv.LaunchKernel(k->fn, (unsigned)nblocks, 1, 1, cfg.mbx, zmarch_block_y(cfg), 1,
                                       (unsigned)k->smem, (CUstream)s, params, nullptr);
         }
         if (r != CUDA_SUCCESS) return cu_fail(r, "cuLaunchKernel (batch)");

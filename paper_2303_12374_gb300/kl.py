@@ -58,6 +58,10 @@ SIGNATURES = {
     "kl_fill_ghosts": ([_P, _I32, ctypes.POINTER(Grid), _P, _P, _P, _P, _P], ctypes.c_int),
     "kl_launch": ([_P, ctypes.POINTER(Op), ctypes.POINTER(Grid), ctypes.POINTER(Fields), _P],
                   ctypes.c_int),
+    "kl_step": ([_P, ctypes.POINTER(Op), ctypes.POINTER(Grid), ctypes.POINTER(Fields), _P],
+                ctypes.c_int),
+    "kl_fill_ghosts_op": ([_P, ctypes.POINTER(Op), ctypes.POINTER(Grid),
+                           ctypes.POINTER(Fields), _P], ctypes.c_int),
     "kl_launch_with_config": ([_P, ctypes.POINTER(Op), _S, ctypes.POINTER(Grid),
                                ctypes.POINTER(Fields), _P], ctypes.c_int),
     "kl_launch_batched": ([_P, ctypes.POINTER(Op), _I32, ctypes.POINTER(Grid),
@@ -144,6 +148,15 @@ def kl_fill_ghosts(ctx, dtype, grid: Grid, u, v, w, nu=None, stream=None) -> Non
 
 def kl_launch(ctx, op: Op, grid: Grid, fields: Fields, stream=None) -> None:
     check(load().kl_launch(ctx, ctypes.byref(op), ctypes.byref(grid), ctypes.byref(fields), stream))
+
+
+def kl_fill_ghosts_op(ctx, op: Op, grid: Grid, fields: Fields, stream=None) -> None:
+    check(load().kl_fill_ghosts_op(ctx, ctypes.byref(op), ctypes.byref(grid), ctypes.byref(fields),
+                                   stream))
+
+
+def kl_step(ctx, op: Op, grid: Grid, fields: Fields, stream=None) -> None:
+    check(load().kl_step(ctx, ctypes.byref(op), ctypes.byref(grid), ctypes.byref(fields), stream))
 
 
 def kl_launch_with_config(ctx, op: Op, config: str, grid: Grid, fields: Fields,

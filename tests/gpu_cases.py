@@ -22,9 +22,21 @@ def make_inputs(nx, ny, nz, *, seed, walls, stretch=0.0, lz=1.0, var_nu=False):
                                  nu0=1e-3 if var_nu else None)
 
 
+def poison_x_ghosts(p, buf):
+    """NaN into the x ghosts of interior rows of interior levels (the cells a
+    kernel that wraps x itself must never read)."""
+    g = p.g
+    pv = p.padded_view(buf)
+    pv[g:g + p.nz, g:g + p.ny, :g] = float("nan")
+    pv[g:g + p.nz, g:g + p.ny, g + p.nx:] = float("nan")
+
+
 def run_gpu(ctx, f, *, adv, diff, dtype, walls, g, config=None, nu=1e-3, stretched=False,
-            accumulate=False, t0=None):
-    """Fill ghosts + tendency through the C ABI; returns (prob, rounded inputs, outputs)."""
+            accumulate=False, t0=None, poison_x=False, step=False):
+    """Fill ghosts + tendency through the C ABI; returns (prob, rounded inputs, outputs).
+
+    poison_x: NaN into the x ghosts of interior rows after the fill (before the
+    launch); step: one kl_step call (its own fill) instead of fill + launch."""
     import torch
     from paper_2303_12374_gb300 import kl
     from paper_2303_12374_gb300.problem import Problem
@@ -38,13 +50,20 @@ def run_gpu(ctx, f, *, adv, diff, dtype, walls, g, config=None, nu=1e-3, stretch
     outs = {}
     for k in ("ut", "vt", "wt"):
         outs[k] = p.upload(t0[k]) if t0 is not None else p.empty()
-    kl.kl_fill_ghosts(ctx, p.dtype, p.grid, bufs["u"].data_ptr(), bufs["v"].data_ptr(),
-                      bufs["w"].data_ptr(), bufs["nu"].data_ptr() if diff == 2 else None)
+    if not step:
+        kl.kl_fill_ghosts(ctx, p.dtype, p.grid, bufs["u"].data_ptr(), bufs["v"].data_ptr(),
+                          bufs["w"].data_ptr(), bufs["nu"].data_ptr() if diff == 2 else None)
+    if poison_x:
+        for k in ("u", "v", "w"):
+            poison_x_ghosts(p, bufs[k])
     op = kl.Op(adv, diff, p.dtype, 1 if accumulate else 0)
     fl = kl.Fields(bufs["u"].data_ptr(), bufs["v"].data_ptr(), bufs["w"].data_ptr(),
                    bufs["nu"].data_ptr() if diff == 2 else None, outs["ut"].data_ptr(),
                    outs["vt"].data_ptr(), outs["wt"].data_ptr())
-    if config is None:
+    if step:
+        assert config is None
+        kl.kl_step(ctx, op, p.grid, fl)
+    elif config is None:
         kl.kl_launch(ctx, op, p.grid, fl)
     else:
         kl.kl_launch_with_config(ctx, op, config, p.grid, fl)

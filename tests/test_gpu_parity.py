@@ -28,6 +28,10 @@ CONFIGS_DIRECT = [
     "zpack:w=2,ly=1,kc=4,ns=12,minb=2",
     "zpack:w=8,ly=1,kc=8,ns=8,minb=2,yx=1",
     "zpack:w=4,ly=2,kc=16,ns=9,minb=1,yx=1",
+    "zpack:w=4,ly=2,kc=16,ns=8,minb=2,cs=1",
+    "zpack:w=2,ly=4,kc=8,ns=9,minb=1,cs=1",
+    "zpack:w=1,ly=1,kc=4,ns=8,minb=1,cs=1",
+    "zpack:w=8,ly=2,kc=32,ns=10,minb=1,cs=1",
 ]
 
 
@@ -91,14 +95,62 @@ def test_tendency_parity_configs(ctx, oracle_mod, config, dtype):
         except kl.KLError:
             continue
         ran += 1
+        # the zpack family wraps x itself: NaN in the memory x ghosts must not matter
         p, _, outs, rin = run_gpu(ctx, f, adv=adv, diff=diff, dtype=dtype, walls=True, g=3,
-                                  stretched=True, config=config)
+                                  stretched=True, config=config,
+                                  poison_x=config.startswith("zpack"))
         ref = oracle_ref(oracle_mod, rin, f["zh"], adv=adv, diff=diff, walls=True, g=3)
         for name, r in zip(("ut", "vt", "wt"), ref):
             e = rel_err(p.download(outs[name]), r)
             assert e <= TOL[dtype], (config, adv, diff, name, e)
     if ran == 0:
         pytest.skip("configuration outside the space for this storage type")
+
+
+@pytest.mark.parametrize("dtype", [0, 1, 3])
+@pytest.mark.parametrize("walls,adv,diff", [(True, 5, 1), (False, 2, 1), (False, 5, 0)])
+def test_component_split_is_bit_identical(ctx, dtype, walls, adv, diff):
+    """cs=1 forms the same faces with the same expressions as cs=0, one warp
+    group per component, so the two give identical bits."""
+    f = make_inputs(70, 45, 23, seed=8, walls=walls, stretch=2.0)
+    res = []
+    for cs in (0, 1):
+        cfg = f"zpack:w=2,ly=2,kc=8,ns=8,minb=1,cs={cs}"
+        p, _, outs, _ = run_gpu(ctx, f, adv=adv, diff=diff, dtype=dtype, walls=walls,
+                                g=3 if adv == 5 else 1, stretched=True, config=cfg)
+        res.append([p.download(outs[k]) for k in ("ut", "vt", "wt")])
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("dtype", [0, 1, 3])
+@pytest.mark.parametrize("nx,ny,nz,walls,adv", [
+    (67, 20, 9, True, 5),     # narrowest grid the kernel wraps itself (64 + 3)
+    (128, 12, 7, False, 5),   # the right halo lies in the last tile
+    (130, 9, 6, True, 2),     # three tiles, second-order halo (wraps from 65)
+    (199, 11, 6, False, 5),   # ragged last tile
+    (40, 20, 9, True, 5),     # narrower: one tile, x ghosts read from memory
+    (65, 12, 7, False, 5),
+])
+def test_zpack_x_wrap_in_kernel(ctx, oracle_mod, dtype, nx, ny, nz, walls, adv):
+    """On grids with nx >= 64 + H, zpack forms the periodic x halo from interior
+    columns: with NaN in every x ghost of the interior rows the tendencies still
+    match the oracle.  Narrower grids read the filled x ghosts."""
+    from paper_2303_12374_gb300 import kl
+    g = 3 if adv == 5 else 1
+    wraps = nx >= 64 + g
+    f = make_inputs(nx, ny, nz, seed=nx + ny, walls=walls, stretch=2.0)
+    for cfg in ("zpack:w=2,ly=2,kc=4,ns=8,minb=1", "zpack:w=4,ly=2,kc=16,ns=9,minb=1,cs=1"):
+        try:
+            kl.kl_config_normalize(kl.Op(adv, 1, dtype, 0), cfg)
+        except kl.KLError:
+            continue
+        p, _, outs, rin = run_gpu(ctx, f, adv=adv, diff=1, dtype=dtype, walls=walls, g=g,
+                                  stretched=True, config=cfg, poison_x=wraps)
+        ref = oracle_ref(oracle_mod, rin, f["zh"], adv=adv, diff=1, walls=walls, g=g)
+        for name, r in zip(("ut", "vt", "wt"), ref):
+            e = rel_err(p.download(outs[name]), r)
+            assert e <= TOL[dtype], (cfg, name, e)
 
 
 def test_accumulate(ctx, oracle_mod):

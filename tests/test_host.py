@@ -74,7 +74,11 @@ def test_default_config_is_table2_default():
 
 @pytest.mark.parametrize("bad", ["direct:bx=512", "direct:bx=256,by=8",  # > 1024 threads
                                  "direct:tx=3", "direct:perm=ABC", "direct:minb=7",
-                                 "direct:foo=1", "nosuch:bx=1", "direct:bx"])
+                                 "direct:foo=1", "nosuch:bx=1", "direct:bx",
+                                 "zpack:w=4,ly=2,cs=1,yx=1",       # cs forms its own y faces
+                                 "zpack:w=16,ly=1,cs=1",           # 1536 threads per block
+                                 "zpack:w=8,ly=1,cs=1,minb=3",     # 2304 threads per SM
+                                 "zpack:w=4,ly=2,cs=2"])
 def test_invalid_configs_are_rejected(bad):
     with pytest.raises(kl.KLError) as e:
         kl.kl_config_normalize(kl.Op(5, 1, 1, 0), bad)
@@ -96,6 +100,10 @@ def test_nvrtc_compiles_tiled_configs():
         log = kl.kl_compile_only(op, cfg, 0, 1)
         m = re.search(r"(\d+) bytes spill stores", log)
         assert m is not None
+    # zpack, all components per thread and one warp group per component
+    for cfg in ["zpack:w=4,ly=2,kc=16,ns=8,minb=2", "zpack:w=4,ly=2,kc=16,ns=8,minb=2,cs=1"]:
+        log = kl.kl_compile_only(kl.Op(5, 1, 1, 0), cfg, 1, 1)
+        assert re.search(r"(\d+) bytes spill stores", log) is not None
 
 
 def test_nvrtc_failure_is_reported():
