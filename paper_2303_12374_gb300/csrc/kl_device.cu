@@ -12,99 +12,143 @@ namespace {
 
 // ------------------------------------------------------------ ghost fill
 //
-// Ghost points form three disjoint groups laid end to end in one linear cell
-// index: the 2g full z planes (x and y ghosts included), the 2g y rows of
-// every interior level (x ghosts included), and the 2g x points of every
-// interior row.  Each ghost maps straight to an interior source point, axis by
-// axis, so one launch fills faces, edges and corners with no ordering between
-// them (no source is ever a ghost).  The copy moves raw bits; the odd (w)
-// mirror flips the sign bit, which negates exactly in every format.
+// Ghost points form three disjoint groups: the 2g full z planes (x and y
+// ghosts included), the 2g y rows of every interior level (x ghosts
+// included), and the 2g x points of every interior row.  Each ghost maps
+// straight to an interior source point, axis by axis, so one launch fills
+// faces, edges and corners with no ordering between them (no source is ever a
+// ghost).  The copy moves raw bits; the odd (w) mirror flips the sign bit,
+// which negates exactly in every format.
 //
-// A block covers FILL_U x 256 consecutive cells; each thread issues the loads
-// of its FILL_U cells (all fields) before any store, so a thread keeps up to
-// 4 x FILL_U loads in flight, and consecutive lanes touch consecutive cells.
+// The first blocks take the rows of the first two groups, one padded row per
+// warp: the row's source row is found once, and the lanes sweep x with
+// FILL_RU cells each in flight (all loads before any store).  The last blocks
+// take the x ghosts of interior rows through one linear cell index, FILL_U
+// cells per thread.
 
-constexpr int FILL_T = 256, FILL_U = 4;
+constexpr int FILL_T = 256, FILL_W = FILL_T / 32, FILL_RU = 3, FILL_U = 4;
 
 struct FillArgs {
     char *f[4];              // u, v, w, nu at interior (0,0,0); nu may be NULL
     long long sj, sk;
     int nx, ny, nz, zbc;
-    unsigned px, py;         // padded row length, padded rows per plane
-    unsigned n0, n1, n2;     // cell index ends of the z-plane, y-row and x groups
+    int rows_z, rows_y;      // rows of the z-plane group (2g x padded ny), y-row group (2g x nz)
+    int nb_rows;             // blocks of the row groups
+    unsigned n_x;            // cells of the x group (0: not filled)
 };
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-template <int G>
-__device__ __forceinline__ void fill_decode(const FillArgs &a, unsigned q, int &i, int &j, int &k)
+// source levels of ghost level k: even mirror / periodic (ske), odd mirror (sko)
+__device__ __forceinline__ void fill_levels(const FillArgs &a, int k, int &ske, int &sko,
+                                            bool &wzero, bool &wneg)
 {
-    if (q < a.n0) {                        // full z planes: px points x py rows x 2G planes
-        unsigned r = q / a.px, p = r / a.py;
-        i = (int)(q - r * a.px) - G;
-        j = (int)(r - p * a.py) - G;
-        k = p < (unsigned)G ? (int)p - G : a.nz + ((int)p - G);
-    } else if (q < a.n1) {                 // y rows: px points x 2G rows x nz levels
-        unsigned t = q - a.n0, r = t / a.px, kk = r / (2 * G), qq = r - kk * (2 * G);
-        i = (int)(t - r * a.px) - G;
-        j = qq < (unsigned)G ? (int)qq - G : a.ny + ((int)qq - G);
-        k = (int)kk;
-    } else {                               // x ghosts: 2G points x ny rows x nz levels
-        unsigned t = q - a.n1, r = t / (2 * G), qq = t - r * (2 * G), kk = r / (unsigned)a.ny;
-        i = qq < (unsigned)G ? (int)qq - G : a.nx + ((int)qq - G);
-        j = (int)(r - kk * (unsigned)a.ny);
-        k = (int)kk;
+    if (a.zbc == 0) {
+        ske = sko = wrapi(k, a.nz);
+        wzero = wneg = false;
+    } else {
+        ske = k < 0 ? -1 - k : (k >= a.nz ? 2 * a.nz - 1 - k : k);
+        sko = k < 0 ? -k : (k > a.nz ? 2 * a.nz - k : k);
+        wzero = k == a.nz;
+        wneg = k < 0 || k > a.nz;
+    }
+}
+
+template <typename B>
+__device__ __forceinline__ B fill_w(B v, bool wzero, bool wneg)
+{
+    const B sign_bit = (B)1 << (sizeof(B) * 8 - 1);
+    return wzero ? (B)0 : (wneg ? (B)(v ^ sign_bit) : v);
+}
+
+// one padded row (x in [-G, nx + G)) at (j, k), by one warp
+template <typename B, int G>
+__device__ __forceinline__ void fill_row(const FillArgs &a, int j, int k, int lane)
+{
+    int ske, sko;
+    bool wzero, wneg;
+    fill_levels(a, k, ske, sko, wzero, wneg);
+    const long long sj = wrapi(j, a.ny);
+    const long long dst0 = j * a.sj + k * a.sk;
+    const long long src0 = sj * a.sj + ske * a.sk, srcw0 = sj * a.sj + sko * a.sk;
+    for (int i0 = -G; i0 < a.nx + G; i0 += 32 * FILL_RU) {
+        B val[FILL_RU][4];
+#pragma unroll
+        for (int c = 0; c < FILL_RU; ++c) {
+            const int i = i0 + lane + 32 * c;
+            if (i >= a.nx + G) continue;
+            const int si = wrapi(i, a.nx);
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                if (f != 2 && !a.f[f]) continue;
+                const B *p = (const B *)a.f[f];
+                if (f != 2) val[c][f] = p[src0 + si];
+                else if (!wzero) val[c][f] = p[srcw0 + si];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < FILL_RU; ++c) {
+            const int i = i0 + lane + 32 * c;
+            if (i >= a.nx + G) continue;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                if (f != 2 && !a.f[f]) continue;
+                ((B *)a.f[f])[dst0 + i] = f != 2 ? val[c][f] : fill_w<B>(val[c][f], wzero, wneg);
+            }
+        }
     }
 }
 
 template <typename B, int G>
 __global__ void __launch_bounds__(FILL_T) fill_kernel(FillArgs a)
 {
-    const B sign_bit = (B)1 << (sizeof(B) * 8 - 1);
+    if ((int)blockIdx.x < a.nb_rows) {
+        // row groups: warp -> row task r
+        const int r = (int)blockIdx.x * FILL_W + (int)(threadIdx.x >> 5);
+        if (r >= a.rows_z + a.rows_y) return;
+        int j, k;
+        if (r < a.rows_z) {                // z planes: 2G planes of ny + 2G rows
+            const int py = a.ny + 2 * G, p = r / py;
+            j = r - p * py - G;
+            k = p < G ? p - G : a.nz + (p - G);
+        } else {                           // y rows: 2G rows of every interior level
+            const int t = r - a.rows_z, kk = t / (2 * G), qq = t - kk * (2 * G);
+            j = qq < G ? qq - G : a.ny + (qq - G);
+            k = kk;
+        }
+        fill_row<B, G>(a, j, k, (int)(threadIdx.x & 31));
+        return;
+    }
+    // x ghosts of interior rows: 2G points x ny rows x nz levels, linear
+    const unsigned base = ((unsigned)blockIdx.x - a.nb_rows) * (unsigned)(FILL_T * FILL_U) + threadIdx.x;
     long long dst[FILL_U], src[FILL_U], srcw[FILL_U];
-    bool live[FILL_U], wzero[FILL_U], wneg[FILL_U];
-    const unsigned base = blockIdx.x * (unsigned)(FILL_T * FILL_U) + threadIdx.x;
+    bool live[FILL_U];
 #pragma unroll
     for (int c = 0; c < FILL_U; ++c) {
         const unsigned q = base + c * FILL_T;
-        live[c] = q < a.n2;
-        int i = 0, j = 0, k = 0;
-        if (live[c]) fill_decode<G>(a, q, i, j, k);
-        const int si = wrapi(i, a.nx), sj = wrapi(j, a.ny);
-        int ske, sko;
-        if (a.zbc == 0) {
-            ske = sko = wrapi(k, a.nz);
-        } else {
-            ske = k < 0 ? -1 - k : (k >= a.nz ? 2 * a.nz - 1 - k : k);
-            sko = k < 0 ? -k : (k > a.nz ? 2 * a.nz - k : k);
-        }
+        live[c] = q < a.n_x;
+        const unsigned rr = q / (2 * G), qq = q - rr * (2 * G), kk = live[c] ? rr / (unsigned)a.ny : 0;
+        const int i = qq < (unsigned)G ? (int)qq - G : a.nx + ((int)qq - G);
+        const int j = (int)(rr - kk * (unsigned)a.ny), k = (int)kk;
+        const int si = wrapi(i, a.nx);
         dst[c] = i + j * a.sj + k * a.sk;
-        src[c] = si + sj * a.sj + (long long)ske * a.sk;
-        srcw[c] = si + sj * a.sj + (long long)sko * a.sk;
-        wzero[c] = a.zbc != 0 && k == a.nz;
-        wneg[c] = a.zbc != 0 && (k < 0 || k > a.nz);
+        src[c] = si + j * a.sj + k * a.sk;       // interior row: only x wraps
+        srcw[c] = src[c];
     }
     B val[FILL_U][4];
 #pragma unroll
     for (int c = 0; c < FILL_U; ++c) {
         if (!live[c]) continue;
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            if (f != 2 && !a.f[f]) continue;
-            const B *p = (const B *)a.f[f];
-            if (f != 2) val[c][f] = p[src[c]];
-            else if (!wzero[c]) val[c][f] = p[srcw[c]];
-        }
+        for (int f = 0; f < 4; ++f)
+            if (f == 2 || a.f[f]) val[c][f] = ((const B *)a.f[f])[f == 2 ? srcw[c] : src[c]];
     }
 #pragma unroll
     for (int c = 0; c < FILL_U; ++c) {
         if (!live[c]) continue;
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            if (f != 2 && !a.f[f]) continue;
-            B v = f != 2 ? val[c][f] : (wzero[c] ? (B)0 : (wneg[c] ? (B)(val[c][f] ^ sign_bit) : val[c][f]));
-            ((B *)a.f[f])[dst[c]] = v;
-        }
+        for (int f = 0; f < 4; ++f)
+            if (f == 2 || a.f[f]) ((B *)a.f[f])[dst[c]] = val[c][f];
     }
 }
 
@@ -232,18 +276,19 @@ cudaError_t fill_ghosts_launch(int esize, const kl_grid &g, void *u, void *v, vo
     a.ny = g.ny;
     a.nz = g.nz;
     a.zbc = g.zbc;
-    long long px = g.nx + 2LL * g.g, py = g.ny + 2LL * g.g;
-    long long n0 = px * py * 2 * g.g;
-    long long n1 = n0 + px * 2 * g.g * g.nz;
-    long long n2 = x_ghosts ? n1 + 2LL * g.g * g.ny * g.nz : n1;
-    // 32-bit cell indices, and the last block's FILL_U x FILL_T cells too
-    if (n2 + FILL_T * FILL_U > 0x7fffffffLL) return cudaErrorInvalidValue;
-    a.px = (unsigned)px;
-    a.py = (unsigned)py;
-    a.n0 = (unsigned)n0;
-    a.n1 = (unsigned)n1;
-    a.n2 = (unsigned)n2;
-    unsigned grid = (unsigned)((n2 + FILL_T * FILL_U - 1) / (FILL_T * FILL_U));
+    long long rows_z = 2LL * g.g * (g.ny + 2LL * g.g), rows_y = 2LL * g.g * g.nz;
+    long long n_x = x_ghosts ? 2LL * g.g * g.ny * g.nz : 0;
+    long long nb_rows = (rows_z + rows_y + FILL_W - 1) / FILL_W;
+    long long nb_x = (n_x + FILL_T * FILL_U - 1) / (FILL_T * FILL_U);
+    // 32-bit row and cell indices (the last x block's cells included)
+    if (rows_z + rows_y > 0x7fffffffLL || n_x + FILL_T * FILL_U > 0xffffffffLL ||
+        nb_rows + nb_x > 0x7fffffffLL)
+        return cudaErrorInvalidValue;
+    a.rows_z = (int)rows_z;
+    a.rows_y = (int)rows_y;
+    a.nb_rows = (int)nb_rows;
+    a.n_x = (unsigned)n_x;
+    unsigned grid = (unsigned)(nb_rows + nb_x);
     if (esize == 8) return fill_dispatch<unsigned long long>(g.g, grid, a, s);
     if (esize == 4) return fill_dispatch<unsigned int>(g.g, grid, a, s);
     return fill_dispatch<unsigned short>(g.g, grid, a, s);
