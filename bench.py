@@ -27,6 +27,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -35,6 +37,7 @@ WORKLOAD = "walls256_adv5_diff"
 NX = NY = NZ = 256
 G = 3
 NU = 1e-3
+REF_SECONDS = 120.0      # reference arm: CPU time of warm-up + timed samples
 
 
 def kernel_source_hash() -> str:
@@ -55,7 +58,10 @@ def parse():
     return ap.parse_args()
 
 
-def dist_init(n):
+def dist_init(n, backend=None):
+    """(rank, local rank, world) from the torchrun environment; joins the
+    process group when world > 1 (NCCL on the GPUs; `backend` overrides, e.g.
+    gloo for the CPU tests of this path)."""
     import torch
     import torch.distributed as dist
     if n > 1 or "RANK" in os.environ:
@@ -63,10 +69,30 @@ def dist_init(n):
         local = int(os.environ.get("LOCAL_RANK", 0))
         world = int(os.environ.get("WORLD_SIZE", 1))
         if world > 1:
-            torch.cuda.set_device(local)
-            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+            if backend is None:
+                torch.cuda.set_device(local)
+                dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+            else:
+                dist.init_process_group(backend)
         return rank, local, world
     return 0, 0, 1
+
+
+def max_over_ranks(x, world, device):
+    """The maximum of a per-rank scalar over all ranks (the job's time)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, pts, steps, total_ms):
+    """Whole-job throughput in Gpts/s: every rank steps its own replica of the
+    grid (weak scaling), the job takes the slowest rank's time."""
+    return world * pts * steps / (total_ms * 1e-3) / 1e9
 
 
 def measured_peaks():
@@ -176,27 +202,104 @@ def time_steps(ctx, p, ins, outs, op, config, steps, warmup, stream, per_kernel=
     return total, kern
 
 
-def cpu_baseline(seconds_target):
-    """The FP64 oracle as it stands on a bounded sample (z levels) of the workload."""
-    import oracle
-    from paper_2303_12374_gb300 import synth
-    oracle.build()
-    spec = synth.WORKLOADS[WORKLOAD]
-    f = synth.velocity_fields(NX, NY, NZ, seed=synth.seed_of(spec["index"]), walls=True)
-    # probe with 2 levels, then size the sample to about seconds_target
-    t = time.perf_counter()
-    oracle.tendencies(f["u"], f["v"], f["w"], adv=5, diff=1, g=G, walls=True, dx=1 / NX,
-                      dy=1 / NY, zh=f["zh"], nu=NU, levels=(0, 2))
-    probe = time.perf_counter() - t
-    levels = max(2, min(NZ, int(seconds_target / max(probe / 2, 1e-6))))
-    t = time.perf_counter()
-    oracle.tendencies(f["u"], f["v"], f["w"], adv=5, diff=1, g=G, walls=True, dx=1 / NX,
-                      dy=1 / NY, zh=f["zh"], nu=NU, levels=(0, levels))
-    dt = time.perf_counter() - t
+class OracleSample:
+    """The FP64 oracle as it stands, timed on z levels of the bench workload.
+
+    Levels [k0, k0 + L) with 3 <= k0 and k0 + L <= nz - 3 are computed from a
+    slab of the fields with the stencil's 3-level reach on each side, so only
+    the slab is padded; the result is the full grid's on those levels."""
+
+    def __init__(self):
+        import oracle
+        from paper_2303_12374_gb300 import synth
+        oracle.build()
+        self.oracle, self.synth = oracle, synth
+        spec = synth.WORKLOADS[WORKLOAD]
+        self.f = synth.velocity_fields(NX, NY, NZ, seed=synth.seed_of(spec["index"]), walls=True)
+
+    def run(self, k0, nlev):
+        """Seconds the oracle takes for interior levels [k0, k0 + nlev)."""
+        assert G <= k0 and k0 + nlev <= NZ - G
+        lo, hi = k0 - G, k0 + nlev + G
+        sl = {k: np.ascontiguousarray(self.f[k][lo:hi]) for k in ("u", "v", "w")}
+        zh = self.synth.zfaces(hi - lo, (hi - lo) / NZ)
+        t = time.perf_counter()
+        self.oracle.tendencies(sl["u"], sl["v"], sl["w"], adv=5, diff=1, g=G, walls=False,
+                               dx=1 / NX, dy=1 / NY, zh=zh, nu=NU, levels=(G, G + nlev))
+        return time.perf_counter() - t
+
+
+def cpu_baseline(seconds_target, sampler=None):
+    """The oracle on a bounded sample (about seconds_target) of the workload."""
+    sampler = sampler or OracleSample()
+    per_level = sampler.run(G, 2) / 2
+    levels = max(2, min(NZ - 2 * G, int(seconds_target / max(per_level, 1e-6))))
+    dt = sampler.run(G, levels)
     pts = NX * NY * levels
     return {"value": pts / dt / 1e9, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
-            "sample": f"levels 0..{levels - 1} of the 256^3 grid ({pts} points, FP64, "
-                      f"single thread, {dt:.1f} s incl. ghost padding)"}, dt
+            "sample": f"levels {G}..{G + levels - 1} of the 256^3 grid ({pts} points, FP64, "
+                      f"single thread, {dt:.1f} s incl. padding of the slab)"}, dt
+
+
+def e2e_run(ctx, p, f, op, device, steps, overlap=True):
+    """Steps from host data to host results through the public API.
+
+    Every step copies the interior of u, v, w from pinned host memory into the
+    padded device buffers, runs kl_step (ghost fill + tendencies) and copies
+    the interior of ut, vt, wt back to pinned host memory.  overlap=True runs
+    the three stages of consecutive steps on three streams with two device
+    buffer sets (step i's copy-in overlaps step i-1's kernels and step i-2's
+    copy-out); overlap=False runs them one after the other on one stream.
+    Returns (ms per step, bytes copied per direction per step)."""
+    import torch
+    from paper_2303_12374_gb300 import kl
+    host_in = [torch.from_numpy(np.ascontiguousarray(f[k])).to(p.tdtype).pin_memory()
+               for k in ("u", "v", "w")]
+    host_out = [torch.empty((p.nz, p.ny, p.nx), dtype=p.tdtype).pin_memory() for _ in range(3)]
+    nbuf = 2 if overlap else 1
+    dev_in = [[p.empty() for _ in range(3)] for _ in range(nbuf)]
+    dev_out = [[p.empty() for _ in range(3)] for _ in range(nbuf)]
+    fields = [kl.Fields(*[t.data_ptr() for t in dev_in[b]], None,
+                        *[t.data_ptr() for t in dev_out[b]]) for b in range(nbuf)]
+    if overlap:
+        s_in, s_c, s_out = (torch.cuda.Stream(device) for _ in range(3))
+    else:
+        s_in = s_c = s_out = torch.cuda.Stream(device)
+    ev_in = [torch.cuda.Event() for _ in range(nbuf)]
+    ev_c = [torch.cuda.Event() for _ in range(nbuf)]
+    ev_out = [torch.cuda.Event() for _ in range(nbuf)]
+
+    def issue(i):
+        b = i % nbuf
+        with torch.cuda.stream(s_in):
+            if i >= nbuf:
+                s_in.wait_event(ev_c[b])        # step i - nbuf's kernels read dev_in[b]
+            for h, d in zip(host_in, dev_in[b]):
+                p.view(d).copy_(h, non_blocking=True)
+            ev_in[b].record(s_in)
+        with torch.cuda.stream(s_c):
+            s_c.wait_event(ev_in[b])
+            if i >= nbuf:
+                s_c.wait_event(ev_out[b])       # step i - nbuf's results left dev_out[b]
+            kl.kl_step(ctx, op, p.grid, fields[b], s_c.cuda_stream)
+            ev_c[b].record(s_c)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(ev_c[b])
+            for h, d in zip(host_out, dev_out[b]):
+                h.copy_(p.view(d), non_blocking=True)
+            ev_out[b].record(s_out)
+
+    for i in range(2 * nbuf):                   # warm-up (allocator, module, pinned paths)
+        issue(i)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s_in)
+    for i in range(steps):
+        issue(i)
+    b.record(s_out)
+    torch.cuda.synchronize()
+    es = host_in[0].element_size()
+    return a.elapsed_time(b) / steps, 3 * p.nx * p.ny * p.nz * es
 
 
 def precision_sweep(ctx, f, device, stream, reps):
@@ -222,6 +325,56 @@ def precision_sweep(ctx, f, device, stream, reps):
         row["speedup"] = row["default"]["kernel_us"] / row["tuned"]["kernel_us"]
         out[name] = row
         del ins, outs
+        torch.cuda.empty_cache()
+    return out
+
+
+def workload_sweep(ctx, device, stream, reps):
+    """Kernel time, tuned (wisdom) vs default, on the other seeded workloads:
+    64^3 periodic 2nd order f64, 512x512x256 walls f32, 1024x1024x64 stretched
+    with variable nu f32 (ghosts filled once, then kernel launches only)."""
+    import torch
+    from paper_2303_12374_gb300 import kl, synth
+    from paper_2303_12374_gb300.tune_cli import build_problem
+    out = {}
+    for wl, dt in (("periodic64_adv2_f64", "f64"), ("walls512x512x256_precision", "f32"),
+                   ("les1024x1024x64_stretched_varnu", "f32")):
+        p, op, bufs, outs, fl = build_problem(wl, dt)
+        spec = synth.WORKLOADS[wl]
+        pts = p.nx * p.ny * p.nz
+        es = {0: 8, 1: 4, 2: 2, 3: 2}[p.dtype]
+        nbytes = (6 + (1 if spec["diff"] == 2 else 0)) * es * pts
+        sp = stream.cuda_stream
+        with torch.cuda.stream(stream):
+            kl.kl_fill_ghosts(ctx, p.dtype, p.grid, bufs["u"].data_ptr(), bufs["v"].data_ptr(),
+                              bufs["w"].data_ptr(), bufs["nu"].data_ptr() if "nu" in bufs else None,
+                              sp)
+            row = {"grid": f"{p.nx}x{p.ny}x{p.nz}", "dtype": dt, "points": pts,
+                   "alg_bytes": nbytes}
+            for label, cfg in (("tuned", None), ("default", "default")):
+                def launch():
+                    if cfg is None:
+                        kl.kl_launch(ctx, op, p.grid, fl, sp)
+                    else:
+                        kl.kl_launch_with_config(ctx, op, cfg, p.grid, fl, sp)
+                for _ in range(3):
+                    launch()
+                torch.cuda.synchronize()
+                n = max(3, reps * 16_777_216 // pts) if dt != "f64" else max(10, reps)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(n):
+                    launch()
+                b.record(stream)
+                torch.cuda.synchronize()
+                us = a.elapsed_time(b) / n * 1e3
+                row[label] = {"kernel_us": us, "gpts": pts / us / 1e3,
+                              "hbm_gbs": nbytes / us / 1e3}
+                if cfg is None:
+                    row[label]["config"] = json.loads(kl.kl_stats(ctx))["last_config"]
+            row["speedup"] = row["default"]["kernel_us"] / row["tuned"]["kernel_us"]
+        out[wl] = row
+        del bufs, outs
         torch.cuda.empty_cache()
     return out
 
@@ -310,19 +463,27 @@ def launch_overhead(local, wisdom, device, calls=1000):
 
 
 def run_reference(args):
+    """The reference arm: the oracle on the host cores, each step a sample of
+    z levels of the workload sized so that warm-up plus timed steps take about
+    REF_SECONDS (one level at least); rank 0 only."""
     rank = int(os.environ.get("RANK", 0))
     if rank != 0:
         return
-    per_step = max(1.0, args.cpu_seconds / max(1, args.steps))
-    vals = []
-    cb = None
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        pass
+    sampler = OracleSample()
+    per_level = sampler.run(G, 2) / 2
+    nsamp = max(1, args.steps + args.warmup)
+    nlev = max(1, min(NZ - 2 * G, int(REF_SECONDS / nsamp / max(per_level, 1e-6))))
+    span = NZ - 2 * G - nlev + 1
+    for s in range(args.warmup):
+        sampler.run(G + (s * nlev) % span, nlev)
+    total = 0.0
     for s in range(args.steps):
-        cb, dt = cpu_baseline(per_step)
-        vals.append(cb["value"])
-    value = statistics.fmean(vals)
-    cb["value"] = value
+        total += sampler.run(G + (s * nlev) % span, nlev)
+    pts = NX * NY * nlev * args.steps
+    value = pts / total / 1e9
+    cb = {"value": value, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
+          "sample": f"{args.steps} steps of {nlev} z level(s) of the 256^3 grid each "
+                    f"({pts} points, FP64, single thread, {total:.1f} s)"}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gpts/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": NX * NY * NZ / (value * 1e9) * 1e3, "higher_is_better": True,
@@ -366,14 +527,11 @@ def main():
         total_ms, kern_ms = time_steps(ctx, p, ins, outs, op, None, args.steps, args.warmup,
                                        stream)
     barrier()
-    if world > 1:
-        t = torch.tensor([total_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, device)
     stats = json.loads(kl.kl_stats(ctx))
     tuned_cfg = stats["last_config"]
     ms_step = total_ms / args.steps
-    value = world * pts * args.steps / (total_ms * 1e-3) / 1e9
+    value = job_value(world, pts, args.steps, total_ms)
 
     peaks = measured_peaks()
     peak_gbs = peaks.get("hbm_gbs") or 6800.0
@@ -400,38 +558,23 @@ def main():
                                   "speedup_vs_default": d_kern / kern_ms}
         extras["precision"] = precision_sweep(ctx, f, device, stream, max(20, args.steps // 20))
         extras["batched"] = batched_run(ctx, device, stream)
+        extras["workloads"] = workload_sweep(ctx, device, stream, max(20, args.steps // 20))
         extras["launch_overhead"] = launch_overhead(local, wisdom, device)
 
-    # --- end to end through the public API with pinned host buffers
-    e2e = None
-    if rank == 0:
-        host_in = [torch.empty(p.extent, dtype=p.tdtype, pin_memory=True) for _ in range(3)]
-        host_out = [torch.empty(p.extent, dtype=p.tdtype, pin_memory=True) for _ in range(3)]
-        for h, d in zip(host_in, ins):
-            h.copy_(d)
-        fl = kl.Fields(*[t.data_ptr() for t in ins], None, *[t.data_ptr() for t in outs])
-        ke = max(5, args.steps // 100)
-        with torch.cuda.stream(stream):
-            def e2e_step():
-                for h, d in zip(host_in, ins):
-                    d.copy_(h, non_blocking=True)
-                kl.kl_step(ctx, op, p.grid, fl, stream.cuda_stream)
-                for h, d in zip(host_out, outs):
-                    h.copy_(d, non_blocking=True)
-            for _ in range(2):
-                e2e_step()
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            for _ in range(ke):
-                e2e_step()
-            b.record(stream)
-            torch.cuda.synchronize()
-        e_ms = a.elapsed_time(b) / ke
-        nbytes = 3 * p.extent * es
-        e2e = {"value": pts / (e_ms * 1e-3) / 1e9, "unit": "Gpts/s",
-               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-               "ms_per_step": e_ms}
+    # --- end to end through the public API with pinned host buffers (every rank)
+    barrier()
+    e_ms, e_bytes = e2e_run(ctx, p, f, op, device, max(10, args.steps // 50), overlap=True)
+    s_ms, _ = e2e_run(ctx, p, f, op, device, max(5, args.steps // 200), overlap=False)
+    barrier()
+    e_ms = max_over_ranks(e_ms, world, device)
+    s_ms = max_over_ranks(s_ms, world, device)
+    e2e = {"value": job_value(world, pts, 1, e_ms), "unit": "Gpts/s",
+           "h2d_bytes_per_step": e_bytes, "d2h_bytes_per_step": e_bytes,
+           "ms_per_step": e_ms,
+           "api": "kl_step; torch copies of the interior u, v, w in and ut, vt, wt out",
+           "pipeline": "copy-in, kl_step and copy-out of consecutive steps overlap on three "
+                       "streams (two device buffer sets)",
+           "serial": {"value": job_value(world, pts, 1, s_ms), "ms_per_step": s_ms}}
 
     cb = None
     if rank == 0 and world == 1:

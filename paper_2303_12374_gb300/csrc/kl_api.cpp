@@ -539,6 +539,8 @@ void kl_destroy(kl_ctx *c)
         cudaFree(p.second.d32);
     }
     for (auto &p : c->tables) cudaFree(p.second.first);
+    for (cudaStream_t st : c->aux_streams) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : c->aux_events) cudaEventDestroy(ev);
     cudaFree(c->d_err);
     cudaFree(c->d_scratch);
     if (c->h_out) cudaFreeHost(c->h_out);

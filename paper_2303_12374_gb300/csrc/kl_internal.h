@@ -169,6 +169,10 @@ struct kl_ctx {
     // tile tables of batched launches, keyed by the batch signature
     std::map<std::string, std::pair<void *, size_t>> tables;
     std::map<std::string, CUtensorMap> tmaps;         // TMA descriptors per buffer/box
+    // streams that run the configuration classes of one batched call side by
+    // side (forked from and joined back into the caller's stream)
+    std::vector<cudaStream_t> aux_streams;
+    std::vector<cudaEvent_t> aux_events;              // [0] fork, [1 + i] join of stream i
     // statistics
     long long launches = 0, cache_hits = 0, cache_misses = 0;
     double t_wisdom_ms = 0, t_nvrtc_ms = 0, t_load_ms = 0, t_launch_ms = 0;

@@ -852,7 +852,32 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
         groups[compile_defines(*op, cfg, grids[i].zbc, zuni)].push_back(i);
     }
     cudaStream_t s = (cudaStream_t)stream;
+    // more than one configuration class: the classes run side by side on
+    // up to kBatchStreams streams forked from s and joined back into it
+    constexpr int kBatchStreams = 4;
+    const int naux = groups.size() > 1 ? (int)std::min<size_t>(groups.size(), kBatchStreams) : 0;
+    if (naux) {
+        while ((int)ctx->aux_streams.size() < naux) {
+            cudaStream_t st;
+            if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+                return fail(KL_ERR_CUDA, "batch stream creation");
+            ctx->aux_streams.push_back(st);
+        }
+        while ((int)ctx->aux_events.size() < 1 + naux) {
+            cudaEvent_t ev;
+            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+                return fail(KL_ERR_CUDA, "batch event creation");
+            ctx->aux_events.push_back(ev);
+        }
+        if (cudaEventRecord(ctx->aux_events[0], s) != cudaSuccess)
+            return fail(KL_ERR_CUDA, "batch fork");
+        for (int i = 0; i < naux; ++i)
+            if (cudaStreamWaitEvent(ctx->aux_streams[i], ctx->aux_events[0], 0) != cudaSuccess)
+                return fail(KL_ERR_CUDA, "batch fork");
+    }
+    int gi = 0;
     for (auto &gp : groups) {
+        cudaStream_t ls = naux ? ctx->aux_streams[gi++ % naux] : s;
         const std::vector<int> &ids = gp.second;
         const Config &cfg = items[ids[0]].cfg;
         const kl_grid &g0 = grids[ids[0]];
@@ -905,6 +930,7 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
         } else {
             if (ctx->tables.size() > 64) {              // bound the cache
                 cudaStreamSynchronize(s);
+                for (cudaStream_t st : ctx->aux_streams) cudaStreamSynchronize(st);
                 for (auto &t : ctx->tables) cudaFree(t.second.first);
                 ctx->tables.clear();
             }
@@ -925,14 +951,19 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
         if (cfg.family == 0) {
             void *params[] = {&argv, &tl};
             r = ctx->drv.LaunchKernel(k->fn, (unsigned)nblocks, 1, 1, cfg.bx, cfg.by, cfg.bz, 0,
-                                      (CUstream)s, params, nullptr);
+                                      (CUstream)ls, params, nullptr);
         } else {
             void *params[] = {&argv, &tl, &tm};
             r = ctx->drv.LaunchKernel(k->fn, (unsigned)nblocks, 1, 1, cfg.mbx, zmarch_block_y(cfg), 1,
-                                      (unsigned)k->smem, (CUstream)s, params, nullptr);
+                                      (unsigned)k->smem, (CUstream)ls, params, nullptr);
         }
         if (r != CUDA_SUCCESS) return cu_fail(r, "cuLaunchKernel (batch)");
         ctx->launches++;
+    }
+    for (int i = 0; i < naux; ++i) {
+        if (cudaEventRecord(ctx->aux_events[1 + i], ctx->aux_streams[i]) != cudaSuccess ||
+            cudaStreamWaitEvent(s, ctx->aux_events[1 + i], 0) != cudaSuccess)
+            return fail(KL_ERR_CUDA, "batch join");
     }
     return KL_OK;
 }
