@@ -296,12 +296,12 @@ bool config_fits(const kl_op &op, const Config &cfg, const kl_grid &g, const kl_
 
 // TMA descriptor of one field for the zmarch box; cached by pointer and layout
 // (box_x elements wide, z.rows rows, one plane)
-static kl_status get_tmap(kl_ctx *ctx, const kl_op &op, const kl_grid &g, const ZGeom &z,
-                          int box_x, const void *ptr, CUtensorMap *out)
+static kl_status get_tmap(kl_ctx *ctx, const kl_op &op, const kl_grid &g, int box_x, int box_y,
+                          const void *ptr, CUtensorMap *out)
 {
     char key[256];
     snprintf(key, sizeof key, "%p/%d/%lld/%lld/%lld/%d/%d", ptr, op.dtype, (long long)g.sj,
-             (long long)g.sk, (long long)g.extent, box_x, z.rows);
+             (long long)g.sk, (long long)g.extent, box_x, box_y);
     auto it = ctx->tmaps.find(key);
     if (it != ctx->tmaps.end()) {
         *out = it->second;
@@ -313,7 +313,7 @@ static kl_status get_tmap(kl_ctx *ctx, const kl_op &op, const kl_grid &g, const 
                                                   : CU_TENSOR_MAP_DATA_TYPE_UINT16;
     cuuint64_t dims[3] = {(cuuint64_t)g.sj, (cuuint64_t)(g.sk / g.sj), (cuuint64_t)(g.extent / g.sk)};
     cuuint64_t strides[2] = {(cuuint64_t)(g.sj * es), (cuuint64_t)(g.sk * es)};
-    cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)z.rows, 1};
+    cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUtensorMap m;
     CUresult r = ctx->drv.TensorMapEncodeTiled(&m, dt, 3, const_cast<void *>(ptr), dims, strides, box,
@@ -387,9 +387,11 @@ kl_status make_kargs(kl_ctx *ctx, const kl_op &op, const Config &cfg, const kl_g
         a.nbz = (g.nz + cfg.kc - 1) / cfg.kc;
         const void *fp[KL_NMAPS] = {f.u, f.v, f.w, op.diff == 2 ? f.nu : f.u, f.u, f.v, f.w};
         for (int q = 0; q < KL_NMAPS; ++q) {
-            // zpack's x-wrap strips are 32 bytes wide; zmarch never reads maps 4..6
+            // zpack's x-wrap strips are 32 bytes wide; zmarch never reads maps 4..6;
+            // zpack's nu box spans tile rows -1 .. tys
             int bx = q >= 4 && cfg.family == 2 ? 32 / es : z.pitch;
-            st = get_tmap(ctx, op, g, z, bx, fp[q], &maps[q]);
+            int by = q == 3 && cfg.family == 2 ? z.tys + 2 : z.rows;
+            st = get_tmap(ctx, op, g, bx, by, fp[q], &maps[q]);
             if (st) return st;
         }
     }
@@ -619,7 +621,8 @@ static kl_status fill_for_op(kl_ctx *ctx, const kl_op *op, const kl_grid *grid,
     st = select_config(ctx, *op, *grid, cfg);
     if (st) return st;
     // the zpack kernel forms the x halo itself on grids with nx >= 64 + H
-    const bool x_ghosts = !(cfg->family == 2 && grid->nx >= 64 + halo_of(*op));
+    // (constant nu)
+    const bool x_ghosts = !(cfg->family == 2 && op->diff != 2 && grid->nx >= 64 + halo_of(*op));
     cudaError_t e = fill_ghosts_launch(esize_of(op->dtype), *grid, (void *)fields->u,
                                        (void *)fields->v, (void *)fields->w, (void *)fields->nu,
                                        (cudaStream_t)stream, x_ghosts);

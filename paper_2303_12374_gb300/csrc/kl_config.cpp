@@ -154,8 +154,15 @@ size_t zmarch_smem_bytes(const kl_op &op, const Config &c)
     ZGeom z = zmarch_geometry(op, c);
     // ring + 128 B of alignment slack + one 8-byte mbarrier per slot
     size_t bytes = z.plane_bytes * z.nf * c.ns + 256;
-    // zpack x-wrap strips: 3 fields x rows x 32 bytes per slot (128-B multiples)
-    if (c.family == 2) bytes += 3 * (size_t)((z.rows * 32 + 127) / 128 * 128) * c.ns;
+    if (c.family == 2 && op.diff == 2) {
+        // zpack, variable nu: u, v, w ring + a nu ring of ns - 2R + 2 planes
+        // of tys + 2 rows; no x-wrap strips
+        size_t nplane = ((size_t)z.pitch * (z.tys + 2) * esize_of(op.dtype) + 127) / 128 * 128;
+        bytes = z.plane_bytes * 3 * c.ns + nplane * (c.ns - 2 * z.halo + 2) + 256;
+    } else if (c.family == 2) {
+        // zpack x-wrap strips: 3 fields x rows x 32 bytes per slot (128-B multiples)
+        bytes += 3 * (size_t)((z.rows * 32 + 127) / 128 * 128) * c.ns;
+    }
     // zpack y-face exchange: 3 fields x warps x 32 lanes x one packed pair
     if (c.family == 2 && c.yx)
         bytes += 3 * (size_t)c.mby * 32 * (op.dtype == KL_F64 ? 16 : 8) + 16;
@@ -217,8 +224,8 @@ bool config_check(const kl_op &op, const Config &c, std::string *err)
             *err = "cs=1 forms every y face in its own warp group (yx must be 0)";
             return false;
         }
-        if (c.family == 2 && op.diff == 2) {
-            *err = "zpack supports diff = 0 or 1";
+        if (c.family == 2 && op.diff == 2 && (c.cs || c.yx)) {
+            *err = "zpack with variable nu needs cs=0 and yx=0";
             return false;
         }
         if (!in(c.kc, {4, 8, 16, 32, 64, 128, 256}) || !in(c.ns, {8, 9, 10, 12}) ||

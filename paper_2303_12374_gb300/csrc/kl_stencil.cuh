@@ -737,12 +737,13 @@ kl_tendency(const kl_args a, const __grid_constant__ kl_tmap tm_u,
 //  * z: the top face of level k is carried as the bottom face of level k+1;
 //  * constant-nu diffusion: the diffusive flux nu (a_{m+1} - a_m) / d of a face
 //    is added to the advective flux of the same face, using the difference
-//    d1 = a_m - a_{m+1} the upwind formula already forms.
-// Supports diff = 0 or 1.
-
-#if KL_DIFF == 2
-#error "zpack supports diff = 0 or 1"
-#endif
+//    d1 = a_m - a_{m+1} the upwind formula already forms;
+//  * variable-nu diffusion (stress form): each face flux gets its stress
+//    -S / FS; a shear stress on an edge (xy, xz, yz) is formed once and used
+//    by both components that share the edge (u's y face and v's x face, u's
+//    z face and w's x face, v's z face and w's y face), the z-edge stresses
+//    carried from one level to the next like the z fluxes; nu streams
+//    through its own ring of planes k-1 .. k+1 (rows -1 .. TYS of the tile).
 
 #if KL_DTYPE == 0 || KL_PK == 0
 // two independent scalars (f64, or f32 with packed arithmetic switched off)
@@ -1032,10 +1033,33 @@ __device__ __forceinline__ void kl_cs_level(const kl_args &a, const kl_vk &K, co
 #define KL_XW_W (32 / (int)sizeof(T))                        // strip width, elements
 #define KL_STRIP_BOX (KL_ROWS * 32)                          // bytes one strip box lands
 #define KL_STRIP_BYTES KL_RUP(KL_STRIP_BOX, 128)
+#if KL_DIFF == 2
+// variable nu: no x-wrap strips (the x ghosts are read from memory); nu ring
+#define KL_ZSLOT (3 * KL_PLANE_BYTES)                        // zpack ring slot
+#define KL_NROWS (KL_TYS + 2)                                // nu box: tile rows -1 .. TYS
+#define KL_NBOX (KL_PITCH * KL_NROWS * (int)sizeof(T))
+#define KL_NPLANE KL_RUP(KL_NBOX, 128)
+#define KL_NNS (KL_NS - 2 * KL_R + 2)                        // nu ring slots
+#define KL_NLEAD (KL_R - 1)                                  // nu plane p - NLEAD rides with plane p
+#else
 #define KL_ZSLOT (3 * KL_PLANE_BYTES + 3 * KL_STRIP_BYTES)   // zpack ring slot
+#endif
 #define KL_NT (32 * KL_MBY * (KL_CS ? 3 : 1))                // threads per block
 #define KL_XW_Q ((3 * KL_ROWS * KL_H + KL_NT - 1) / KL_NT)   // halo values per thread
 static_assert(KL_AL - 1 + KL_H - 1 < KL_XW_W, "a strip must hold the wrapped columns");
+
+#if KL_DIFF == 2
+#define KL_NOFF(x, row) ((((row) + 1) * KL_PITCH + (x)) * (int)sizeof(T))
+// aligned pair of nu on plane k+DK at columns (lx + DX, lx + DX + 1), tile row
+// `row` in [-1, TYS]
+template <int DK, int DX>
+__device__ __forceinline__ V kl_npr(const char *const *npl, int lx, int row)
+{
+    static_assert(DK >= -1 && DK <= 1, "nu plane outside the staged window");
+    static_assert(DX % 2 == 0 && DX >= -KL_LPAD && KL_LPAD + 62 + DX + 1 < KL_PITCH, "nu x offset");
+    return vld((const T *)(npl[DK + 1] + KL_NOFF(lx + DX, row)));
+}
+#endif
 
 __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *const *maps,
                                               int bxi, int byi, int bzi)
@@ -1048,7 +1072,12 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
     static_assert(KL_PITCH >= KL_LPAD + 64 + (KL_ADV == 5 ? 3 : 1), "right pad too small");
     extern __shared__ unsigned char kl_smem_raw[];
     unsigned char *ring = (unsigned char *)(((unsigned long long)kl_smem_raw + 127) & ~127ull);
+#if KL_DIFF == 2
+    unsigned char *nring = ring + KL_NS * KL_ZSLOT;
+    unsigned long long *bars = (unsigned long long *)(nring + KL_NNS * KL_NPLANE);
+#else
     unsigned long long *bars = (unsigned long long *)(ring + KL_NS * KL_ZSLOT);
+#endif
 #if KL_YX
     // y-face exchange buffer after the barriers: [3 fields][warps][32 lanes]
     V *xbuf = (V *)(((unsigned long long)(bars + KL_NS) + 15) & ~15ull);
@@ -1070,18 +1099,29 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
     }
     __syncthreads();
     // x wrap (see above): which side this tile wraps, never both
-    const bool xw_on = nx >= 64 + KL_H;
+    const bool xw_on = KL_DIFF != 2 && nx >= 64 + KL_H;
     const bool need_l = xw_on && tx0 == 0, need_r = xw_on && tx0 + 64 + KL_H > nx;
     const bool xwrap = need_l || need_r;
     const int xs0 = need_l ? (nx - KL_H) / KL_AL * KL_AL : 0;   // first strip column
     auto issue = [&](int p) {
         int slot = (p - (kb - KL_R)) % KL_NS;
         unsigned bar = kl_smem_addr(&bars[slot]);
+#if KL_DIFF == 2
+        // nu plane q rides with plane p; planes below kb - 1 are never read
+        const int q = p - KL_NLEAD;
+        kl_mbar_expect(bar, 3 * KL_BOX_BYTES + (q >= kb - 1 ? KL_NBOX : 0));
+#else
         kl_mbar_expect(bar, 3 * KL_BOX_BYTES + (xwrap ? 3 * KL_STRIP_BOX : 0));
+#endif
         unsigned dst = kl_smem_addr(ring + slot * KL_ZSLOT);
 #pragma unroll
         for (int f = 0; f < 3; ++f)
             kl_tma_load3(dst + f * KL_PLANE_BYTES, maps[f], gx, gy, gz0 + p, bar);
+#if KL_DIFF == 2
+        if (q >= kb - 1)
+            kl_tma_load3(kl_smem_addr(nring + ((q - (kb - 1)) % KL_NNS) * KL_NPLANE), maps[3], gx,
+                         (int)a.tile_y0 + ty0 - 1, gz0 + q, bar);
+#endif
         if (xwrap) {
             // the halo columns of this slot were last written through the
             // generic proxy; order that before the asynchronous writes
@@ -1136,6 +1176,9 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
 #else
     V zb[KL_MPY][3];
 #endif
+#if KL_DIFF == 2
+    V sxz[KL_MPY], syz[KL_MPY];     // stresses of the xz and yz edges at zh_k, per row
+#endif
     bool timed_out = false;
     int p_waited = p_first - 1;
 
@@ -1170,6 +1213,40 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
         const V vczu = vsplat(KL_FS * Z.dzi), vczw = vsplat(KL_FS * Z.dzhi);
         const V vkzu_top = vsplat(nu * Z.dzhi_up / KL_FS);   // u, v top face zh_{k+1}
         const V vkzw_top = vsplat(nu * Z.dzi / KL_FS);       // w top face z_k
+#if KL_DIFF == 2
+        // nu planes k-1 .. k+1 and the stress coefficients of this level
+        const char *npl[3];
+#pragma unroll
+        for (int d = -1; d <= 1; ++d)
+            npl[d + 1] = (const char *)(nring + ((k + d - (kb - 1)) % KL_NNS) * KL_NPLANE);
+#define KL_N(dk, dx, row) kl_npr<(dk), (dx)>(npl, lx, (row))
+        // nu summed over the two columns (c-1, c) of an xh edge
+#define KL_NSX(dk, row) vadd(vcross(KL_N(dk, -2, row), KL_N(dk, 0, row)), KL_N(dk, 0, row))
+        const V kxn = vsplat(C(2) * dxi / KL_FS), kyn = vsplat(C(2) * dyi / KL_FS);
+        const V kzn = vsplat(C(2) * Z.dzi / KL_FS);
+        const V kx4 = vsplat(dxi / (C(4) * KL_FS)), ky4 = vsplat(dyi / (C(4) * KL_FS));
+        const V kz4t = vsplat(Z.dzhi_up / (C(4) * KL_FS)), kz4b = vsplat(Z.dzhi / (C(4) * KL_FS));
+        // the term an edge stress adds to a face flux, -S / FS, with S =
+        // (nu4 / 4) (difference along the face normal x metric + cross
+        // difference x metric): d1 = a_m - a_{m+1} of the face's own window
+        auto shear = [&](V nu4, V d1, V ka, V db, V kb_) {
+            return vmul(nu4, vsub(vmul(d1, ka), vmul(db, kb_)));
+        };
+        if (k == kb) {
+            // z-edge stresses at zh_k of the first level (carried afterwards)
+#pragma unroll
+            for (int r = 0; r < KL_MPY; ++r) {
+                const int yr = r0 + r;
+                const V u_0 = KL_Q(0, 0, 0, yr), w_0 = KL_Q(2, 0, 0, yr);
+                sxz[r] = shear(vadd(KL_NSX(-1, yr), KL_NSX(0, yr)), vsub(KL_Q(0, -1, 0, yr), u_0), kz4b,
+                               vsub(w_0, vcross(KL_Q(2, 0, -2, yr), w_0)), kx4);
+                syz[r] = shear(vadd(vadd(KL_N(-1, 0, yr - 1), KL_N(-1, 0, yr)),
+                                    vadd(KL_N(0, 0, yr - 1), KL_N(0, 0, yr))),
+                               vsub(KL_Q(1, -1, 0, yr), KL_Q(1, 0, 0, yr)), kz4b,
+                               vsub(w_0, KL_Q(2, 0, 0, yr - 1)), ky4);
+            }
+        }
+#endif
 
         // ---- side pass: the x face beyond the warp's columns, every row
         C extra;
@@ -1197,6 +1274,27 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
             const char *p2 = f == 0 ? base + KL_OFF(xs + 3, row) : pl[KL_R] + KL_OFF(KL_LPAD + 64, row);
             C us = lds((const T *)p1) + lds((const T *)p2);
             extra = kl_sflux(us, a0, a1, a2, a3, a4, a5, kdx);
+#if KL_DIFF == 2
+            {
+                // the face's stress, as the pair code forms it
+                const C nl = lds((const T *)(npl[1] + KL_NOFF(KL_LPAD + 63, row)));
+                const C nr = lds((const T *)(npl[1] + KL_NOFF(KL_LPAD + 64, row)));
+                const C d1c = lds((const T *)p1) - lds((const T *)p2);   // cross: two u's
+                C st;
+                if (f == 0) {
+                    st = C(2) * dxi / KL_FS * lds((const T *)(npl[1] + KL_NOFF(KL_LPAD - 1, row))) * (a2 - a3);
+                } else if (f == 1) {
+                    const C nu4 = lds((const T *)(npl[1] + KL_NOFF(KL_LPAD + 63, row - 1))) +
+                                  lds((const T *)(npl[1] + KL_NOFF(KL_LPAD + 64, row - 1))) + nl + nr;
+                    st = nu4 * (d1c * (dyi / (C(4) * KL_FS)) - (a3 - a2) * (dxi / (C(4) * KL_FS)));
+                } else {
+                    const C nu4 = lds((const T *)(npl[0] + KL_NOFF(KL_LPAD + 63, row))) +
+                                  lds((const T *)(npl[0] + KL_NOFF(KL_LPAD + 64, row))) + nl + nr;
+                    st = nu4 * (d1c * (Z.dzhi / (C(4) * KL_FS)) - (a3 - a2) * (dxi / (C(4) * KL_FS)));
+                }
+                extra += st;
+            }
+#endif
         }
 
         // ---- y faces
@@ -1255,6 +1353,20 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
                              KL_Q(2, 0, 0, yr), KL_A5(KL_Q(2, 0, 0, yr + 1)), KL_A5(KL_Q(2, 0, 0, yr + 2)), vkdy);
         }
 #endif
+#if KL_DIFF == 2
+        // stress of the xy edge at the bottom of the current row: u's y face
+        // and v's x face of that row
+        V sxy;
+        {
+            const int yr = r0;
+            const V v0 = KL_Q(1, 0, 0, yr);
+            sxy = shear(vadd(KL_NSX(0, yr - 1), KL_NSX(0, yr)), vsub(KL_Q(0, 0, 0, yr - 1), KL_Q(0, 0, 0, yr)),
+                        ky4, vsub(v0, vcross(KL_Q(1, 0, -2, yr), v0)), kx4);
+            fuy_b = vadd(fuy_b, sxy);
+            fvy_b = vfma(vmul(kyn, KL_N(0, 0, yr - 1)), vsub(KL_Q(1, 0, 0, yr - 1), v0), fvy_b);
+            fwy_b = vadd(fwy_b, syz[0]);
+        }
+#endif
 
 #pragma unroll
         for (int r = 0; r < KL_MPY; ++r) {
@@ -1275,6 +1387,11 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
             V fwx = kl_vflux(K, vadd(KL_Q(0, -1, 0, yr), u_0),
                              KL_A5(vcross(w_m4, w_m2)), KL_A5(w_m2), vcross(w_m2, w_0),
                              w_0, KL_A5(vcross(w_0, w_2)), KL_A5(w_2), vkdx);
+#if KL_DIFF == 2
+            fux = vfma(vmul(kxn, KL_N(0, 0, yr)), vsub(u_0, vcross(u_0, u_2)), fux);
+            fvx = vadd(fvx, sxy);
+            fwx = vadd(fwx, sxz[r]);
+#endif
             // faces on the other side: u left = (lane-1 hi, own lo);
             // v, w right = (own hi, lane+1 lo); warp edges from the side pass
             C ul_hi = __shfl_sync(0xffffffffu, vhi(fux), (lane + 31) & 31);
@@ -1311,6 +1428,26 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
                                KL_A5(KL_Q(2, 0, 0, yt - 3)), KL_A5(KL_Q(2, 0, 0, yt - 2)), KL_Q(2, 0, 0, yt - 1),
                                KL_Q(2, 0, 0, yt), KL_A5(KL_Q(2, 0, 0, yt + 1)), KL_A5(KL_Q(2, 0, 0, yt + 2)), vkdy);
 #endif
+#if KL_DIFF == 2
+            V sxy_t;
+            {
+                const int yt = yr + 1;
+                const V v0t = KL_Q(1, 0, 0, yt);
+                sxy_t = shear(vadd(KL_NSX(0, yr), KL_NSX(0, yt)), vsub(KL_Q(0, 0, 0, yr), KL_Q(0, 0, 0, yt)),
+                              ky4, vsub(v0t, vcross(KL_Q(1, 0, -2, yt), v0t)), kx4);
+                fuy_t = vadd(fuy_t, sxy_t);
+                fvy_t = vfma(vmul(kyn, KL_N(0, 0, yr)), vsub(KL_Q(1, 0, 0, yr), v0t), fvy_t);
+                // yz edge at the bottom of row yt: carried for the thread's own
+                // rows, formed here above its last row
+                V syz_t;
+                if (r + 1 < KL_MPY)
+                    syz_t = syz[r + 1 < KL_MPY ? r + 1 : 0];
+                else
+                    syz_t = shear(vadd(vadd(KL_N(-1, 0, yr), KL_N(-1, 0, yt)), vadd(KL_N(0, 0, yr), KL_N(0, 0, yt))),
+                                  vsub(KL_Q(1, -1, 0, yt), v0t), kz4b, vsub(KL_Q(2, 0, 0, yt), KL_Q(2, 0, 0, yr)), ky4);
+                fwy_t = vadd(fwy_t, syz_t);
+            }
+#endif
 
             // ---- z faces: bottom carried, top formed here
             V fz_u = kl_vflux(K, vadd(vcross(KL_Q(2, 1, -2, yr), KL_Q(2, 1, 0, yr)), KL_Q(2, 1, 0, yr)),
@@ -1335,6 +1472,28 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
                                     KL_A5(KL_Q(2, -3, 0, yr)), KL_A5(KL_Q(2, -2, 0, yr)), KL_Q(2, -1, 0, yr),
                                     w_0, KL_A5(KL_Q(2, 1, 0, yr)), KL_A5(KL_Q(2, 2, 0, yr)), kzw_b);
             }
+#if KL_DIFF == 2
+            {
+                // top z faces: xz and yz edges at zh_{k+1}, w's normal stress at z_k
+                const V w10 = KL_Q(2, 1, 0, yr);
+                const V sxz_t = shear(vadd(KL_NSX(0, yr), KL_NSX(1, yr)), vsub(u_0, KL_Q(0, 1, 0, yr)), kz4t,
+                                      vsub(w10, vcross(KL_Q(2, 1, -2, yr), w10)), kx4);
+                const V syz_t = shear(vadd(vadd(KL_N(0, 0, yr - 1), KL_N(0, 0, yr)),
+                                           vadd(KL_N(1, 0, yr - 1), KL_N(1, 0, yr))),
+                                      vsub(v_0, KL_Q(1, 1, 0, yr)), kz4t, vsub(w10, KL_Q(2, 1, 0, yr - 1)), ky4);
+                fz_u = vadd(fz_u, sxz_t);
+                fz_v = vadd(fz_v, syz_t);
+                fz_w = vfma(vmul(kzn, KL_N(0, 0, yr)), vsub(w_0, w10), fz_w);
+                if (k == kb) {
+                    zb[r][0] = vadd(zb[r][0], sxz[r]);
+                    zb[r][1] = vadd(zb[r][1], syz[r]);
+                    zb[r][2] = vfma(vmul(vsplat(C(2) * Z.dzi_dn / KL_FS), KL_N(-1, 0, yr)),
+                                    vsub(KL_Q(2, -1, 0, yr), w_0), zb[r][2]);
+                }
+                sxz[r] = sxz_t;
+                syz[r] = syz_t;
+            }
+#endif
             // ---- tendencies
             V tu = vfma(vsub(ul, fux), vcx, vfma(vsub(fuy_b, fuy_t), vcy, vmul(vsub(zb[r][0], fz_u), vczu)));
             V tv = vfma(vsub(fvx, vr), vcx, vfma(vsub(fvy_b, fvy_t), vcy, vmul(vsub(zb[r][1], fz_v), vczu)));
@@ -1345,6 +1504,9 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
             fuy_b = fuy_t;
             fvy_b = fvy_t;
             fwy_b = fwy_t;
+#if KL_DIFF == 2
+            sxy = sxy_t;
+#endif
             if (KL_ZBC == 1 && k == 0) tw = vsplat(C(0));
             const int j = ty0 + yr;
             if (j < ny) {
@@ -1365,6 +1527,10 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
                 }
             }
         }
+#if KL_DIFF == 2
+#undef KL_N
+#undef KL_NSX
+#endif
 #endif  // KL_CS
 #undef KL_Q
         bool ok = true;

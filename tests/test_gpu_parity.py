@@ -95,10 +95,11 @@ def test_tendency_parity_configs(ctx, oracle_mod, config, dtype):
         except kl.KLError:
             continue
         ran += 1
-        # the zpack family wraps x itself: NaN in the memory x ghosts must not matter
+        # the zpack family wraps x itself (constant nu): NaN in the memory x
+        # ghosts must not matter
         p, _, outs, rin = run_gpu(ctx, f, adv=adv, diff=diff, dtype=dtype, walls=True, g=3,
                                   stretched=True, config=config,
-                                  poison_x=config.startswith("zpack"))
+                                  poison_x=config.startswith("zpack") and diff != 2)
         ref = oracle_ref(oracle_mod, rin, f["zh"], adv=adv, diff=diff, walls=True, g=3)
         for name, r in zip(("ut", "vt", "wt"), ref):
             e = rel_err(p.download(outs[name]), r)
@@ -151,6 +152,36 @@ def test_zpack_x_wrap_in_kernel(ctx, oracle_mod, dtype, nx, ny, nz, walls, adv):
         for name, r in zip(("ut", "vt", "wt"), ref):
             e = rel_err(p.download(outs[name]), r)
             assert e <= TOL[dtype], (cfg, name, e)
+
+
+@pytest.mark.parametrize("dtype", [0, 1, 2])
+@pytest.mark.parametrize("nx,ny,nz,walls,adv,stretch", [
+    (70, 45, 23, True, 5, 2.0),
+    (37, 21, 17, True, 5, 0.0),     # one tile, ragged
+    (130, 19, 12, False, 2, 0.0),   # periodic z, second order
+    (64, 16, 9, True, 0, 2.0),      # diffusion only
+])
+def test_zpack_variable_nu(ctx, oracle_mod, dtype, nx, ny, nz, walls, adv, stretch):
+    """zpack with the stress-form variable-nu diffusion: every edge stress is
+    formed once and shared by the two faces on it, z-edge stresses carried."""
+    from paper_2303_12374_gb300 import kl
+    g = 3 if adv == 5 else 1
+    f = make_inputs(nx, ny, nz, seed=nx * ny, walls=walls, stretch=stretch, var_nu=True)
+    ran = 0
+    for cfg in ("zpack:w=4,ly=2,kc=8,ns=8,minb=1", "zpack:w=2,ly=4,kc=4,ns=9,minb=1",
+                "zpack:w=1,ly=1,kc=16,ns=10,minb=1"):
+        try:
+            kl.kl_config_normalize(kl.Op(adv, 2, dtype, 0), cfg)
+        except kl.KLError:
+            continue
+        ran += 1
+        p, _, outs, rin = run_gpu(ctx, f, adv=adv, diff=2, dtype=dtype, walls=walls, g=g,
+                                  stretched=stretch > 0, config=cfg)
+        ref = oracle_ref(oracle_mod, rin, f["zh"], adv=adv, diff=2, walls=walls, g=g)
+        for name, r in zip(("ut", "vt", "wt"), ref):
+            e = rel_err(p.download(outs[name]), r)
+            assert e <= TOL[dtype], (cfg, name, e)
+    assert ran
 
 
 def test_accumulate(ctx, oracle_mod):

@@ -104,6 +104,16 @@ def test_nvrtc_compiles_tiled_configs():
     for cfg in ["zpack:w=4,ly=2,kc=16,ns=8,minb=2", "zpack:w=4,ly=2,kc=16,ns=8,minb=2,cs=1"]:
         log = kl.kl_compile_only(kl.Op(5, 1, 1, 0), cfg, 1, 1)
         assert re.search(r"(\d+) bytes spill stores", log) is not None
+    # zpack with variable nu (stretched z)
+    log = kl.kl_compile_only(kl.Op(5, 2, 1, 0), "zpack:w=4,ly=2,kc=16,ns=8,minb=2", 1, 0)
+    assert re.search(r"(\d+) bytes spill stores", log) is not None
+
+
+def test_zpack_variable_nu_needs_cs0_yx0():
+    for bad in ("zpack:w=4,ly=2,cs=1", "zpack:w=4,ly=2,yx=1"):
+        with pytest.raises(kl.KLError):
+            kl.kl_config_normalize(kl.Op(5, 2, 1, 0), bad)
+    assert kl.kl_config_normalize(kl.Op(5, 2, 1, 0), "zpack:w=4,ly=2").startswith("zpack:")
 
 
 def test_nvrtc_failure_is_reported():
