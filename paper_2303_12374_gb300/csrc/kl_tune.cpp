@@ -575,7 +575,7 @@ kl_status kl_tune(kl_ctx *ctx, const char *capture_path, const char *opts, const
     std::vector<int> fams;
     if (O.family == "all" || O.family == "direct") fams.push_back(0);
     if (O.family == "all" || O.family == "zmarch") fams.push_back(1);
-    if ((O.family == "all" || O.family == "zpack") && op.diff != 2) fams.push_back(2);
+    if (O.family == "all" || O.family == "zpack") fams.push_back(2);
     if (fams.empty()) return fail(KL_ERR_INVALID_ARG, "no configuration family applies to this op");
     std::map<std::string, Eval> done;
     read_log(O.log, &done);
