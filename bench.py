@@ -379,6 +379,25 @@ def workload_sweep(ctx, device, stream, reps):
     return out
 
 
+def diag_timing(ctx, p, outs, stream, reps=20):
+    """kl_diag (FP64 max, rms, sums, metric-weighted sum) on one 256^3 tendency,
+    per call including the 48-byte read-back it synchronises on."""
+    import torch
+    from paper_2303_12374_gb300 import kl
+    out = None
+    for _ in range(3):
+        out = kl.kl_diag(ctx, p.dtype, p.grid, 0, outs[0].data_ptr(), None, stream.cuda_stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        kl.kl_diag(ctx, p.dtype, p.grid, 0, outs[0].data_ptr(), None, stream.cuda_stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    us = a.elapsed_time(b) / reps * 1e3
+    nbytes = p.nx * p.ny * p.nz * outs[0].element_size()
+    return {"us": us, "read_gbs": nbytes / us / 1e3, "values": list(out)}
+
+
 def batched_run(ctx, device, stream, reps=20):
     """64 uneven grids: one batched call (tuned size classes) vs 64 default launches."""
     import torch
@@ -560,6 +579,7 @@ def main():
         extras["batched"] = batched_run(ctx, device, stream)
         extras["workloads"] = workload_sweep(ctx, device, stream, max(20, args.steps // 20))
         extras["launch_overhead"] = launch_overhead(local, wisdom, device)
+        extras["diag"] = diag_timing(ctx, p, outs, stream)
 
     # --- end to end through the public API with pinned host buffers (every rank)
     barrier()

@@ -206,27 +206,102 @@ __device__ __forceinline__ void reduce6(double v[6], double *out)
     }
 }
 
-template <typename T>
+// float-float accumulator: hi + lo carries the sum of FP32 values with about
+// 48 significant bits; every addition is Knuth's error-free TwoSum, products
+// of two floats enter exactly through their FMA residual
+struct kl_ff { float hi, lo; };
+
+__device__ __forceinline__ void ff_add(kl_ff &acc, float x)
+{
+    const float s = acc.hi + x;
+    const float bp = s - acc.hi;
+    const float err = (acc.hi - (s - bp)) + (x - bp);
+    acc.hi = s;
+    acc.lo += err;
+}
+
+__device__ __forceinline__ void ff_add_square(kl_ff &acc, float x)
+{
+    const float p = x * x;
+    const float pe = fmaf(x, x, -p);          // x*x = p + pe exactly
+    ff_add(acc, p);
+    acc.lo += pe;
+}
+
+__device__ __forceinline__ double ff_value(const kl_ff &acc) { return (double)acc.hi + (double)acc.lo; }
+
+// Each warp takes a contiguous block of interior rows (j, k) (consecutive
+// rows of a level lie next to each other in memory), lanes along x, every
+// load coalesced.  Without a reference (the common case: t in f32 or 16-bit
+// storage) the per-element work stays in FP32: the maximum is exact in FP32
+// and the sums run in float-float; a lane folds its float-float partials into
+// FP64 once per level it touches (the dz-weighted sum takes that level's sum
+// times w_k).  GB300 runs FP64 at a small fraction of its FP32 rate, which is
+// what this keeps off the per-element path.  With a reference, or f64
+// storage, every element is reduced in FP64.
+template <typename T, bool REF>
 __global__ void __launch_bounds__(256) diag_kernel(DiagArgs a)
 {
     double v[6] = {0, 0, 0, 0, 0, 0};
     const T *t = (const T *)a.t;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < a.n;
-         q += (long long)gridDim.x * blockDim.x) {
-        int i = (int)(q % a.nx);
-        long long r = q / a.nx;
-        int j = (int)(r % a.ny);
-        int k = (int)(r / a.ny);
-        long long o = i + j * a.sj + k * a.sk;
-        double tv = to_d(t[o]);
-        double rv = a.ref ? a.ref[o] : 0.0;
-        double e = tv - rv;
-        v[0] = fmax(v[0], fabs(e));
-        v[1] += e * e;
-        v[2] = fmax(v[2], fabs(rv));
-        v[3] += rv * rv;
-        v[4] += tv;
-        v[5] += tv * a.wz[k];
+    const int lane = (int)(threadIdx.x & 31);
+    const long long rows = (long long)a.ny * a.nz;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long per = (rows + nw - 1) / nw;
+    const long long rb = wid * per, re = rb + per < rows ? rb + per : rows;
+    if (rb < re) {
+        int k = (int)(rb / a.ny), j = (int)(rb - (long long)k * a.ny);
+        float tmax = 0.0f;
+        kl_ff s1 = {0.0f, 0.0f}, s2 = {0.0f, 0.0f};      // this level's sum and squares
+        double rs = 0.0;                                 // this level's sum (FP64 path)
+        for (long long r = rb; r < re; ++r) {
+            const long long o0 = j * a.sj + (long long)k * a.sk;
+            if (REF || sizeof(T) == 8) {
+#pragma unroll 4
+                for (int i = lane; i < a.nx; i += 32) {
+                    const double tv = to_d(t[o0 + i]);
+                    const double rv = REF ? a.ref[o0 + i] : 0.0;
+                    const double e = tv - rv;
+                    v[0] = fmax(v[0], fabs(e));
+                    v[1] = fma(e, e, v[1]);
+                    if (REF) {
+                        v[2] = fmax(v[2], fabs(rv));
+                        v[3] = fma(rv, rv, v[3]);
+                    }
+                    rs += tv;
+                }
+            } else {
+                // eight loads per lane in flight before the arithmetic
+                for (int i0 = lane; i0 < a.nx; i0 += 32 * 8) {
+                    float x[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        x[u] = i0 + 32 * u < a.nx ? (float)to_d(t[o0 + i0 + 32 * u]) : 0.0f;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        tmax = fmaxf(tmax, fabsf(x[u]));
+                        ff_add(s1, x[u]);
+                        ff_add_square(s2, x[u]);
+                    }
+                }
+            }
+            // next row; at the end of a level (or of the block) fold the level's sum
+            if (++j == a.ny || r + 1 == re) {
+                const double ls = (REF || sizeof(T) == 8) ? rs : ff_value(s1);
+                v[4] += ls;
+                v[5] = fma(ls, a.wz[k], v[5]);
+                if (!(REF || sizeof(T) == 8)) v[1] += ff_value(s2);
+                rs = 0.0;
+                s1.hi = s1.lo = 0.0f;
+                s2.hi = s2.lo = 0.0f;
+                if (j == a.ny) {
+                    j = 0;
+                    ++k;
+                }
+            }
+        }
+        if (!(REF || sizeof(T) == 8)) v[0] = fmax(v[0], (double)tmax);
     }
     reduce6(v, a.partial + 6 * (size_t)blockIdx.x);
 }
@@ -294,7 +369,7 @@ cudaError_t fill_ghosts_launch(int esize, const kl_grid &g, void *u, void *v, vo
     return fill_dispatch<unsigned short>(g.g, grid, a, s);
 }
 
-int diag_blocks(int nsm) { return nsm * 4; }
+int diag_blocks(int nsm) { return nsm * 8; }
 
 cudaError_t diag_launch(int dtype, const kl_grid &g, int level, const void *t, const double *ref,
                         const double *wz, double *scratch, int nblocks, double *dout,
@@ -313,11 +388,15 @@ cudaError_t diag_launch(int dtype, const kl_grid &g, int level, const void *t, c
     a.nz = g.nz;
     a.n = (long long)g.nx * g.ny * g.nz;
     a.partial = scratch;
-    switch (dtype) {
-    case KL_F64: diag_kernel<double><<<nblocks, 256, 0, s>>>(a); break;
-    case KL_F32: diag_kernel<float><<<nblocks, 256, 0, s>>>(a); break;
-    case KL_BF16: diag_kernel<__nv_bfloat16><<<nblocks, 256, 0, s>>>(a); break;
-    default: diag_kernel<__half><<<nblocks, 256, 0, s>>>(a); break;
+    switch (dtype * 2 + (ref ? 1 : 0)) {
+    case 2 * KL_F64: diag_kernel<double, false><<<nblocks, 256, 0, s>>>(a); break;
+    case 2 * KL_F64 + 1: diag_kernel<double, true><<<nblocks, 256, 0, s>>>(a); break;
+    case 2 * KL_F32: diag_kernel<float, false><<<nblocks, 256, 0, s>>>(a); break;
+    case 2 * KL_F32 + 1: diag_kernel<float, true><<<nblocks, 256, 0, s>>>(a); break;
+    case 2 * KL_BF16: diag_kernel<__nv_bfloat16, false><<<nblocks, 256, 0, s>>>(a); break;
+    case 2 * KL_BF16 + 1: diag_kernel<__nv_bfloat16, true><<<nblocks, 256, 0, s>>>(a); break;
+    case 2 * KL_F16: diag_kernel<__half, false><<<nblocks, 256, 0, s>>>(a); break;
+    default: diag_kernel<__half, true><<<nblocks, 256, 0, s>>>(a); break;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
