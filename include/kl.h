@@ -157,8 +157,25 @@ kl_status kl_fill_ghosts_op(kl_ctx *ctx, const kl_op *op, const kl_grid *grid,
 kl_status kl_step(kl_ctx *ctx, const kl_op *op, const kl_grid *grid, const kl_fields *fields,
                   void *stream);
 
-/* As kl_launch with an explicit configuration string (see kl_config_help);
- * "default" is the untuned default configuration. */
+/*
+ * As kl_launch with an explicit configuration string.  Configuration strings
+ * name a family and its parameters (omitted keys take their defaults):
+ *   "default"  the untuned default of Table 2 (direct, 256 x 1 x 1 threads)
+ *   "direct:bx=,by=,bz=,tx=,ty=,tz=,ux=,uy=,uz=,cx=,cy=,cz=,perm=,minb="
+ *              Table 2: block shape, points per thread, unroll and
+ *              consecutive/strided per axis, unravel order (XYZ .. ZYX),
+ *              minimum blocks per SM
+ *   "zmarch:bx=,by=,px=,py=,kc=,ns=,minb="
+ *              z-marching CTAs over a TMA plane ring: threads along x and y,
+ *              points per thread along x and y, z levels per CTA, ring slots
+ *   "zpack:w=,ly=,kc=,ns=,minb=,yx=,pk=,cs="
+ *              z-marching over 64-column tiles with packed column pairs: warps,
+ *              rows per warp, z levels per CTA, ring slots, minimum blocks,
+ *              y faces exchanged between warps (yx), packed f32x2 arithmetic
+ *              (pk), one warp group per tendency component (cs)
+ * A configuration outside the space or the op's constraints (threads, shared
+ * memory, TMA box) is rejected with KL_ERR_INVALID_ARG.
+ */
 kl_status kl_launch_with_config(kl_ctx *ctx, const kl_op *op, const char *config,
                                 const kl_grid *grid, const kl_fields *fields, void *stream);
 
@@ -247,7 +264,8 @@ kl_status kl_compile_only(const kl_op *op, const char *config, int32_t zbc, int3
 
 /*
  * Wisdom selection (Sec. 4.5) over the file at path: the record matching
- * device name and size; else the same device, nearest size (Euclidean);
+ * device name and size (several such records, one per tuning session: the
+ * fastest, ties to the newest); else the same device, nearest size (Euclidean);
  * else the same architecture (compute capability), nearest size; else any
  * record, nearest size; else (empty, missing or unreadable file) the
  * default.  Records of another zbc are never chosen.  Writes the chosen
