@@ -541,7 +541,9 @@ void kl_destroy(kl_ctx *c)
         cudaFree(p.second.d32);
     }
     for (auto &p : c->tables) cudaFree(p.second.first);
+    for (auto &gr : c->graphs) cudaGraphExecDestroy(gr.second);
     for (cudaStream_t st : c->aux_streams) cudaStreamDestroy(st);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (cudaEvent_t ev : c->aux_events) cudaEventDestroy(ev);
     cudaFree(c->d_err);
     cudaFree(c->d_scratch);
@@ -711,11 +713,12 @@ kl_status kl_stats(kl_ctx *ctx, char *buf, size_t n)
                      "\"cache_hits\":%lld,\"cache_misses\":%lld,\"modules\":%zu,"
                      "\"stage_ms\":{\"wisdom\":%.3f,\"nvrtc\":%.3f,\"module_load\":%.3f,"
                      "\"launch\":%.3f},\"last_config\":\"%s\",\"rules\":{%s},\"note\":\"%s\","
-                     "\"tables\":%zu}",
+                     "\"tables\":%zu,\"graphs\":%zu,\"graph_replays\":%lld}",
                      ctx->name.c_str(), ctx->cc_major, ctx->cc_minor, ctx->nsm, ctx->launches,
                      ctx->cache_hits, ctx->cache_misses, ctx->kernels.size(), ctx->t_wisdom_ms,
                      ctx->t_nvrtc_ms, ctx->t_load_ms, ctx->t_launch_ms, ctx->last_config.c_str(),
-                     rules.c_str(), ctx->last_rule_text.c_str(), ctx->tables.size());
+                     rules.c_str(), ctx->last_rule_text.c_str(), ctx->tables.size(),
+                     ctx->graphs.size(), ctx->graph_replays);
     if (m < 0 || (size_t)m >= n) return fail(KL_ERR_INVALID_ARG, "stats buffer too small");
     return KL_OK;
 }

@@ -173,6 +173,10 @@ struct kl_ctx {
     // side (forked from and joined back into the caller's stream)
     std::vector<cudaStream_t> aux_streams;
     std::vector<cudaEvent_t> aux_events;              // [0] fork, [1 + i] join of stream i
+    // one executable CUDA graph per batch (op, grids, fields) seen before
+    std::map<std::string, cudaGraphExec_t> graphs;
+    cudaStream_t cap_stream = nullptr;                // where batch graphs are recorded
+    long long graph_replays = 0;
     // statistics
     long long launches = 0, cache_hits = 0, cache_misses = 0;
     double t_wisdom_ms = 0, t_nvrtc_ms = 0, t_load_ms = 0, t_launch_ms = 0;

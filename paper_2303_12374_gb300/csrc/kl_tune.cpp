@@ -4,6 +4,7 @@
 #include <unistd.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -827,6 +828,37 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
     if (n < 1) return fail(KL_ERR_INVALID_ARG, "batch needs at least one grid");
     kl_status st = check_op(op);
     if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // the batch's identity: op, every grid (with its z profile) and every
+    // field pointer.  A batch seen before replays the CUDA graph that holds
+    // all of its launches (one graph launch), unless the caller's stream is
+    // itself being captured, in which case the launches go into that capture.
+    uint64_t bh = 1469598103934665603ull;
+    auto mix = [&](const void *p, size_t nb) {
+        const unsigned char *c = (const unsigned char *)p;
+        for (size_t q = 0; q < nb; ++q) bh = (bh ^ c[q]) * 1099511628211ull;
+    };
+    mix(op, sizeof *op);
+    mix(&n, sizeof n);
+    for (int i = 0; i < n; ++i) {
+        mix(&grids[i], offsetof(kl_grid, zh));
+        mix(&fields[i], sizeof fields[i]);
+        if (grids[i].zh && grids[i].nz > 0) mix(grids[i].zh, sizeof(double) * ((size_t)grids[i].nz + 1));
+    }
+    const std::string bkey = "graph:" + std::to_string(bh) + ":" + std::to_string(n);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return fail(KL_ERR_CUDA, "batch: stream query");
+    const bool capturing = cap != cudaStreamCaptureStatusNone;
+    if (!capturing) {
+        auto gi = ctx->graphs.find(bkey);
+        if (gi != ctx->graphs.end()) {
+            if (cudaGraphLaunch(gi->second, s) != cudaSuccess) return fail(KL_ERR_CUDA, "batch graph launch");
+            ctx->graph_replays++;
+            return KL_OK;
+        }
+    }
+
     // per grid: the configuration of its nearest tuned size (Sec. 4.5 rules)
     struct Item {
         Config cfg;
@@ -851,37 +883,20 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
         int zuni = grids[i].zh ? 0 : 1;
         groups[compile_defines(*op, cfg, grids[i].zbc, zuni)].push_back(i);
     }
-    cudaStream_t s = (cudaStream_t)stream;
-    // more than one configuration class: the classes run side by side on
-    // up to kBatchStreams streams forked from s and joined back into it
-    constexpr int kBatchStreams = 4;
-    const int naux = groups.size() > 1 ? (int)std::min<size_t>(groups.size(), kBatchStreams) : 0;
-    if (naux) {
-        while ((int)ctx->aux_streams.size() < naux) {
-            cudaStream_t st;
-            if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
-                return fail(KL_ERR_CUDA, "batch stream creation");
-            ctx->aux_streams.push_back(st);
-        }
-        while ((int)ctx->aux_events.size() < 1 + naux) {
-            cudaEvent_t ev;
-            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
-                return fail(KL_ERR_CUDA, "batch event creation");
-            ctx->aux_events.push_back(ev);
-        }
-        if (cudaEventRecord(ctx->aux_events[0], s) != cudaSuccess)
-            return fail(KL_ERR_CUDA, "batch fork");
-        for (int i = 0; i < naux; ++i)
-            if (cudaStreamWaitEvent(ctx->aux_streams[i], ctx->aux_events[0], 0) != cudaSuccess)
-                return fail(KL_ERR_CUDA, "batch fork");
-    }
-    int gi = 0;
+
+    // per configuration class: its device table [descriptors | argument
+    // blocks | tile list] (uploaded once per content) and its compiled kernel
+    struct Launch {
+        Kernel *k;
+        Config cfg;
+        size_t nblocks;
+        void *argv, *tl, *tm;
+    };
+    std::vector<Launch> plan;
     for (auto &gp : groups) {
-        cudaStream_t ls = naux ? ctx->aux_streams[gi++ % naux] : s;
         const std::vector<int> &ids = gp.second;
         const Config &cfg = items[ids[0]].cfg;
         const kl_grid &g0 = grids[ids[0]];
-        // host image of the table: [descriptors | argument blocks | tile list]
         std::vector<int> tiles;                 // 4 ints per block
         for (size_t q = 0; q < ids.size(); ++q) {
             const KArgs &a = items[ids[q]].a;
@@ -917,8 +932,6 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
             memcpy(img.data() + off_args + q * sizeof(KArgs), &items[ids[q]].a, sizeof(KArgs));
         }
         memcpy(img.data() + off_tiles, tiles.data(), tiles.size() * sizeof(int));
-        // cached per table content: a time loop re-launching the same batch
-        // uploads its table once
         uint64_t h = 1469598103934665603ull;
         for (char c : gp.first) h = (h ^ (unsigned char)c) * 1099511628211ull;
         for (char c : img) h = (h ^ (unsigned char)c) * 1099511628211ull;
@@ -928,12 +941,16 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
         if (it != ctx->tables.end()) {
             dev = it->second.first;
         } else {
-            if (ctx->tables.size() > 64) {              // bound the cache
+            if (ctx->tables.size() > 64) {              // bound the cache (graphs use tables)
+                if (capturing) return fail(KL_ERR_UNSUPPORTED, "batch table cache full while capturing");
                 cudaStreamSynchronize(s);
-                for (cudaStream_t st : ctx->aux_streams) cudaStreamSynchronize(st);
+                for (cudaStream_t st2 : ctx->aux_streams) cudaStreamSynchronize(st2);
+                for (auto &gr : ctx->graphs) cudaGraphExecDestroy(gr.second);
+                ctx->graphs.clear();
                 for (auto &t : ctx->tables) cudaFree(t.second.first);
                 ctx->tables.clear();
             }
+            if (capturing) return fail(KL_ERR_UNSUPPORTED, "a new batch cannot upload its table while the stream is captured");
             if (cudaMalloc(&dev, total) != cudaSuccess) return fail(KL_ERR_OOM, "batch table allocation");
             cudaError_t e = cudaMemcpy(dev, img.data(), total, cudaMemcpyHostToDevice);
             if (e != cudaSuccess) {
@@ -946,25 +963,87 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
         st = get_kernel(ctx, *op, cfg, g0.zbc, g0.zh ? 0 : 1, &k, true);
         if (st) return st;
         char *base = (char *)dev;
-        void *argv = base + off_args, *tl = base + off_tiles, *tm = base + off_maps;
-        CUresult r;
-        if (cfg.family == 0) {
-            void *params[] = {&argv, &tl};
-            r = ctx->drv.LaunchKernel(k->fn, (unsigned)nblocks, 1, 1, cfg.bx, cfg.by, cfg.bz, 0,
-                                      (CUstream)ls, params, nullptr);
-        } else {
-            void *params[] = {&argv, &tl, &tm};
-            r = ctx->drv.LaunchKernel(k->fn, (unsigned)nblocks, 1, 1, cfg.mbx, zmarch_block_y(cfg), 1,
-                                      (unsigned)k->smem, (CUstream)ls, params, nullptr);
+        plan.push_back({k, cfg, nblocks, base + off_args, base + off_tiles, base + off_maps});
+    }
+
+    // streams: with several configuration classes, the classes run side by
+    // side on up to kBatchStreams streams forked from s and joined back
+    constexpr int kBatchStreams = 4;
+    const int naux = plan.size() > 1 ? (int)std::min<size_t>(plan.size(), kBatchStreams) : 0;
+    while ((int)ctx->aux_streams.size() < naux) {
+        cudaStream_t st2;
+        if (cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(KL_ERR_CUDA, "batch stream creation");
+        ctx->aux_streams.push_back(st2);
+    }
+    while ((int)ctx->aux_events.size() < 1 + naux) {
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+            return fail(KL_ERR_CUDA, "batch event creation");
+        ctx->aux_events.push_back(ev);
+    }
+    // all launches of the batch, forked from and joined back into `root`
+    auto issue_all = [&](cudaStream_t root) -> kl_status {
+        if (naux) {
+            if (cudaEventRecord(ctx->aux_events[0], root) != cudaSuccess) return fail(KL_ERR_CUDA, "batch fork");
+            for (int i = 0; i < naux; ++i)
+                if (cudaStreamWaitEvent(ctx->aux_streams[i], ctx->aux_events[0], 0) != cudaSuccess)
+                    return fail(KL_ERR_CUDA, "batch fork");
         }
-        if (r != CUDA_SUCCESS) return cu_fail(r, "cuLaunchKernel (batch)");
-        ctx->launches++;
+        for (size_t q = 0; q < plan.size(); ++q) {
+            const Launch &L = plan[q];
+            cudaStream_t ls = naux ? ctx->aux_streams[q % naux] : root;
+            void *argv = L.argv, *tl = L.tl, *tm = L.tm;
+            CUresult r;
+            if (L.cfg.family == 0) {
+                void *params[] = {&argv, &tl};
+                r = ctx->drv.LaunchKernel(L.k->fn, (unsigned)L.nblocks, 1, 1, L.cfg.bx, L.cfg.by,
+                                          L.cfg.bz, 0, (CUstream)ls, params, nullptr);
+            } else {
+                void *params[] = {&argv, &tl, &tm};
+                r = ctx->drv.LaunchKernel(L.k->fn, (unsigned)L.nblocks, 1, 1, L.cfg.mbx,
+                                          zmarch_block_y(L.cfg), 1, (unsigned)L.k->smem, (CUstream)ls,
+                                          params, nullptr);
+            }
+            if (r != CUDA_SUCCESS) return cu_fail(r, "cuLaunchKernel (batch)");
+            ctx->launches++;
+        }
+        for (int i = 0; i < naux; ++i) {
+            if (cudaEventRecord(ctx->aux_events[1 + i], ctx->aux_streams[i]) != cudaSuccess ||
+                cudaStreamWaitEvent(root, ctx->aux_events[1 + i], 0) != cudaSuccess)
+                return fail(KL_ERR_CUDA, "batch join");
+        }
+        return KL_OK;
+    };
+    if (capturing) return issue_all(s);
+
+    // capture the launches into a graph once (on a private stream: capture
+    // records, it runs nothing), then launch the graph on s, now and on every
+    // repeat of the batch
+    if (ctx->graphs.size() >= 16) {
+        cudaStreamSynchronize(s);
+        for (auto &gr : ctx->graphs) cudaGraphExecDestroy(gr.second);
+        ctx->graphs.clear();
     }
-    for (int i = 0; i < naux; ++i) {
-        if (cudaEventRecord(ctx->aux_events[1 + i], ctx->aux_streams[i]) != cudaSuccess ||
-            cudaStreamWaitEvent(s, ctx->aux_events[1 + i], 0) != cudaSuccess)
-            return fail(KL_ERR_CUDA, "batch join");
+    if (!ctx->cap_stream &&
+        cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(KL_ERR_CUDA, "batch: capture stream creation");
+    if (cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return fail(KL_ERR_CUDA, "batch: begin capture");
+    kl_status ist = issue_all(ctx->cap_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    if (ist) {
+        if (graph) cudaGraphDestroy(graph);
+        return ist;
     }
+    if (e != cudaSuccess || !graph) return cuda_fail(e, "batch: end capture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "batch: graph instantiate");
+    ctx->graphs[bkey] = exec;
+    if (cudaGraphLaunch(exec, s) != cudaSuccess) return fail(KL_ERR_CUDA, "batch graph launch");
     return KL_OK;
 }
 

@@ -61,10 +61,16 @@ def test_batched_matches_oracle_and_single_launches(tmp_path, oracle_mod, dtype,
         got = [[p.download(o) for o in outs] for f, p, bufs, outs, fl in probs]
         st = json.loads(kl.kl_stats(ctx))
         assert st["tables"] >= 1
-        # the same batch again reuses its device tables
+        # the same batch again reuses its device tables and replays its graph
         kl.kl_launch_batched(ctx, op, grids, fields)
         torch.cuda.synchronize()
-        assert json.loads(kl.kl_stats(ctx))["tables"] == st["tables"]
+        st2 = json.loads(kl.kl_stats(ctx))
+        assert st2["tables"] == st["tables"]
+        assert st2["graphs"] == 1 and st2["graph_replays"] == 1
+        again = [[p.download(o) for o in outs] for f, p, bufs, outs, fl in probs]
+        for a3, b3 in zip(got, again):
+            for a, b in zip(a3, b3):
+                assert np.array_equal(a, b)
         for (f, p, bufs, outs, fl), g3 in zip(probs, got):
             rin = {k: p.rounded(f[k]) for k in ("u", "v", "w")}
             ref = oracle_ref(oracle_mod, rin, f["zh"], adv=5, diff=1, walls=True, g=3)
@@ -79,6 +85,43 @@ def test_batched_matches_oracle_and_single_launches(tmp_path, oracle_mod, dtype,
             for o, a in zip(outs, g3):
                 b = p.download(o)
                 assert np.abs(a - b).max() <= TOL[p.dtype] * max(np.abs(b).max(), 1e-300)
+    finally:
+        kl.kl_destroy(ctx)
+
+
+def test_batched_inside_a_caller_capture(tmp_path):
+    """A batch seen before can be recorded into the caller's own CUDA graph:
+    its launches join the caller's capture instead of a graph of its own."""
+    import torch
+    from paper_2303_12374_gb300 import kl
+    _wisdom(tmp_path / "tendency_adv5_diff1_f32.wisdom", "f32",
+            [((32, 32, 16), "zmarch:bx=32,by=4,px=1,py=2,kc=8,ns=8,minb=2"),
+             ((80, 48, 24), "zpack:w=4,ly=2,kc=16,ns=8,minb=2")])
+    ctx = kl.kl_create(0, str(tmp_path))
+    try:
+        probs = _setup(1, False)
+        op = kl.Op(5, 1, 1, 0)
+        for f, p, bufs, outs, fl in probs:
+            kl.kl_fill_ghosts(ctx, p.dtype, p.grid, *[b.data_ptr() for b in bufs], None)
+        grids = [pr[1].grid for pr in probs]
+        fields = [pr[4] for pr in probs]
+        kl.kl_launch_batched(ctx, op, grids, fields)        # tables, kernels, own graph
+        torch.cuda.synchronize()
+        want = [[p.download(o) for o in outs] for f, p, bufs, outs, fl in probs]
+        for f, p, bufs, outs, fl in probs:
+            for o in outs:
+                o.zero_()
+        torch.cuda.synchronize()
+        side = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            kl.kl_launch_batched(ctx, op, grids, fields, side.cuda_stream)
+        g.replay()
+        torch.cuda.synchronize()
+        got = [[p.download(o) for o in outs] for f, p, bufs, outs, fl in probs]
+        for a3, b3 in zip(want, got):
+            for a, b in zip(a3, b3):
+                assert np.array_equal(a, b)
     finally:
         kl.kl_destroy(ctx)
 
