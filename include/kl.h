@@ -221,6 +221,18 @@ kl_status kl_diag(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, int32_t level
                   const void *t, const double *ref, double out[6], void *stream);
 
 /*
+ * FP64 inner product over the interior of two fields a and b (device, layout
+ * grid, both of type dtype): *out (host) = sum a(i,j,k) b(i,j,k) w_k with
+ * w_k = dz_k (level = 0, u, v and centre points), dzh_k (level = 1, w
+ * points) or 1 (level = -1).  The kinetic-energy tendency of a step (per unit
+ * dx dy) is kl_dot(u, ut, 0) + kl_dot(v, vt, 0) + kl_dot(w, wt, 1).  Products
+ * of f32 or 16-bit values are formed exactly and summed in float-float within
+ * a level, then in FP64.  Synchronises `stream`.
+ */
+kl_status kl_dot(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, int32_t level, const void *a,
+                 const void *b, double *out, void *stream);
+
+/*
  * kl_diag_noalloc: the diagnostics of kl_diag, for callers that may not
  * allocate GPU memory while they run (an application that reserves its whole
  * device-memory budget at start-up and owns the allocator, or a time loop

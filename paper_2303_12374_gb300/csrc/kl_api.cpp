@@ -701,6 +701,43 @@ kl_status kl_diag(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, int32_t level
     return KL_OK;
 }
 
+kl_status kl_dot(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, int32_t level, const void *a,
+                 const void *b, double *out, void *stream)
+{
+    if (!ctx || !a || !b || !out) return fail(KL_ERR_INVALID_ARG, "ctx, a, b and out must not be NULL");
+    if (dtype < 0 || dtype > 3 || level < -1 || level > 1)
+        return fail(KL_ERR_INVALID_ARG, "bad dtype or level");
+    kl_status st = check_grid(grid, 1, nullptr);
+    if (st) return st;
+    const double *wz = nullptr;
+    if (level >= 0) {
+        Profile *prof = nullptr;
+        st = get_profile(ctx, *grid, &prof);
+        if (st) return st;
+        wz = prof->d64 + (level == 0 ? 2 : 3) * prof->n + grid->g;
+    }
+    int nb = diag_blocks(ctx->nsm);
+    size_t need = (size_t)nb * 6 + 8;
+    if (ctx->scratch_doubles < need) {
+        cudaFree(ctx->d_scratch);
+        ctx->d_scratch = nullptr;
+        ctx->scratch_doubles = 0;
+        cudaError_t e = cudaMalloc(&ctx->d_scratch, need * sizeof(double));
+        if (e != cudaSuccess) return fail(KL_ERR_OOM, "cudaMalloc(diag scratch) failed");
+        ctx->scratch_doubles = need;
+    }
+    double *dout = ctx->d_scratch + (size_t)nb * 6;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = dot_launch(dtype, *grid, a, b, wz, ctx->d_scratch, nb, dout, s);
+    if (e != cudaSuccess) return cuda_fail(e, "dot launch");
+    e = cudaMemcpyAsync(ctx->h_out, dout, 6 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "dot readback");
+    *out = ctx->h_out[4];
+    ctx->launches += 2;
+    return KL_OK;
+}
+
 kl_status kl_stats(kl_ctx *ctx, char *buf, size_t n)
 {
     if (!ctx || !buf || !n) return fail(KL_ERR_INVALID_ARG, "bad arguments");

@@ -306,6 +306,64 @@ __global__ void __launch_bounds__(256) diag_kernel(DiagArgs a)
     reduce6(v, a.partial + 6 * (size_t)blockIdx.x);
 }
 
+// inner product sum a*b over the interior, weighted per level by wz[k] (wz
+// NULL: weight 1), in the layout of diag_kernel: f32 and 16-bit products are
+// exact FP32 pairs (p + FMA residual) summed in float-float and folded into
+// FP64 once per level; f64 products are summed in FP64.  The block's partial
+// goes to record slot 4 (the other slots are zero), which diag_final sums.
+template <typename T>
+__global__ void __launch_bounds__(256) dot_kernel(DiagArgs a, const void *bptr)
+{
+    double acc = 0.0;
+    const T *x = (const T *)a.t, *y = (const T *)bptr;
+    const int lane = (int)(threadIdx.x & 31);
+    const long long rows = (long long)a.ny * a.nz;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long per = (rows + nw - 1) / nw;
+    const long long rb = wid * per, re = rb + per < rows ? rb + per : rows;
+    if (rb < re) {
+        int k = (int)(rb / a.ny), j = (int)(rb - (long long)k * a.ny);
+        kl_ff s = {0.0f, 0.0f};
+        double ds = 0.0;
+        for (long long r = rb; r < re; ++r) {
+            const long long o0 = j * a.sj + (long long)k * a.sk;
+            if (sizeof(T) == 8) {
+                for (int i = lane; i < a.nx; i += 32) ds = fma(to_d(x[o0 + i]), to_d(y[o0 + i]), ds);
+            } else {
+                for (int i0 = lane; i0 < a.nx; i0 += 32 * 4) {
+                    float xa[4], ya[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const bool in = i0 + 32 * u < a.nx;
+                        xa[u] = in ? (float)to_d(x[o0 + i0 + 32 * u]) : 0.0f;
+                        ya[u] = in ? (float)to_d(y[o0 + i0 + 32 * u]) : 0.0f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float p = xa[u] * ya[u];
+                        const float pe = fmaf(xa[u], ya[u], -p);   // xa*ya = p + pe exactly
+                        ff_add(s, p);
+                        s.lo += pe;
+                    }
+                }
+            }
+            if (++j == a.ny || r + 1 == re) {
+                const double ls = sizeof(T) == 8 ? ds : ff_value(s);
+                acc = a.wz ? fma(ls, a.wz[k], acc) : acc + ls;
+                ds = 0.0;
+                s.hi = s.lo = 0.0f;
+                if (j == a.ny) {
+                    j = 0;
+                    ++k;
+                }
+            }
+        }
+    }
+    double v[6] = {0, 0, 0, 0, acc, 0};
+    reduce6(v, a.partial + 6 * (size_t)blockIdx.x);
+}
+
 __global__ void __launch_bounds__(256) diag_final(const double *partial, int nb, long long n, double *out)
 {
     double v[6] = {0, 0, 0, 0, 0, 0};
@@ -397,6 +455,35 @@ cudaError_t diag_launch(int dtype, const kl_grid &g, int level, const void *t, c
     case 2 * KL_BF16 + 1: diag_kernel<__nv_bfloat16, true><<<nblocks, 256, 0, s>>>(a); break;
     case 2 * KL_F16: diag_kernel<__half, false><<<nblocks, 256, 0, s>>>(a); break;
     default: diag_kernel<__half, true><<<nblocks, 256, 0, s>>>(a); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    diag_final<<<1, 256, 0, s>>>(scratch, nblocks, a.n, dout);
+    return cudaGetLastError();
+}
+
+cudaError_t dot_launch(int dtype, const kl_grid &g, const void *x, const void *y,
+                       const double *wz, double *scratch, int nblocks, double *dout,
+                       cudaStream_t s)
+{
+    int es = esize_of(dtype);
+    DiagArgs a;
+    a.t = (const char *)x + (size_t)g.origin * es;
+    a.ref = nullptr;
+    a.wz = wz;
+    a.sj = g.sj;
+    a.sk = g.sk;
+    a.nx = g.nx;
+    a.ny = g.ny;
+    a.nz = g.nz;
+    a.n = (long long)g.nx * g.ny * g.nz;
+    a.partial = scratch;
+    const void *yb = (const char *)y + (size_t)g.origin * es;
+    switch (dtype) {
+    case KL_F64: dot_kernel<double><<<nblocks, 256, 0, s>>>(a, yb); break;
+    case KL_F32: dot_kernel<float><<<nblocks, 256, 0, s>>>(a, yb); break;
+    case KL_BF16: dot_kernel<__nv_bfloat16><<<nblocks, 256, 0, s>>>(a, yb); break;
+    default: dot_kernel<__half><<<nblocks, 256, 0, s>>>(a, yb); break;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

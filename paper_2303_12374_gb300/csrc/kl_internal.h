@@ -210,6 +210,9 @@ cudaError_t diag_launch(int dtype, const kl_grid &g, int level, const void *t,
                         const double *ref, const double *wz, double *scratch, int nblocks,
                         double *dout, cudaStream_t s);
 int diag_blocks(int nsm);
+cudaError_t dot_launch(int dtype, const kl_grid &g, const void *x, const void *y,
+                       const double *wz, double *scratch, int nblocks, double *dout,
+                       cudaStream_t s);
 cudaError_t compare_launch(int dtype, const kl_grid &g, const void *a, const void *b,
                            unsigned long long *dout, int nsm, cudaStream_t s);
 // load a compiled cubin into the context's cache under its compile key

@@ -71,6 +71,8 @@ SIGNATURES = {
     "kl_tune": ([_P, _S, _S, _S], ctypes.c_int),
     "kl_diag": ([_P, _I32, ctypes.POINTER(Grid), _I32, _P, _P, ctypes.POINTER(_D), _P],
                 ctypes.c_int),
+    "kl_dot": ([_P, _I32, ctypes.POINTER(Grid), _I32, _P, _P, ctypes.POINTER(_D), _P],
+               ctypes.c_int),
     "kl_diag_noalloc": ([_I32, ctypes.POINTER(Grid), _P, _P, _P, ctypes.POINTER(_D), _P],
                         ctypes.c_int),
     "kl_stats": ([_P, ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
@@ -185,6 +187,13 @@ def kl_diag(ctx, dtype, grid: Grid, level, t, ref=None, stream=None):
     out = (ctypes.c_double * 6)()
     check(load().kl_diag(ctx, dtype, ctypes.byref(grid), level, t, ref, out, stream))
     return list(out)
+
+
+def kl_dot(ctx, dtype, grid: Grid, level, a, b, stream=None) -> float:
+    """FP64 sum over the interior of a*b, weighted per level (0: dz, 1: dzh, -1: none)."""
+    out = ctypes.c_double()
+    check(load().kl_dot(ctx, dtype, ctypes.byref(grid), level, a, b, ctypes.byref(out), stream))
+    return out.value
 
 
 def kl_diag_noalloc(dtype, grid: Grid, t, ref=None, wz=None, stream=None):

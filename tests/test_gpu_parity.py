@@ -246,6 +246,69 @@ def test_diag_matches_oracle(ctx, oracle_mod):
             assert got[c] == pytest.approx(want[c], rel=1e-9, abs=1e-9 * np.abs(t).sum())
 
 
+@pytest.mark.parametrize("dtype", [0, 1, 2])
+def test_diag_without_reference(ctx, oracle_mod, dtype):
+    """No reference: f32 and 16-bit sums run in float-float, folded into FP64
+    per level; they must match an FP64 reduction of the same values."""
+    nx, ny, nz = 70, 33, 21
+    f = make_inputs(nx, ny, nz, seed=19, walls=True, stretch=2.0)
+    from paper_2303_12374_gb300 import kl
+    p, _, outs, _ = run_gpu(ctx, f, adv=5, diff=1, dtype=dtype, walls=True, g=3, stretched=True)
+    dz, dzh = oracle_mod.zprofile(nz, 3, True, f["zh"])
+    for level, name in ((0, "ut"), (1, "wt")):
+        got = kl.kl_diag(ctx, p.dtype, p.grid, level, outs[name].data_ptr(), None)
+        t = p.download(outs[name])
+        wgt = np.broadcast_to((dz if level == 0 else dzh)[3:3 + nz][:, None, None], t.shape)
+        want = oracle_mod.diag(t, None, wgt)
+        assert got[0] == want[0]
+        assert got[2] == 0.0 and got[3] == 0.0
+        assert got[1] == pytest.approx(want[1], rel=1e-12)
+        scale = np.abs(t).sum()
+        assert abs(got[4] - want[4]) <= 1e-12 * scale
+        assert abs(got[5] - want[5]) <= 1e-12 * np.abs(t * wgt).sum()
+
+
+@pytest.mark.parametrize("dtype", [0, 1, 2])
+def test_dot_matches_fp64(ctx, oracle_mod, dtype):
+    from paper_2303_12374_gb300 import kl
+    nx, ny, nz = 45, 38, 17
+    f = make_inputs(nx, ny, nz, seed=23, walls=True, stretch=2.0)
+    p, bufs, outs, rin = run_gpu(ctx, f, adv=5, diff=1, dtype=dtype, walls=True, g=3,
+                                 stretched=True)
+    dz, dzh = oracle_mod.zprofile(nz, 3, True, f["zh"])
+    for level, a, b in ((0, "u", "ut"), (1, "w", "wt"), (-1, "v", "vt")):
+        x, y = rin[a], p.download(outs[b])
+        wz = {0: dz, 1: dzh}.get(level)
+        wgt = np.ones(nz) if wz is None else wz[3:3 + nz]
+        prod = x * y * wgt[:, None, None]
+        got = kl.kl_dot(ctx, p.dtype, p.grid, level, bufs[a].data_ptr(), outs[b].data_ptr())
+        assert abs(got - prod.sum()) <= 1e-12 * np.abs(prod).sum(), (level, got, prod.sum())
+
+
+def test_energy_on_gpu():
+    """The kinetic-energy tendency from kl_dot: zero to rounding for the
+    centred 2nd-order scheme on a discretely divergence-free periodic field,
+    negative for the upwind-biased 5th-order scheme (f64 storage)."""
+    import torch
+    from paper_2303_12374_gb300 import kl
+    pins = pytest.importorskip("test_oracle_pins")
+    f = pins.divergence_free(n=(24, 20, 16))
+    c = kl.kl_create(0, None)
+    try:
+        for adv, g in ((2, 1), (5, 3)):
+            p, bufs, outs, _ = run_gpu(c, f, adv=adv, diff=0, dtype=0, walls=False, g=g)
+            e = sum(kl.kl_dot(c, 0, p.grid, lv, bufs[a].data_ptr(), outs[b].data_ptr())
+                    for lv, a, b in ((0, "u", "ut"), (0, "v", "vt"), (1, "w", "wt")))
+            terms = sum(np.abs(f[a] * p.download(outs[b])).sum()
+                        for a, b in (("u", "ut"), ("v", "vt"), ("w", "wt"))) / 16
+            if adv == 2:
+                assert abs(e) <= 1e-12 * terms, e
+            else:
+                assert e < -1e-3 * terms, e
+    finally:
+        kl.kl_destroy(c)
+
+
 def test_second_launch_is_cached(ctx):
     import json
     from paper_2303_12374_gb300 import kl
