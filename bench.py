@@ -379,7 +379,7 @@ def workload_sweep(ctx, device, stream, reps):
     return out
 
 
-def diag_timing(ctx, p, outs, stream, reps=20):
+def diag_timing(ctx, p, outs, stream, reps=20, ins=None):
     """kl_diag (FP64 max, rms, sums, metric-weighted sum) on one 256^3 tendency,
     per call including the 48-byte read-back it synchronises on."""
     import torch
@@ -394,8 +394,16 @@ def diag_timing(ctx, p, outs, stream, reps=20):
     b.record(stream)
     torch.cuda.synchronize()
     us = a.elapsed_time(b) / reps * 1e3
-    nbytes = p.nx * p.ny * p.nz * outs[0].element_size()
-    return {"us": us, "read_gbs": nbytes / us / 1e3, "values": list(out)}
+    nbytes = p.nx * p.nz * p.ny * outs[0].element_size()
+    res = {"us": us, "read_gbs": nbytes / us / 1e3, "values": list(out)}
+    if ins is not None:
+        # kinetic-energy tendency of the step (three FP64 inner products)
+        t0 = time.perf_counter()
+        energy = sum(kl.kl_dot(ctx, p.dtype, p.grid, lv, x.data_ptr(), y.data_ptr(), stream.cuda_stream)
+                     for lv, x, y in ((0, ins[0], outs[0]), (0, ins[1], outs[1]), (1, ins[2], outs[2])))
+        res["energy_tendency"] = energy
+        res["energy_host_us"] = (time.perf_counter() - t0) * 1e6
+    return res
 
 
 def batched_run(ctx, device, stream, reps=20):
@@ -579,7 +587,7 @@ def main():
         extras["batched"] = batched_run(ctx, device, stream)
         extras["workloads"] = workload_sweep(ctx, device, stream, max(20, args.steps // 20))
         extras["launch_overhead"] = launch_overhead(local, wisdom, device)
-        extras["diag"] = diag_timing(ctx, p, outs, stream)
+        extras["diag"] = diag_timing(ctx, p, outs, stream, ins=ins)
 
     # --- end to end through the public API with pinned host buffers (every rank)
     barrier()
