@@ -41,7 +41,7 @@ typedef int kl_status;
 #define KL_ERR_NVRTC        -3   /* run-time compilation failed; log in kl_last_error */
 #define KL_ERR_IO           -4   /* a file could not be read or written */
 #define KL_ERR_WISDOM_PARSE -5   /* malformed wisdom or capture file */
-#define KL_ERR_UNSUPPORTED  -6   /* valid request this build or device cannot run */
+#define KL_ERR_UNSUPPORTED  -6   /* valid request the library or device cannot run */
 #define KL_ERR_BOUNDS       -7   /* strides/extent do not hold the stencil footprint */
 #define KL_ERR_TIMEOUT      -8   /* a bounded device wait gave up */
 #define KL_ERR_OOM          -9   /* a library-internal allocation failed */
