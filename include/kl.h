@@ -55,13 +55,16 @@ typedef enum { KL_F64 = 0, KL_F32 = 1, KL_BF16 = 2, KL_F16 = 3 } kl_dtype;
  * 1 constant-nu Laplacian, 2 variable-nu stress divergence (the Smagorinsky
  * diffusion of Sec. 5.2 with a given nu field).  dtype: storage type of every
  * field; f64 computes in f64, the others in f32.  accumulate: 0 writes
- * t = tendency, 1 adds t += tendency.
+ * t = tendency, 1 adds t += tendency.  out_f32: with 16-bit storage, 1 keeps
+ * the tendencies in f32 buffers (no output rounding to 16 bits); 0 (and
+ * always for f32 and f64) stores them in dtype.
  */
 typedef struct {
     int32_t adv;
     int32_t diff;
     int32_t dtype;
     int32_t accumulate;
+    int32_t out_f32;    /* 1: ut, vt, wt are f32 buffers (16-bit dtype only); 0: dtype */
 } kl_op;
 
 /*

@@ -242,6 +242,10 @@ kl_status check_op(const kl_op *op)
         return fail(KL_ERR_INVALID_ARG, "dtype must be 0..3");
     if (op->accumulate != 0 && op->accumulate != 1)
         return fail(KL_ERR_INVALID_ARG, "accumulate must be 0 or 1");
+    if (op->out_f32 != 0 && op->out_f32 != 1)
+        return fail(KL_ERR_INVALID_ARG, "out_f32 must be 0 or 1");
+    if (op->out_f32 && op->dtype != KL_BF16 && op->dtype != KL_F16)
+        return fail(KL_ERR_INVALID_ARG, "out_f32 applies to 16-bit storage (bf16, f16)");
     return KL_OK;
 }
 
@@ -251,10 +255,13 @@ kl_status check_fields(const kl_op &op, const kl_fields *f)
     if (!f->u || !f->v || !f->w || !f->ut || !f->vt || !f->wt)
         return fail(KL_ERR_INVALID_ARG, "a field pointer is NULL");
     if (op.diff == 2 && !f->nu) return fail(KL_ERR_INVALID_ARG, "diff = 2 needs the nu field");
-    int es = esize_of(op.dtype);
-    const void *ps[] = {f->u, f->v, f->w, f->ut, f->vt, f->wt, op.diff == 2 ? f->nu : f->u};
+    const uintptr_t es = (uintptr_t)esize_of(op.dtype), eo = (uintptr_t)esize_of(out_dtype(op));
+    const void *ps[] = {f->u, f->v, f->w, op.diff == 2 ? f->nu : f->u};
     for (const void *p : ps)
-        if ((uintptr_t)p % (uintptr_t)es) return fail(KL_ERR_INVALID_ARG, "misaligned field pointer");
+        if ((uintptr_t)p % es) return fail(KL_ERR_INVALID_ARG, "misaligned field pointer");
+    const void *po[] = {f->ut, f->vt, f->wt};
+    for (const void *p : po)
+        if ((uintptr_t)p % eo) return fail(KL_ERR_INVALID_ARG, "misaligned tendency pointer");
     return KL_OK;
 }
 
@@ -353,9 +360,10 @@ kl_status make_kargs(kl_ctx *ctx, const kl_op &op, const Config &cfg, const kl_g
     a.v = base[1] + off;
     a.w = base[2] + off;
     a.nu = f.nu ? base[3] + off : nullptr;
-    a.ut = (void *)(base[4] + off);
-    a.vt = (void *)(base[5] + off);
-    a.wt = (void *)(base[6] + off);
+    size_t offo = (size_t)g.origin * esize_of(out_dtype(op));
+    a.ut = (void *)(base[4] + offo);
+    a.vt = (void *)(base[5] + offo);
+    a.wt = (void *)(base[6] + offo);
     if (prof) {
         if (op.dtype == KL_F64) {
             a.dzi = prof->d64 + g.g;

@@ -512,8 +512,8 @@ std::string compile_defines(const kl_op &op, const Config &c, int zbc, int zuni)
 {
     char b[512];
     int n = snprintf(b, sizeof b, "-DKL_DTYPE=%d -DKL_ADV=%d -DKL_DIFF=%d -DKL_ZBC=%d -DKL_ZUNI=%d "
-                     "-DKL_ACC=%d -DKL_FAMILY=%d", op.dtype, op.adv, op.diff, zbc, zuni,
-                     op.accumulate ? 1 : 0, c.family);
+                     "-DKL_ACC=%d -DKL_OF32=%d -DKL_FAMILY=%d", op.dtype, op.adv, op.diff, zbc, zuni,
+                     op.accumulate ? 1 : 0, op.out_f32 ? 1 : 0, c.family);
     if (c.family == 0) {
         snprintf(b + n, sizeof b - n,
                  " -DKL_BX=%d -DKL_BY=%d -DKL_BZ=%d -DKL_TX=%d -DKL_TY=%d -DKL_TZ=%d -DKL_UX=%d"

@@ -42,6 +42,9 @@ struct Config {
     int cs = 0;                // zpack: one warp group per tendency component (3 x w warps)
 };
 
+// storage type of the tendencies ut, vt, wt
+inline int out_dtype(const kl_op &op) { return op.out_f32 ? (int)KL_F32 : op.dtype; }
+
 // TMA descriptors per launch: u, v, w, nu with the plane box, then u, v, w
 // with the 32-byte x-wrap strip box (zpack)
 constexpr int KL_NMAPS = 7;

@@ -12,6 +12,7 @@
 //   KL_ZBC     0 periodic z, 1 free-slip walls (wt = 0 on the bottom wall face)
 //   KL_ZUNI    1 uniform dz (scalars), 0 profiles dzi[k], dzhi[k]
 //   KL_ACC     0 t = tendency, 1 t += tendency
+//   KL_OF32    1: ut, vt, wt stored as f32 (16-bit storage only), 0: as KL_DTYPE
 // Family KL_FAMILY 0 ("direct", the tunable space of Table 2):
 //   KL_BX KL_BY KL_BZ  thread-block shape
 //   KL_TX KL_TY KL_TZ  points per thread along each axis (tile factors)
@@ -49,6 +50,12 @@
 #ifndef KL_BATCH
 #define KL_BATCH 0    // 1: one launch over many grids through a device tile table
 #endif
+#ifndef KL_OF32
+#define KL_OF32 0     // 1: tendencies stored as f32 (16-bit storage of the inputs)
+#endif
+#if KL_OF32 && KL_DTYPE < 2
+#error "KL_OF32 applies to 16-bit storage"
+#endif
 
 typedef unsigned short kl_u16;
 
@@ -62,11 +69,16 @@ typedef float C;
 typedef kl_u16 T;
 typedef float C;
 #endif
+#if KL_OF32
+typedef float TO;     // storage of the tendencies
+#else
+typedef T TO;
+#endif
 
 // Kernel argument block; the host fills an identical struct (8-byte members).
 struct kl_args {
     const T *u, *v, *w, *nu;      // pointers at interior point (0,0,0)
-    T *ut, *vt, *wt;
+    TO *ut, *vt, *wt;
     const C *dzi, *dzhi;          // profiles, index k = interior level (may be < 0)
     int *err;                     // device status word (0 = ok)
     long long sj, sk;             // element strides of y and z
@@ -132,6 +144,15 @@ __device__ __forceinline__ void st(T *p, C v)
 #endif
 }
 
+#if KL_OF32
+__device__ __forceinline__ void out(TO *p, C v)
+{
+#if KL_ACC
+    v += *p;
+#endif
+    *p = v;
+}
+#else
 __device__ __forceinline__ void out(T *p, C v)
 {
 #if KL_ACC
@@ -139,6 +160,7 @@ __device__ __forceinline__ void out(T *p, C v)
 #endif
     st(p, v);
 }
+#endif
 
 // ------------------------------------------------------------ face fluxes
 //
@@ -829,6 +851,14 @@ __device__ __forceinline__ void vst(T *p, V a)
 __device__ __forceinline__ V vldg(const T *p) { return vld(p); }
 #endif
 __device__ __forceinline__ V vsplat(C a) { return vmk(a, a); }
+// aligned pair of tendencies (outputs): the storage type, or f32 (KL_OF32)
+#if KL_OF32
+__device__ __forceinline__ void vsto(TO *p, V a) { *(float2 *)p = make_float2(vlo(a), vhi(a)); }
+__device__ __forceinline__ V vldo(const TO *p) { float2 d = *(const float2 *)p; return vmk(d.x, d.y); }
+#else
+__device__ __forceinline__ void vsto(TO *p, V a) { vst(p, a); }
+__device__ __forceinline__ V vldo(const TO *p) { return vldg(p); }
+#endif
 // (hi of a, lo of b): the pair starting one element after a's
 __device__ __forceinline__ V vcross(V a, V b) { return vmk(vhi(a), vlo(b)); }
 
@@ -972,7 +1002,7 @@ __device__ __forceinline__ void kl_cs_level(const kl_args &a, const kl_vk &K, co
     }
 
     V fy_b = kl_cs_yface<CP>(K, pl, lx, r0, vkdy);
-    T *const dst = CP == 0 ? a.ut : CP == 1 ? a.vt : a.wt;
+    TO *const dst = CP == 0 ? a.ut : CP == 1 ? a.vt : a.wt;
 #pragma unroll
     for (int r = 0; r < KL_MPY; ++r) {
         const int yr = r0 + r;
@@ -1010,9 +1040,9 @@ __device__ __forceinline__ void kl_cs_level(const kl_args &a, const kl_vk &K, co
             const long long o = (long long)c0 + (long long)j * a.sj + (long long)k * a.sk;
             if (c0 + 1 < (int)a.nx) {
 #if KL_ACC
-                t = vadd(t, vldg(dst + o));
+                t = vadd(t, vldo(dst + o));
 #endif
-                vst(dst + o, t);
+                vsto(dst + o, t);
             } else if (c0 < (int)a.nx) {
                 out(dst + o, vlo(t));
             }
@@ -1513,13 +1543,13 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
                 const long long o = (long long)c0 + (long long)j * a.sj + (long long)k * a.sk;
                 if (c0 + 1 < nx) {
 #if KL_ACC
-                    tu = vadd(tu, vldg(a.ut + o));
-                    tv = vadd(tv, vldg(a.vt + o));
-                    tw = vadd(tw, vldg(a.wt + o));
+                    tu = vadd(tu, vldo(a.ut + o));
+                    tv = vadd(tv, vldo(a.vt + o));
+                    tw = vadd(tw, vldo(a.wt + o));
 #endif
-                    vst(a.ut + o, tu);
-                    vst(a.vt + o, tv);
-                    vst(a.wt + o, tw);
+                    vsto(a.ut + o, tu);
+                    vsto(a.vt + o, tv);
+                    vsto(a.wt + o, tw);
                 } else if (c0 < nx) {
                     out(a.ut + o, vlo(tu));
                     out(a.vt + o, vlo(tv));

@@ -59,7 +59,8 @@ struct Capture {
     std::string device;
     int cc_major = 0, cc_minor = 0;
     std::vector<std::string> names;
-    size_t blob_bytes = 0;
+    size_t blob_bytes = 0;          // u, v, w, nu
+    size_t out_bytes = 0;           // ut, vt, wt (accumulate)
     std::vector<std::vector<char>> blobs;
 };
 
@@ -84,11 +85,12 @@ kl_status capture_write(kl_ctx *ctx, const kl_op &op, const kl_grid &g, const kl
     std::map<std::string, const void *> ptr = {{"u", f.u}, {"v", f.v}, {"w", f.w}, {"nu", f.nu},
                                                 {"ut", f.ut}, {"vt", f.vt}, {"wt", f.wt}};
     size_t bytes = (size_t)g.extent * esize_of(op.dtype);
+    size_t obytes = (size_t)g.extent * esize_of(out_dtype(op));
     FILE *out = fopen(path.c_str(), "wb");
     if (!out) return fail(KL_ERR_IO, "capture: cannot open " + path);
     fprintf(out, "KLCAPTURE 1\n");
-    fprintf(out, "kernel=tendency adv=%d diff=%d dtype=%d accumulate=%d\n", op.adv, op.diff,
-            op.dtype, op.accumulate);
+    fprintf(out, "kernel=tendency adv=%d diff=%d dtype=%d accumulate=%d out_f32=%d\n", op.adv,
+            op.diff, op.dtype, op.accumulate, op.out_f32);
     fprintf(out, "nx=%d ny=%d nz=%d g=%d sj=%lld sk=%lld origin=%lld extent=%lld zbc=%d\n", g.nx,
             g.ny, g.nz, g.g, (long long)g.sj, (long long)g.sk, (long long)g.origin,
             (long long)g.extent, g.zbc);
@@ -101,15 +103,16 @@ kl_status capture_write(kl_ctx *ctx, const kl_op &op, const kl_grid &g, const kl
             ctx->cc_minor, now_iso().c_str(), host_name().c_str());
     std::string list;
     for (auto &n : names) list += (list.empty() ? "" : ",") + n;
-    fprintf(out, "blobs=%s bytes=%zu\nEND\n", list.c_str(), bytes);
-    std::vector<char> host(bytes);
+    fprintf(out, "blobs=%s bytes=%zu obytes=%zu\nEND\n", list.c_str(), bytes, obytes);
+    std::vector<char> host(std::max(bytes, obytes));
     for (auto &n : names) {
-        e = cudaMemcpy(host.data(), ptr[n], bytes, cudaMemcpyDeviceToHost);
+        const size_t nb = (n == "ut" || n == "vt" || n == "wt") ? obytes : bytes;
+        e = cudaMemcpy(host.data(), ptr[n], nb, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) {
             fclose(out);
             return cuda_fail(e, "capture: device to host copy");
         }
-        if (fwrite(host.data(), 1, bytes, out) != bytes) {
+        if (fwrite(host.data(), 1, nb, out) != nb) {
             fclose(out);
             return fail(KL_ERR_IO, "capture: short write to " + path);
         }
@@ -215,7 +218,10 @@ kl_status capture_read(const std::string &path, Capture *c)
         fclose(in);
         return fail(KL_ERR_WISDOM_PARSE, "capture: header lacks a field: " + path);
     }
-    c->op = kl_op{(int)adv, (int)diff, (int)dtype, (int)acc};
+    long long of32 = 0, obytes = 0;
+    if (!geti("out_f32", &of32)) of32 = 0;          // captures written before the field
+    c->op = kl_op{(int)adv, (int)diff, (int)dtype, (int)acc, (int)of32};
+    if (!geti("obytes", &obytes)) obytes = (long long)extent * esize_of(out_dtype(c->op));
     c->zh = zh;
     kl_grid &G = c->grid;
     memset(&G, 0, sizeof G);
@@ -233,13 +239,16 @@ kl_status capture_read(const std::string &path, Capture *c)
     std::string n;
     while (std::getline(ss, n, ',')) c->names.push_back(n);
     if (c->names != capture_blob_names(c->op) ||
-        (size_t)bytes != (size_t)extent * esize_of((int)dtype)) {
+        (size_t)bytes != (size_t)extent * esize_of((int)dtype) ||
+        (size_t)obytes != (size_t)extent * esize_of(out_dtype(c->op))) {
         fclose(in);
         return fail(KL_ERR_WISDOM_PARSE, "capture: blob list or size does not match the op");
     }
     c->blob_bytes = (size_t)bytes;
+    c->out_bytes = (size_t)obytes;
     for (size_t q = 0; q < c->names.size(); ++q) {
-        std::vector<char> b(c->blob_bytes);
+        const std::string &bn = c->names[q];
+        std::vector<char> b(bn == "ut" || bn == "vt" || bn == "wt" ? c->out_bytes : c->blob_bytes);
         if (fread(b.data(), 1, b.size(), in) != b.size()) {
             fclose(in);
             return fail(KL_ERR_WISDOM_PARSE, "capture: truncated data in " + path);
@@ -302,7 +311,7 @@ struct Replay {
     void *ref[3] = {nullptr, nullptr, nullptr};
     void *init[3] = {nullptr, nullptr, nullptr};   // accumulate: pristine outputs
     unsigned long long *cmp = nullptr;
-    size_t bytes = 0;
+    size_t bytes = 0, obytes = 0;
     ~Replay()
     {
         for (void *p : in) cudaFree(p);
@@ -415,7 +424,7 @@ static kl_status verify(kl_ctx *ctx, const kl_op &op, const kl_grid &g, Replay &
 {
     double worst = 0;
     for (int q = 0; q < 3; ++q) {
-        cudaError_t e = compare_launch(op.dtype, g, R.out[q], R.ref[q], R.cmp, ctx->nsm, 0);
+        cudaError_t e = compare_launch(out_dtype(op), g, R.out[q], R.ref[q], R.cmp, ctx->nsm, 0);
         unsigned long long h[2];
         if (e == cudaSuccess) e = cudaMemcpy(h, R.cmp, sizeof h, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "tune: verify");
@@ -433,7 +442,7 @@ static kl_status reset_outputs(const kl_op &op, Replay &R)
 {
     if (!op.accumulate) return KL_OK;
     for (int q = 0; q < 3; ++q) {
-        cudaError_t e = cudaMemcpy(R.out[q], R.init[q], R.bytes, cudaMemcpyDeviceToDevice);
+        cudaError_t e = cudaMemcpy(R.out[q], R.init[q], R.obytes, cudaMemcpyDeviceToDevice);
         if (e != cudaSuccess) return cuda_fail(e, "tune: reset outputs");
     }
     return KL_OK;
@@ -537,7 +546,9 @@ kl_status kl_tune(kl_ctx *ctx, const char *capture_path, const char *opts, const
     // device buffers
     Replay R;
     R.bytes = C.blob_bytes;
+    R.obytes = C.out_bytes;
     auto alloc = [&](void **p) { return cudaMalloc(p, R.bytes); };
+    auto alloc_out = [&](void **p) { return cudaMalloc(p, R.obytes); };
     size_t nin = op.diff == 2 ? 4 : 3;
     for (size_t q = 0; q < nin; ++q) {
         void *p = nullptr;
@@ -547,14 +558,14 @@ kl_status kl_tune(kl_ctx *ctx, const char *capture_path, const char *opts, const
             return fail(KL_ERR_CUDA, "tune: upload failed");
     }
     for (int q = 0; q < 3; ++q) {
-        if (alloc(&R.out[q]) != cudaSuccess || alloc(&R.ref[q]) != cudaSuccess)
+        if (alloc_out(&R.out[q]) != cudaSuccess || alloc_out(&R.ref[q]) != cudaSuccess)
             return fail(KL_ERR_OOM, "tune: device allocation failed");
-        cudaMemset(R.out[q], 0, R.bytes);
-        cudaMemset(R.ref[q], 0, R.bytes);
+        cudaMemset(R.out[q], 0, R.obytes);
+        cudaMemset(R.ref[q], 0, R.obytes);
         if (op.accumulate) {
-            if (alloc(&R.init[q]) != cudaSuccess) return fail(KL_ERR_OOM, "tune: allocation failed");
-            cudaMemcpy(R.init[q], C.blobs[nin + q].data(), R.bytes, cudaMemcpyHostToDevice);
-            cudaMemcpy(R.ref[q], R.init[q], R.bytes, cudaMemcpyDeviceToDevice);
+            if (alloc_out(&R.init[q]) != cudaSuccess) return fail(KL_ERR_OOM, "tune: allocation failed");
+            cudaMemcpy(R.init[q], C.blobs[nin + q].data(), R.obytes, cudaMemcpyHostToDevice);
+            cudaMemcpy(R.ref[q], R.init[q], R.obytes, cudaMemcpyDeviceToDevice);
         }
     }
     if (cudaMalloc(&R.cmp, 2 * sizeof(unsigned long long)) != cudaSuccess)
@@ -569,7 +580,7 @@ kl_status kl_tune(kl_ctx *ctx, const char *capture_path, const char *opts, const
         if (cudaDeviceSynchronize() != cudaSuccess) return fail(KL_ERR_CUDA, "tune: reference run failed");
     }
     double tol = O.verify_tol > 0 ? O.verify_tol
-                 : op.dtype == KL_F64 ? 1e-10 : op.dtype == KL_F32 ? 1e-4 : 2e-2;
+                 : op.dtype == KL_F64 ? 1e-10 : out_dtype(op) == KL_F32 ? 1e-4 : 2e-2;
 
     // candidates
     std::mt19937_64 rng(O.seed);

@@ -28,7 +28,7 @@ class KLError(RuntimeError):
 
 class Op(ctypes.Structure):
     _fields_ = [("adv", ctypes.c_int32), ("diff", ctypes.c_int32), ("dtype", ctypes.c_int32),
-                ("accumulate", ctypes.c_int32)]
+                ("accumulate", ctypes.c_int32), ("out_f32", ctypes.c_int32)]
 
 
 class Grid(ctypes.Structure):

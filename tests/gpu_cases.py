@@ -32,11 +32,12 @@ def poison_x_ghosts(p, buf):
 
 
 def run_gpu(ctx, f, *, adv, diff, dtype, walls, g, config=None, nu=1e-3, stretched=False,
-            accumulate=False, t0=None, poison_x=False, step=False):
+            accumulate=False, t0=None, poison_x=False, step=False, out_f32=False):
     """Fill ghosts + tendency through the C ABI; returns (prob, rounded inputs, outputs).
 
     poison_x: NaN into the x ghosts of interior rows after the fill (before the
-    launch); step: one kl_step call (its own fill) instead of fill + launch."""
+    launch); step: one kl_step call (its own fill) instead of fill + launch;
+    out_f32: f32 tendency buffers (16-bit storage)."""
     import torch
     from paper_2303_12374_gb300 import kl
     from paper_2303_12374_gb300.problem import Problem
@@ -48,15 +49,16 @@ def run_gpu(ctx, f, *, adv, diff, dtype, walls, g, config=None, nu=1e-3, stretch
     if diff == 2:
         bufs["nu"] = p.upload(f["nu"])
     outs = {}
+    odt = torch.float32 if out_f32 else None
     for k in ("ut", "vt", "wt"):
-        outs[k] = p.upload(t0[k]) if t0 is not None else p.empty()
+        outs[k] = p.upload(t0[k], dtype=odt) if t0 is not None else p.empty(odt)
     if not step:
         kl.kl_fill_ghosts(ctx, p.dtype, p.grid, bufs["u"].data_ptr(), bufs["v"].data_ptr(),
                           bufs["w"].data_ptr(), bufs["nu"].data_ptr() if diff == 2 else None)
     if poison_x:
         for k in ("u", "v", "w"):
             poison_x_ghosts(p, bufs[k])
-    op = kl.Op(adv, diff, p.dtype, 1 if accumulate else 0)
+    op = kl.Op(adv, diff, p.dtype, 1 if accumulate else 0, 1 if out_f32 else 0)
     fl = kl.Fields(bufs["u"].data_ptr(), bufs["v"].data_ptr(), bufs["w"].data_ptr(),
                    bufs["nu"].data_ptr() if diff == 2 else None, outs["ut"].data_ptr(),
                    outs["vt"].data_ptr(), outs["wt"].data_ptr())

@@ -184,6 +184,33 @@ def test_zpack_variable_nu(ctx, oracle_mod, dtype, nx, ny, nz, walls, adv, stret
     assert ran
 
 
+@pytest.mark.parametrize("dtype", [2, 3])
+@pytest.mark.parametrize("config", ["default", "zmarch:bx=32,by=4,px=1,py=2,kc=8,ns=8,minb=1",
+                                    "zpack:w=4,ly=2,kc=8,ns=8,minb=1",
+                                    "zpack:w=2,ly=2,kc=8,ns=8,minb=1,cs=1"])
+@pytest.mark.parametrize("diff,acc", [(1, False), (2, False), (1, True)])
+def test_16bit_storage_f32_tendencies(ctx, oracle_mod, dtype, config, diff, acc):
+    """16-bit storage with f32 tendencies (out_f32): the inputs are exact in
+    f32, so the only error left is the f32 arithmetic (the f32 bound)."""
+    from paper_2303_12374_gb300 import kl
+    try:
+        kl.kl_config_normalize(kl.Op(5, diff, dtype, 0), config)
+    except kl.KLError:
+        pytest.skip("configuration outside the space for this op")
+    nx, ny, nz = 70, 29, 13
+    f = make_inputs(nx, ny, nz, seed=31, walls=True, stretch=2.0, var_nu=diff == 2)
+    rng = np.random.default_rng(5)
+    t0 = {k: rng.standard_normal((nz, ny, nx)) for k in ("ut", "vt", "wt")} if acc else None
+    p, _, outs, rin = run_gpu(ctx, f, adv=5, diff=diff, dtype=dtype, walls=True, g=3,
+                              stretched=True, config=config, out_f32=True, accumulate=acc, t0=t0)
+    ref = oracle_ref(oracle_mod, rin, f["zh"], adv=5, diff=diff, walls=True, g=3)
+    for name, r in zip(("ut", "vt", "wt"), ref):
+        if acc:
+            r = r + t0[name].astype(np.float32)
+        e = rel_err(p.download(outs[name]), r)
+        assert e <= TOL[1], (config, name, e)
+
+
 def test_accumulate(ctx, oracle_mod):
     nx, ny, nz = 30, 20, 12
     f = make_inputs(nx, ny, nz, seed=3, walls=True)

@@ -63,6 +63,32 @@ def test_capture_file_holds_definition_and_data(ctx, tmp_path, diff):
     assert np.array_equal(u, bufs["u"].cpu().numpy())
 
 
+def test_tune_16bit_storage_with_f32_tendencies(ctx, tmp_path):
+    """A capture of an accumulating bf16 op with f32 tendencies carries the f32
+    output blobs; tuning replays it and verifies candidates in f32."""
+    import torch
+    from paper_2303_12374_gb300 import kl
+    nx, ny, nz = 40, 24, 12
+    f = make_inputs(nx, ny, nz, seed=3, walls=True)
+    rng = np.random.default_rng(1)
+    t0 = {k: rng.standard_normal((nz, ny, nx)) for k in ("ut", "vt", "wt")}
+    p, bufs, outs, rin = run_gpu(ctx, f, adv=5, diff=1, dtype=2, walls=True, g=3,
+                                 accumulate=True, t0=t0, out_f32=True)
+    op = kl.Op(5, 1, 2, 1, 1)
+    cap = str(tmp_path / "c.klcap")
+    kl.kl_capture(ctx, op, p.grid, _fields(p, bufs, outs, 1), cap)
+    head = _header(cap)
+    assert b"out_f32=1" in head
+    # u, v, w in bf16, ut, vt, wt in f32
+    assert os.path.getsize(cap) == len(head) + 3 * p.extent * 2 + 3 * p.extent * 4
+    wpath = str(tmp_path / "tendency_adv5_diff1_bf16.wisdom")
+    log = str(tmp_path / "tune.jsonl")
+    kl.kl_tune(ctx, cap, f"strategy=random max_evals=5 budget_s=60 seed=2 log={log}", wpath)
+    evals = [json.loads(l) for l in open(log)]
+    assert any(e["ok"] for e in evals)
+    assert all(e["err"] <= 1e-4 for e in evals if e["ok"])
+
+
 def test_capture_env_hook(ctx, tmp_path, monkeypatch):
     from paper_2303_12374_gb300 import kl
     monkeypatch.setenv("KERNEL_LAUNCHER_CAPTURE", "other,tendency")

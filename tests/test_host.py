@@ -109,6 +109,15 @@ def test_nvrtc_compiles_tiled_configs():
     assert re.search(r"(\d+) bytes spill stores", log) is not None
 
 
+def test_out_f32_only_with_16bit_storage():
+    for dt in (0, 1):
+        with pytest.raises(kl.KLError) as e:
+            kl.kl_compile_only(kl.Op(5, 1, dt, 0, 1), "default", 1, 1)
+        assert "16-bit" in str(e.value)
+    log = kl.kl_compile_only(kl.Op(5, 1, 2, 0, 1), "zpack:w=4,ly=2,kc=16,ns=8,minb=2", 1, 1)
+    assert "registers" in log
+
+
 def test_zpack_variable_nu_needs_cs0_yx0():
     for bad in ("zpack:w=4,ly=2,cs=1", "zpack:w=4,ly=2,yx=1"):
         with pytest.raises(kl.KLError):
