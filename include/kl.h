@@ -295,6 +295,20 @@ kl_status kl_wisdom_append(const char *path, const char *device, int32_t cc_majo
                            int32_t cc_minor, int32_t zbc, int32_t nx, int32_t ny, int32_t nz,
                            const char *config, double time_us, const char *extra);
 
+/*
+ * Failure detection.  Every device wait of the kernels (for a TMA copy into
+ * shared memory) is bounded; a wait that gives up makes its CTA record
+ * KL_ERR_TIMEOUT in the context's device status word, wait (bounded) for its
+ * copies still in flight and return, so the GPU and the context stay usable.
+ * kl_check synchronises `stream`, reads and clears that word: KL_OK, or
+ * KL_ERR_TIMEOUT when a launch since the last check gave up somewhere (its
+ * outputs are then incomplete).  kl_set_wait_limit sets the limit of one wait
+ * in SM clock cycles for later launches (0 restores the default, 2^31, about
+ * a second); the waits for in-flight copies keep the default.
+ */
+kl_status kl_check(kl_ctx *ctx, void *stream);
+kl_status kl_set_wait_limit(kl_ctx *ctx, int64_t cycles);
+
 /* Library version string (static). */
 const char *kl_version(void);
 

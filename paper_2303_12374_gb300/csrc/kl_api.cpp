@@ -374,6 +374,7 @@ kl_status make_kargs(kl_ctx *ctx, const kl_op &op, const Config &cfg, const kl_g
         }
     }
     a.err = ctx->d_err;
+    a.wait_cycles = ctx->wait_cycles;
     a.sj = g.sj;
     a.sk = g.sk;
     a.nx = g.nx;
@@ -744,6 +745,30 @@ kl_status kl_dot(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, int32_t level,
     *out = ctx->h_out[4];
     ctx->launches += 2;
     return KL_OK;
+}
+
+kl_status kl_set_wait_limit(kl_ctx *ctx, int64_t cycles)
+{
+    if (!ctx || cycles < 0) return fail(KL_ERR_INVALID_ARG, "ctx is NULL or cycles < 0");
+    ctx->wait_cycles = cycles ? (long long)cycles : (1ll << 31);
+    return KL_OK;
+}
+
+kl_status kl_check(kl_ctx *ctx, void *stream)
+{
+    if (!ctx) return fail(KL_ERR_INVALID_ARG, "ctx is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    int word = 0;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&word, ctx->d_err, sizeof word, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "kl_check: status read");
+    if (!word) return KL_OK;
+    e = cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "kl_check: status reset");
+    return fail(KL_ERR_TIMEOUT, "a device wait for a TMA plane gave up (status " +
+                                    std::to_string(word) + "); the outputs of that launch are incomplete");
 }
 
 kl_status kl_stats(kl_ctx *ctx, char *buf, size_t n)

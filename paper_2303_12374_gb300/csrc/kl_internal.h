@@ -127,6 +127,7 @@ struct KArgs {
     long long tile_x0, tile_y0, tile_z0;
     double cd[8];
     float cf[8];
+    long long wait_cycles;
 };
 
 struct Kernel {
@@ -178,6 +179,7 @@ struct kl_ctx {
     std::vector<cudaEvent_t> aux_events;              // [0] fork, [1 + i] join of stream i
     // one executable CUDA graph per batch (op, grids, fields) seen before
     std::map<std::string, cudaGraphExec_t> graphs;
+    long long wait_cycles = 1ll << 31;                // limit of one device wait
     cudaStream_t cap_stream = nullptr;                // where batch graphs are recorded
     long long graph_replays = 0;
     // statistics

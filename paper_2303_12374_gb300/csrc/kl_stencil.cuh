@@ -91,6 +91,7 @@ struct kl_args {
     // nu*dyi^2, unused
     double cd[8];
     float cf[8];
+    long long wait_cycles;        // limit of one device wait, SM clock cycles
 };
 
 #if KL_DTYPE == 0
@@ -549,14 +550,30 @@ __device__ __forceinline__ bool kl_mbar_try(unsigned bar, unsigned parity)
     return ok != 0;
 }
 
-// bounded wait (iteration cap and a clock64 deadline of ~2^31 cycles, about
-// one second); false on time-out
-__device__ __forceinline__ bool kl_mbar_wait(unsigned bar, unsigned parity)
+// non-blocking probe of the phase
+__device__ __forceinline__ bool kl_mbar_test(unsigned bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// bounded wait (iteration cap and a clock64 deadline: `cycles`, by default
+// 2^31, about one second); false on time-out.  try_wait may suspend the
+// thread for a while on its own, so deadlines below 2^20 cycles poll with the
+// non-blocking test instead.  Waits for copies still in flight before a CTA
+// leaves (the drain) always use the default deadline.
+#define KL_DRAIN_CYCLES (1ll << 31)
+__device__ __forceinline__ bool kl_mbar_wait(unsigned bar, unsigned parity,
+                                             long long cycles = KL_DRAIN_CYCLES)
 {
     long long t0 = clock64();
+    const bool poll = cycles < (1ll << 20);
     for (int it = 0; it < KL_WAIT_LIMIT; ++it) {
-        if (kl_mbar_try(bar, parity)) return true;
-        if (clock64() - t0 > (1ll << 31)) break;
+        if (poll ? kl_mbar_test(bar, parity) : kl_mbar_try(bar, parity)) return true;
+        if (clock64() - t0 > cycles) break;
     }
     return false;
 }
@@ -656,13 +673,13 @@ __device__ __forceinline__ void kl_zmarch_body(const kl_args &a, const kl_tmap *
             if (k == kb) {
                 for (int q = p_first; q < p; ++q) {
                     unsigned b2 = kl_smem_addr(&bars[(q - p_first) % KL_NS]);
-                    bool ok2 = kl_mbar_wait(b2, ((q - p_first) / KL_NS) & 1);
+                    bool ok2 = kl_mbar_wait(b2, ((q - p_first) / KL_NS) & 1, a.wait_cycles);
                     if (__syncthreads_or(!ok2)) { timed_out = true; break; }
                     p_waited = q;
                 }
                 if (timed_out) break;
             }
-            bool ok = kl_mbar_wait(bar, use & 1);
+            bool ok = kl_mbar_wait(bar, use & 1, a.wait_cycles);
             if (__syncthreads_or(!ok)) { timed_out = true; break; }
             p_waited = p;
         }
@@ -1218,7 +1235,8 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
     {
         bool ok = true;
         for (int q = p_first; q <= kb + KL_R && ok; ++q) {
-            ok = kl_mbar_wait(kl_smem_addr(&bars[(q - p_first) % KL_NS]), ((q - p_first) / KL_NS) & 1);
+            ok = kl_mbar_wait(kl_smem_addr(&bars[(q - p_first) % KL_NS]), ((q - p_first) / KL_NS) & 1,
+                              a.wait_cycles);
             if (ok && xwrap) xw_copy(slot_of(q));
         }
         timed_out = __syncthreads_or(!ok);
@@ -1566,7 +1584,8 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
         bool ok = true;
         if (k + 1 < ke) {
             const int p = k + 1 + KL_R;
-            ok = kl_mbar_wait(kl_smem_addr(&bars[(p - p_first) % KL_NS]), ((p - p_first) / KL_NS) & 1);
+            ok = kl_mbar_wait(kl_smem_addr(&bars[(p - p_first) % KL_NS]), ((p - p_first) / KL_NS) & 1,
+                              a.wait_cycles);
             if (ok && xwrap) xw_copy(slot_of(p));
         }
         if (__syncthreads_or(!ok)) {

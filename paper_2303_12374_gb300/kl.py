@@ -73,6 +73,8 @@ SIGNATURES = {
                 ctypes.c_int),
     "kl_dot": ([_P, _I32, ctypes.POINTER(Grid), _I32, _P, _P, ctypes.POINTER(_D), _P],
                ctypes.c_int),
+    "kl_check": ([_P, _P], ctypes.c_int),
+    "kl_set_wait_limit": ([_P, _I64], ctypes.c_int),
     "kl_diag_noalloc": ([_I32, ctypes.POINTER(Grid), _P, _P, _P, ctypes.POINTER(_D), _P],
                         ctypes.c_int),
     "kl_stats": ([_P, ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
@@ -194,6 +196,15 @@ def kl_dot(ctx, dtype, grid: Grid, level, a, b, stream=None) -> float:
     out = ctypes.c_double()
     check(load().kl_dot(ctx, dtype, ctypes.byref(grid), level, a, b, ctypes.byref(out), stream))
     return out.value
+
+
+def kl_check(ctx, stream=None) -> None:
+    """Raise KLError(KL_ERR_TIMEOUT) if a device wait gave up since the last check."""
+    check(load().kl_check(ctx, stream))
+
+
+def kl_set_wait_limit(ctx, cycles: int) -> None:
+    check(load().kl_set_wait_limit(ctx, cycles))
 
 
 def kl_diag_noalloc(dtype, grid: Grid, t, ref=None, wz=None, stream=None):
