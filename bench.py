@@ -554,6 +554,7 @@ def main():
         total_ms, kern_ms = time_steps(ctx, p, ins, outs, op, None, args.steps, args.warmup,
                                        stream)
     barrier()
+    kl.kl_check(ctx, stream.cuda_stream)       # no device wait gave up while timed
     total_ms = max_over_ranks(total_ms, world, device)
     stats = json.loads(kl.kl_stats(ctx))
     tuned_cfg = stats["last_config"]
