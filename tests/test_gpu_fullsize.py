@@ -88,6 +88,33 @@ def test_walls256_every_point(ctx, oracle_mod, dtype):
         assert rel_err(p.download(o), r) <= TOL[p.dtype], cfg
 
 
+def test_walls256_f32_step_as_bench_times_it(ctx, oracle_mod):
+    """The bench step: kl_step (the fill the selected kernel reads, then the
+    tuned zpack launch) on the 256^3 f32 workload, with NaN in every x ghost
+    of the interior rows beforehand; every point against the oracle."""
+    import torch
+    from gpu_cases import poison_x_ghosts
+    from paper_2303_12374_gb300 import kl, synth
+    from paper_2303_12374_gb300.problem import Problem
+    f = synth.velocity_fields(256, 256, 256, seed=synth.seed_of(1), walls=True)
+    p = Problem(256, 256, 256, g=3, dtype="f32", walls=True, dz=1.0 / 256, nu=1e-3)
+    bufs = {k: p.upload(f[k]) for k in ("u", "v", "w")}
+    for b in bufs.values():
+        poison_x_ghosts(p, b)
+    outs = [p.empty() for _ in range(3)]
+    fl = kl.Fields(bufs["u"].data_ptr(), bufs["v"].data_ptr(), bufs["w"].data_ptr(), None,
+                   *[o.data_ptr() for o in outs])
+    kl.kl_step(ctx, kl.Op(5, 1, p.dtype, 0), p.grid, fl)
+    torch.cuda.synchronize()
+    kl.kl_check(ctx)
+    cfg = json.loads(kl.kl_stats(ctx))["last_config"]
+    assert cfg.startswith("zpack:"), cfg
+    rin = {k: p.rounded(f[k]) for k in bufs}
+    ref = _oracle(oracle_mod, rin, f["zh"], adv=5, diff=1, walls=True, g=3)
+    for o, r in zip(outs, ref):
+        assert rel_err(p.download(o), r) <= TOL[1], cfg
+
+
 def test_precision_512x512x256_sampled_levels(ctx, oracle_mod):
     from paper_2303_12374_gb300 import synth
     f = synth.velocity_fields(512, 512, 256, seed=synth.seed_of(2), walls=True)
