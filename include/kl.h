@@ -304,7 +304,8 @@ kl_status kl_wisdom_append(const char *path, const char *device, int32_t cc_majo
  * KL_ERR_TIMEOUT when a launch since the last check gave up somewhere (its
  * outputs are then incomplete).  kl_set_wait_limit sets the limit of one wait
  * in SM clock cycles for later launches (0 restores the default, 2^31, about
- * a second); the waits for in-flight copies keep the default.
+ * a second); the waits for in-flight copies keep the default.  A context with
+ * a non-default limit compiles separate kernels whose waits poll against it.
  */
 kl_status kl_check(kl_ctx *ctx, void *stream);
 kl_status kl_set_wait_limit(kl_ctx *ctx, int64_t cycles);

@@ -156,10 +156,16 @@ kl_status load_compiled(kl_ctx *ctx, const kl_op &op, const Config &cfg, const s
     return KL_OK;
 }
 
+std::string kernel_key(const kl_ctx *ctx, const kl_op &op, const Config &cfg, int zbc, int zuni)
+{
+    return compile_defines(op, cfg, zbc, zuni) +
+           (ctx->wait_cycles != kDefaultWaitCycles ? " -DKL_WAITPOLL=1" : "");
+}
+
 kl_status get_kernel(kl_ctx *ctx, const kl_op &op, const Config &cfg, int zbc, int zuni,
                      Kernel **out, bool batch)
 {
-    std::string key = compile_defines(op, cfg, zbc, zuni) + (batch ? " -DKL_BATCH=1" : "");
+    std::string key = kernel_key(ctx, op, cfg, zbc, zuni) + (batch ? " -DKL_BATCH=1" : "");
     auto it = ctx->kernels.find(key);
     if (it != ctx->kernels.end()) {
         *out = &it->second;
@@ -418,7 +424,7 @@ kl_status launch_config(kl_ctx *ctx, const kl_op &op, const Config &cfg, const k
     int zuni = g.zh ? 0 : 1;
     Kernel *k = nullptr;
     auto t0 = std::chrono::steady_clock::now();
-    bool miss = ctx->kernels.find(compile_defines(op, cfg, g.zbc, zuni)) == ctx->kernels.end();
+    bool miss = ctx->kernels.find(kernel_key(ctx, op, cfg, g.zbc, zuni)) == ctx->kernels.end();
     st = get_kernel(ctx, op, cfg, g.zbc, zuni, &k);
     if (st) return st;
     if (!miss) ctx->cache_hits++;
@@ -750,7 +756,7 @@ kl_status kl_dot(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, int32_t level,
 kl_status kl_set_wait_limit(kl_ctx *ctx, int64_t cycles)
 {
     if (!ctx || cycles < 0) return fail(KL_ERR_INVALID_ARG, "ctx is NULL or cycles < 0");
-    ctx->wait_cycles = cycles ? (long long)cycles : (1ll << 31);
+    ctx->wait_cycles = cycles ? (long long)cycles : kDefaultWaitCycles;
     return KL_OK;
 }
 

@@ -26,7 +26,7 @@ namespace {
 // take the x ghosts of interior rows through one linear cell index, FILL_U
 // cells per thread.
 
-constexpr int FILL_T = 256, FILL_W = FILL_T / 32, FILL_RU = 3, FILL_U = 4;
+constexpr int FILL_T = 256, FILL_W = FILL_T / 32, FILL_RU = 9, FILL_U = 4;
 
 struct FillArgs {
     char *f[4];              // u, v, w, nu at interior (0,0,0); nu may be NULL

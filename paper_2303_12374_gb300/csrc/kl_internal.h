@@ -42,6 +42,9 @@ struct Config {
     int cs = 0;                // zpack: one warp group per tendency component (3 x w warps)
 };
 
+// default deadline of one device wait, SM clock cycles (about a second)
+constexpr long long kDefaultWaitCycles = 1ll << 31;
+
 // storage type of the tendencies ut, vt, wt
 inline int out_dtype(const kl_op &op) { return op.out_f32 ? (int)KL_F32 : op.dtype; }
 
@@ -179,7 +182,7 @@ struct kl_ctx {
     std::vector<cudaEvent_t> aux_events;              // [0] fork, [1 + i] join of stream i
     // one executable CUDA graph per batch (op, grids, fields) seen before
     std::map<std::string, cudaGraphExec_t> graphs;
-    long long wait_cycles = 1ll << 31;                // limit of one device wait
+    long long wait_cycles = kl::kDefaultWaitCycles;   // limit of one device wait
     cudaStream_t cap_stream = nullptr;                // where batch graphs are recorded
     long long graph_replays = 0;
     // statistics
@@ -194,6 +197,9 @@ namespace kl {
 // kl_launch, kl_launch_with_config and the tuner)
 kl_status launch_config(kl_ctx *ctx, const kl_op &op, const Config &cfg, const kl_grid &g,
                         const kl_fields &f, cudaStream_t s);
+// cache key and NVRTC defines of a kernel in a context: compile_defines,
+// plus KL_WAITPOLL=1 when the context's wait limit differs from the default
+std::string kernel_key(const kl_ctx *ctx, const kl_op &op, const Config &cfg, int zbc, int zuni);
 kl_status get_kernel(kl_ctx *ctx, const kl_op &op, const Config &cfg, int zbc, int zuni,
                      Kernel **out, bool batch = false);
 // kernel arguments and TMA descriptors of one launch (validated)

@@ -560,22 +560,40 @@ __device__ __forceinline__ bool kl_mbar_test(unsigned bar, unsigned parity)
     return ok != 0;
 }
 
-// bounded wait (iteration cap and a clock64 deadline: `cycles`, by default
-// 2^31, about one second); false on time-out.  try_wait may suspend the
-// thread for a while on its own, so deadlines below 2^20 cycles poll with the
-// non-blocking test instead.  Waits for copies still in flight before a CTA
-// leaves (the drain) always use the default deadline.
+// bounded waits (iteration cap and a clock64 deadline).  The default build
+// waits with try_wait up to 2^31 cycles, about one second.  A context whose
+// wait limit was changed (kl_set_wait_limit) compiles its kernels with
+// KL_WAITPOLL=1: the compute waits then poll with the non-blocking test_wait
+// against the limit in the kernel arguments (try_wait may suspend on its
+// own).  kl_mbar_drain, the wait for copies still in flight before a CTA
+// leaves, always uses the default deadline.  Both return false on time-out.
+#ifndef KL_WAITPOLL
+#define KL_WAITPOLL 0
+#endif
 #define KL_DRAIN_CYCLES (1ll << 31)
-__device__ __forceinline__ bool kl_mbar_wait(unsigned bar, unsigned parity,
-                                             long long cycles = KL_DRAIN_CYCLES)
+__device__ __forceinline__ bool kl_mbar_drain(unsigned bar, unsigned parity)
 {
     long long t0 = clock64();
-    const bool poll = cycles < (1ll << 20);
     for (int it = 0; it < KL_WAIT_LIMIT; ++it) {
-        if (poll ? kl_mbar_test(bar, parity) : kl_mbar_try(bar, parity)) return true;
+        if (kl_mbar_try(bar, parity)) return true;
+        if (clock64() - t0 > KL_DRAIN_CYCLES) break;
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool kl_mbar_wait(unsigned bar, unsigned parity, long long cycles)
+{
+#if KL_WAITPOLL
+    long long t0 = clock64();
+    for (int it = 0; it < KL_WAIT_LIMIT; ++it) {
+        if (kl_mbar_test(bar, parity)) return true;
         if (clock64() - t0 > cycles) break;
     }
     return false;
+#else
+    (void)cycles;
+    return kl_mbar_drain(bar, parity);
+#endif
 }
 
 // a descriptor read from global memory (batched launches) is ordered after
@@ -724,7 +742,7 @@ __device__ __forceinline__ void kl_zmarch_body(const kl_args &a, const kl_tmap *
             // leaving, so no TMA write lands in shared memory after exit
             for (int q = p_waited + 1; q < p_next; ++q) {
                 unsigned b2 = kl_smem_addr(&bars[(q - p_first) % KL_NS]);
-                kl_mbar_wait(b2, ((q - p_first) / KL_NS) & 1);
+                kl_mbar_drain(b2, ((q - p_first) / KL_NS) & 1);
             }
         }
         __syncthreads();
@@ -1601,7 +1619,7 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
             atomicOr(a.err, KL_DEV_TIMEOUT);
             for (int q = p_waited + 1; q < p_next; ++q) {
                 unsigned b2 = kl_smem_addr(&bars[(q - p_first) % KL_NS]);
-                kl_mbar_wait(b2, ((q - p_first) / KL_NS) & 1);
+                kl_mbar_drain(b2, ((q - p_first) / KL_NS) & 1);
             }
         }
         __syncthreads();

@@ -693,7 +693,7 @@ kl_status kl_tune(kl_ctx *ctx, const char *capture_path, const char *opts, const
     auto launch_compile = [&](const Config &c) {
         Pending p;
         p.cfg = c;
-        p.key = compile_defines(op, c, g.zbc, zuni);
+        p.key = kernel_key(ctx, op, c, g.zbc, zuni);
         queued.insert(config_string(c));
         ++produced;
         std::string key = p.key;
