@@ -166,3 +166,43 @@ def test_les_1024x1024x64_stretched_variable_nu_sampled(ctx, oracle_mod):
         ref = _oracle(oracle_mod, rin, zh, adv=5, diff=2, walls=True, g=3, levels=(a, b))
         for o, r in zip(outs, ref):
             assert rel_err(p.download(o)[a:b], r) <= TOL[1], (cfg, a)
+
+
+def test_batch64_uneven_as_bench_times_it(oracle_mod):
+    """The 64-grid batch of the bench (uneven sizes, tuned size classes from
+    the committed wisdom, one CUDA graph) against the oracle on two levels of
+    every grid (a wall level and an interior one)."""
+    import torch
+    from paper_2303_12374_gb300 import kl, synth
+    from paper_2303_12374_gb300.problem import Problem
+    spec = synth.WORKLOADS["batch64_uneven"]
+    sizes = synth.batch_sizes(synth.seed_of(spec["index"]), spec["count"])
+    ctx = kl.kl_create(0, WISDOM)
+    try:
+        probs = []
+        for q, (nx, ny, nz) in enumerate(sizes):
+            f = synth.velocity_fields(nx, ny, nz, seed=synth.seed_of(spec["index"]) * 1000 + q,
+                                      walls=True)
+            p = Problem(nx, ny, nz, g=3, dtype="f32", walls=True, dz=1.0 / nz, nu=1e-3)
+            bufs = [p.upload(f[k]) for k in ("u", "v", "w")]
+            outs = [p.empty() for _ in range(3)]
+            kl.kl_fill_ghosts(ctx, p.dtype, p.grid, *[b.data_ptr() for b in bufs], None)
+            fl = kl.Fields(*[b.data_ptr() for b in bufs], None, *[o.data_ptr() for o in outs])
+            probs.append((f, p, outs, fl))
+        op = kl.Op(5, 1, 1, 0)
+        grids = [pr[1].grid for pr in probs]
+        fields = [pr[3] for pr in probs]
+        kl.kl_launch_batched(ctx, op, grids, fields)
+        kl.kl_launch_batched(ctx, op, grids, fields)       # the replay of its graph
+        torch.cuda.synchronize()
+        kl.kl_check(ctx)
+        assert json.loads(kl.kl_stats(ctx))["graph_replays"] == 1
+        for f, p, outs, fl in probs:
+            rin = {k: p.rounded(f[k]) for k in ("u", "v", "w")}
+            for a, b in ((0, 1), (p.nz // 2, p.nz // 2 + 1)):
+                ref = _oracle(oracle_mod, rin, f["zh"], adv=5, diff=1, walls=True, g=3,
+                              levels=(a, b))
+                for o, r in zip(outs, ref):
+                    assert rel_err(p.download(o)[a:b], r) <= TOL[1], (p.nx, p.ny, p.nz, a)
+    finally:
+        kl.kl_destroy(ctx)
