@@ -188,7 +188,7 @@ def test_batch64_uneven_as_bench_times_it(oracle_mod):
             outs = [p.empty() for _ in range(3)]
             kl.kl_fill_ghosts(ctx, p.dtype, p.grid, *[b.data_ptr() for b in bufs], None)
             fl = kl.Fields(*[b.data_ptr() for b in bufs], None, *[o.data_ptr() for o in outs])
-            probs.append((f, p, outs, fl))
+            probs.append((f, p, outs, fl, bufs))      # bufs: the buffers must outlive the calls
         op = kl.Op(5, 1, 1, 0)
         grids = [pr[1].grid for pr in probs]
         fields = [pr[3] for pr in probs]
@@ -197,7 +197,7 @@ def test_batch64_uneven_as_bench_times_it(oracle_mod):
         torch.cuda.synchronize()
         kl.kl_check(ctx)
         assert json.loads(kl.kl_stats(ctx))["graph_replays"] == 1
-        for f, p, outs, fl in probs:
+        for f, p, outs, fl, bufs in probs:
             rin = {k: p.rounded(f[k]) for k in ("u", "v", "w")}
             for a, b in ((0, 1), (p.nz // 2, p.nz // 2 + 1)):
                 ref = _oracle(oracle_mod, rin, f["zh"], adv=5, diff=1, walls=True, g=3,
