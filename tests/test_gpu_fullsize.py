@@ -199,10 +199,15 @@ def test_batch64_uneven_as_bench_times_it(oracle_mod):
         assert json.loads(kl.kl_stats(ctx))["graph_replays"] == 1
         for f, p, outs, fl, bufs in probs:
             rin = {k: p.rounded(f[k]) for k in ("u", "v", "w")}
-            for a, b in ((0, 1), (p.nz // 2, p.nz // 2 + 1)):
-                ref = _oracle(oracle_mod, rin, f["zh"], adv=5, diff=1, walls=True, g=3,
-                              levels=(a, b))
-                for o, r in zip(outs, ref):
-                    assert rel_err(p.download(o)[a:b], r) <= TOL[1], (p.nx, p.ny, p.nz, a)
+            slabs = ((0, 1), (p.nz // 2, p.nz // 2 + 1))
+            refs = [_oracle(oracle_mod, rin, f["zh"], adv=5, diff=1, walls=True, g=3,
+                            levels=s_) for s_ in slabs]
+            # the error bound is relative to the largest tendency of the sampled
+            # levels taken together (as for the other sampled checks)
+            for c, o in enumerate(outs):
+                got = p.download(o)
+                g_s = np.concatenate([got[a:b] for a, b in slabs])
+                r_s = np.concatenate([r[c] for r in refs])
+                assert rel_err(g_s, r_s) <= TOL[1], (p.nx, p.ny, p.nz, c)
     finally:
         kl.kl_destroy(ctx)
