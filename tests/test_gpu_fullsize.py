@@ -170,8 +170,8 @@ def test_les_1024x1024x64_stretched_variable_nu_sampled(ctx, oracle_mod):
 
 def test_batch64_uneven_as_bench_times_it(oracle_mod):
     """The 64-grid batch of the bench (uneven sizes, tuned size classes from
-    the committed wisdom, one CUDA graph) against the oracle on two levels of
-    every grid (a wall level and an interior one)."""
+    the committed wisdom, one CUDA graph) against the oracle on three levels of
+    every grid (the two wall-side levels and a middle one)."""
     import torch
     from paper_2303_12374_gb300 import kl, synth
     from paper_2303_12374_gb300.problem import Problem
@@ -199,7 +199,7 @@ def test_batch64_uneven_as_bench_times_it(oracle_mod):
         assert json.loads(kl.kl_stats(ctx))["graph_replays"] == 1
         for f, p, outs, fl, bufs in probs:
             rin = {k: p.rounded(f[k]) for k in ("u", "v", "w")}
-            slabs = ((0, 1), (p.nz // 2, p.nz // 2 + 1))
+            slabs = ((0, 2), (p.nz // 2, p.nz // 2 + 1))    # w: level 1 (0 is the wall)
             refs = [_oracle(oracle_mod, rin, f["zh"], adv=5, diff=1, walls=True, g=3,
                             levels=s_) for s_ in slabs]
             # the error bound is relative to the largest tendency of the sampled
