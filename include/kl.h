@@ -204,8 +204,8 @@ kl_status kl_capture(kl_ctx *ctx, const kl_op *op, const kl_grid *grid,
 /*
  * Tune (Sec. 4.3): replay the capture at capture_path, search the
  * configuration space with the strategy in opts (host string of key=value
- * pairs: strategy=random|exhaustive|local, budget_s, max_evals, seed,
- * family=direct|zmarch|all, verify_tol, log=<path of a JSON-lines log>),
+ * pairs: strategy=random|exhaustive|local|bayes, budget_s, max_evals, seed,
+ * family=direct|zmarch|zpack|all, verify_tol, log=<path of a JSON-lines log>),
  * verify each candidate against the default configuration's output, and
  * append the best record with provenance to the wisdom file wisdom_path.
  * Synchronous; uses its own device buffers.
@@ -271,6 +271,41 @@ kl_status kl_config_normalize(const kl_op *op, const char *config, char *buf, si
  * idx-th (0-based, constraint-satisfying ones first counted) into buf. */
 kl_status kl_space_size(const kl_op *op, int32_t family, int64_t *count);
 kl_status kl_space_config(const kl_op *op, int32_t family, int64_t idx, char *buf, size_t n);
+
+/*
+ * Surrogate of the tuner's Bayesian optimisation (strategy=bayes; the paper
+ * tunes with Bayesian optimisation and random search, Sec. 5.3), usable for
+ * any search over encoded configurations.  Gaussian-process regression: the
+ * n observations y (host, minimised) at the rows of X (host, n x d,
+ * row-major) are standardised to zero mean and unit population variance;
+ * prior variance 1 and noise variance `noise` (<= 0: 1e-4) in those units;
+ * Matern-5/2 covariance k(r) = (1 + a + a^2/3) exp(-a), a = sqrt(5) r / l,
+ * r the Euclidean distance of two rows.  length_scale <= 0 selects l from
+ * {0.05, 0.1, 0.2, 0.3, 0.5, 0.75, 1, 1.5, 2, 3} by the log marginal
+ * likelihood (first maximum).
+ *
+ * kl_bo_posterior: the posterior mean and latent variance (y's units) at the
+ * m rows of Xq (host, m x d) into mean and var (host, m each); the length
+ * scale used into *ls_used (may be NULL).
+ *
+ * kl_bo_suggest: the np pending rows P (host, np x d; chosen, not yet
+ * measured) are added as observations equal to their posterior mean, with
+ * the length scale of the fit to y; then the expected improvement over
+ * min(y) with margin xi, EI = (b - m - xi) Phi(z) + s phi(z),
+ * z = (b - m - xi)/s, of each of the m candidate rows C (host, m x d) goes to
+ * ei (host, m; may be NULL) and the index of the largest (first on ties) to
+ * *choice.
+ *
+ * Both: KL_ERR_INVALID_ARG for a non-positive n or d, a NULL array that is
+ * needed, a non-finite value, or a covariance that is not positive definite
+ * (duplicate rows with noise too small).  Host only, no GPU.
+ */
+kl_status kl_bo_posterior(int32_t n, int32_t d, const double *X, const double *y, int32_t m,
+                          const double *Xq, double length_scale, double noise, double *mean,
+                          double *var, double *ls_used);
+kl_status kl_bo_suggest(int32_t n, int32_t d, const double *X, const double *y, int32_t np,
+                        const double *P, int32_t m, const double *C, double xi,
+                        double length_scale, double noise, int32_t *choice, double *ei);
 
 /* Compile a configuration with NVRTC for sm_103a without loading it; the
  * compiler log (with ptxas register/spill lines) goes to log (host, n). */

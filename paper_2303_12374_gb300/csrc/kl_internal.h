@@ -61,6 +61,15 @@ bool config_parse(const std::string &s, Config *c, std::string *err);
 // ghost width, ...).  smem_limit 0 = use the sm_103a per-block maximum.
 bool config_check(const kl_op &op, const Config &c, std::string *err);
 int64_t space_size(int family);
+
+// Bayesian-optimisation surrogate (kl_bayes.cpp): fit a GP to n observations
+// (X: n x d row-major features, y: values to minimise), add np pending points
+// as kriging believers, and return the index of the candidate (C: m x d) of
+// largest expected improvement (margin xi), or -1 with *err set.  ls <= 0
+// selects the length scale by marginal likelihood (written to *ls_used).
+int bo_suggest(int n, int d, const double *X, const double *y, int np, const double *P, int m,
+               const double *C, double xi, double ls, double noise, double *ls_used,
+               std::vector<double> *ei, std::string *err);
 bool space_config(int family, int64_t idx, Config *c);
 
 // tile / plane geometry of a zmarch configuration (mirrors the KL_* macros of

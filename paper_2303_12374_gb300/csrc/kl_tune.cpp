@@ -297,8 +297,9 @@ static kl_status parse_opts(const char *text, TuneOpts *o)
         else if (k == "threads") o->threads = atoi(v.c_str());
         else return fail(KL_ERR_INVALID_ARG, "unknown tune option '" + k + "'");
     }
-    if (o->strategy != "random" && o->strategy != "exhaustive" && o->strategy != "local")
-        return fail(KL_ERR_INVALID_ARG, "strategy must be random, exhaustive or local");
+    if (o->strategy != "random" && o->strategy != "exhaustive" && o->strategy != "local" &&
+        o->strategy != "bayes")
+        return fail(KL_ERR_INVALID_ARG, "strategy must be random, exhaustive, local or bayes");
     if (o->family != "all" && o->family != "direct" && o->family != "zmarch" && o->family != "zpack")
         return fail(KL_ERR_INVALID_ARG, "family must be all, direct, zmarch or zpack");
     return KL_OK;
@@ -487,6 +488,53 @@ static std::vector<int64_t> neighbours(int family, int64_t idx)
     return out;
 }
 
+// the digits of a configuration in its family's raw space (inverse of
+// space_config); false if a value is not one of the space's
+static bool config_digits(const Config &c, std::vector<int> *digits)
+{
+    std::vector<std::vector<int>> vals;
+    if (c.family == 0)
+        vals = {{16, 32, 64, 128, 256}, {1, 2, 4, 8, 16}, {1, 2, 4, 8, 16}, {1, 2, 4}, {1, 2, 4},
+                {1, 2, 4}, {0, 1}, {0, 1}, {0, 1}, {0, 1}, {0, 1}, {0, 1}, {0, 1, 2, 3, 4, 5},
+                {1, 2, 3, 4, 5, 6}};
+    else if (c.family == 2)
+        vals = {{1, 2, 4, 8, 16}, {1, 2, 4, 8}, {4, 8, 16, 32, 64, 128, 256}, {8, 9, 10, 12},
+                {1, 2, 3, 4}, {0, 1}, {0, 1}};
+    else
+        vals = {{32, 64, 128}, {1, 2, 4, 8, 16}, {1, 2, 4}, {1, 2, 4}, {4, 8, 16, 32, 64, 128, 256},
+                {8, 9, 10, 12}, {1, 2, 3, 4}};
+    std::vector<int> cur = c.family == 0
+        ? std::vector<int>{c.bx, c.by, c.bz, c.tx, c.ty, c.tz, c.ux, c.uy, c.uz, c.cx, c.cy, c.cz, c.perm, c.minb}
+        : c.family == 2 ? std::vector<int>{c.mby, c.mpy, c.kc, c.ns, c.mminb, c.yx, c.cs}
+                        : std::vector<int>{c.mbx, c.mby, c.mpx, c.mpy, c.kc, c.ns, c.mminb};
+    digits->resize(vals.size());
+    for (size_t p = 0; p < vals.size(); ++p) {
+        auto it = std::find(vals[p].begin(), vals[p].end(), cur[p]);
+        if (it == vals[p].end()) return false;
+        (*digits)[p] = (int)(it - vals[p].begin());
+    }
+    return true;
+}
+
+// Surrogate features of a configuration: a one-hot of the family (3 values),
+// then one block per family (14 direct, 7 zmarch, 7 zpack digits), the
+// configuration's own block holding each digit scaled to [0, 1] and the others
+// zero.  The value lists of the space are ordered (powers of two, counts), so
+// neighbouring digits are neighbouring settings.
+static const int kFeatDims = 3 + 14 + 7 + 7;
+
+static bool config_features(const Config &c, double *f)
+{
+    std::vector<int> dg;
+    if (!config_digits(c, &dg)) return false;
+    std::vector<int> r = radices(c.family);
+    std::fill(f, f + kFeatDims, 0.0);
+    f[c.family] = 1.0;
+    int off = 3 + (c.family == 0 ? 0 : c.family == 1 ? 14 : 21);
+    for (size_t q = 0; q < dg.size(); ++q) f[off + q] = r[q] > 1 ? (double)dg[q] / (r[q] - 1) : 0.0;
+    return true;
+}
+
 }  // namespace kl
 
 using namespace kl;
@@ -622,33 +670,10 @@ kl_status kl_tune(kl_ctx *ctx, const char *capture_path, const char *opts, const
     };
     // local search: neighbours of the best evaluated configuration
     auto index_of = [&](const Config &c, int64_t *idx) {
-        // brute inverse over the digits of the family's space
-        std::vector<int> r = radices(c.family);
-        int64_t total = space_size(c.family);
-        (void)total;
-        Config probe;
-        // encode by matching each digit's value list
-        std::vector<std::vector<int>> vals;
-        if (c.family == 0)
-            vals = {{16, 32, 64, 128, 256}, {1, 2, 4, 8, 16}, {1, 2, 4, 8, 16}, {1, 2, 4}, {1, 2, 4},
-                    {1, 2, 4}, {0, 1}, {0, 1}, {0, 1}, {0, 1}, {0, 1}, {0, 1}, {0, 1, 2, 3, 4, 5},
-                    {1, 2, 3, 4, 5, 6}};
-        else if (c.family == 2)
-            vals = {{1, 2, 4, 8, 16}, {1, 2, 4, 8}, {4, 8, 16, 32, 64, 128, 256}, {8, 9, 10, 12},
-                    {1, 2, 3, 4}, {0, 1}, {0, 1}};
-        else
-            vals = {{32, 64, 128}, {1, 2, 4, 8, 16}, {1, 2, 4}, {1, 2, 4}, {4, 8, 16, 32, 64, 128, 256},
-                    {8, 9, 10, 12}, {1, 2, 3, 4}};
-        std::vector<int> cur = c.family == 0
-            ? std::vector<int>{c.bx, c.by, c.bz, c.tx, c.ty, c.tz, c.ux, c.uy, c.uz, c.cx, c.cy, c.cz, c.perm, c.minb}
-            : c.family == 2 ? std::vector<int>{c.mby, c.mpy, c.kc, c.ns, c.mminb, c.yx, c.cs}
-                            : std::vector<int>{c.mbx, c.mby, c.mpx, c.mpy, c.kc, c.ns, c.mminb};
+        std::vector<int> r = radices(c.family), dg;
+        if (!config_digits(c, &dg)) return false;
         int64_t y = 0;
-        for (size_t p = r.size(); p-- > 0;) {
-            auto it = std::find(vals[p].begin(), vals[p].end(), cur[p]);
-            if (it == vals[p].end()) return false;
-            y = y * r[p] + (int64_t)(it - vals[p].begin());
-        }
+        for (size_t p = r.size(); p-- > 0;) y = y * r[p] + dg[p];
         *idx = y;
         return true;
     };
@@ -662,8 +687,82 @@ kl_status kl_tune(kl_ctx *ctx, const char *capture_path, const char *opts, const
     };
     int random_phase = std::max(8, O.max_evals / 4);
     int produced = 0;
+    // candidates compiling on host threads, in launch order
+    struct Pending {
+        Config cfg;
+        std::string key;
+        std::future<std::pair<kl_status, Compiled>> fut;
+    };
+    std::vector<Pending> pipe;
+
+    // Bayesian optimisation (Sec. 5.3 tunes with it): after an initial random
+    // design, the candidate of largest expected improvement of log(time) among
+    // a pool of random unqueued configurations and the unqueued neighbours of
+    // the five fastest so far; candidates still compiling count as observed at
+    // their predicted value.  The surrogate's length scale is re-selected
+    // after every 8 new observations.
+    const int bo_initial = std::max(8, std::min(32, O.max_evals / 8));
+    const int bo_pool = 512;
+    const double bo_xi = 0.01;        // margin in log(time): about 1 %
+    double bo_ls = 0;
+    size_t bo_ls_n = 0;
+    auto propose_bayes = [&](Config *c) -> bool {
+        std::vector<double> X, y, P, C, f(kFeatDims);
+        std::vector<std::pair<double, Config>> obs;
+        for (auto &e : evals) {
+            Config ec;
+            std::string err;
+            if (!e.ok || !(e.time_us > 0) || !std::isfinite(e.time_us)) continue;
+            if (!config_parse(e.config, &ec, &err) || !config_features(ec, f.data())) continue;
+            X.insert(X.end(), f.begin(), f.end());
+            y.push_back(std::log(e.time_us));
+            obs.emplace_back(e.time_us, ec);
+        }
+        int n = (int)y.size();
+        if (n < 2) return false;
+        for (auto &p : pipe)
+            if (config_features(p.cfg, f.data())) P.insert(P.end(), f.begin(), f.end());
+        std::vector<Config> pool;
+        std::set<std::string> in_pool;
+        auto add = [&](const Config &k) {
+            std::string s = config_string(k);
+            if (queued.count(s) || !config_features(k, f.data()) || !in_pool.insert(s).second) return;
+            pool.push_back(k);
+            C.insert(C.end(), f.begin(), f.end());
+        };
+        std::sort(obs.begin(), obs.end(), [](const std::pair<double, Config> &a,
+                                             const std::pair<double, Config> &b) { return a.first < b.first; });
+        for (size_t q = 0; q < obs.size() && q < 5; ++q) {
+            int64_t idx;
+            if (!index_of(obs[q].second, &idx)) continue;
+            for (int64_t nb : neighbours(obs[q].second.family, idx)) {
+                Config k;
+                if (valid_for(op, g, obs[q].second.family, nb, &k)) add(k);
+            }
+        }
+        for (int q = 0; q < bo_pool; ++q) {
+            Config k;
+            if (!draw_random(&k)) break;
+            add(k);
+        }
+        if (pool.empty()) return false;
+        double ls = bo_ls > 0 && (size_t)n < bo_ls_n + 8 ? bo_ls : 0.0, used = 0;
+        std::vector<double> ei;
+        std::string err;
+        int pick = bo_suggest(n, kFeatDims, X.data(), y.data(), (int)(P.size() / kFeatDims), P.data(),
+                              (int)pool.size(), C.data(), bo_xi, ls, 0.0, &used, &ei, &err);
+        if (pick < 0) return false;
+        if (ls <= 0) {
+            bo_ls = used;
+            bo_ls_n = (size_t)n;
+        }
+        *c = pool[pick];
+        return true;
+    };
+
     auto next_candidate = [&](Config *c) -> bool {
         if (O.strategy == "exhaustive") return draw_exhaustive(c);
+        if (O.strategy == "bayes" && produced >= bo_initial && propose_bayes(c)) return true;
         if (O.strategy == "local" && produced >= random_phase) {
             const Eval *b = best_so_far();
             Config bc;
@@ -684,12 +783,6 @@ kl_status kl_tune(kl_ctx *ctx, const char *capture_path, const char *opts, const
     int nthreads = O.threads > 0 ? O.threads
                    : std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
     int zuni = g.zh ? 0 : 1;
-    struct Pending {
-        Config cfg;
-        std::string key;
-        std::future<std::pair<kl_status, Compiled>> fut;
-    };
-    std::vector<Pending> pipe;
     auto launch_compile = [&](const Config &c) {
         Pending p;
         p.cfg = c;
@@ -712,7 +805,9 @@ kl_status kl_tune(kl_ctx *ctx, const char *capture_path, const char *opts, const
             Config c;
             if (!next_candidate(&c)) break;
             launch_compile(c);
-            if (O.strategy == "local" && produced > random_phase) break;  // keep the search adaptive
+            // keep the search adaptive: one new candidate per evaluation
+            if (O.strategy == "local" && produced > random_phase) break;
+            if (O.strategy == "bayes" && produced > bo_initial) break;
         }
         if (pipe.empty()) break;
         Pending p = std::move(pipe.front());

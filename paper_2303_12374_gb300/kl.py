@@ -88,6 +88,10 @@ SIGNATURES = {
     "kl_wisdom_select": ([_S, _S, _I32, _I32, _I32, _I32, _I32, _I32, ctypes.c_char_p,
                           ctypes.c_size_t, ctypes.POINTER(_I32)], ctypes.c_int),
     "kl_wisdom_append": ([_S, _S, _I32, _I32, _I32, _I32, _I32, _I32, _S, _D, _S], ctypes.c_int),
+    "kl_bo_posterior": ([_I32, _I32, _P, _P, _I32, _P, _D, _D, _P, _P, ctypes.POINTER(_D)],
+                        ctypes.c_int),
+    "kl_bo_suggest": ([_I32, _I32, _P, _P, _I32, _P, _I32, _P, _D, _D, _D,
+                       ctypes.POINTER(_I32), _P], ctypes.c_int),
     "kl_version": ([], _S),
 }
 
@@ -245,6 +249,44 @@ def kl_compile_only(op: Op, config: str, zbc: int = 0, zuni: int = 1) -> str:
     buf = ctypes.create_string_buffer(65536)
     check(load().kl_compile_only(ctypes.byref(op), _b(config), zbc, zuni, buf, len(buf)))
     return buf.value.decode()
+
+
+def _f64(a, cols=None):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if cols is not None:
+        a = a.reshape(-1, cols)
+    return a
+
+
+def kl_bo_posterior(X, y, Xq, length_scale: float = 0.0, noise: float = 0.0):
+    """(mean, var, length scale used) of the surrogate at the rows of Xq."""
+    import numpy as np
+    X = _f64(X)
+    n, d = X.shape
+    y, Xq = _f64(y), _f64(Xq, d)
+    m = Xq.shape[0]
+    mean, var, ls = np.zeros(m), np.zeros(m), ctypes.c_double()
+    check(load().kl_bo_posterior(n, d, X.ctypes.data, y.ctypes.data, m, Xq.ctypes.data,
+                                 length_scale, noise, mean.ctypes.data, var.ctypes.data,
+                                 ctypes.byref(ls)))
+    return mean, var, ls.value
+
+
+def kl_bo_suggest(X, y, C, pending=None, xi: float = 0.0, length_scale: float = 0.0,
+                  noise: float = 0.0):
+    """(index of the candidate row of C with the largest expected improvement, EI of every row)."""
+    import numpy as np
+    X = _f64(X)
+    n, d = X.shape
+    y, C = _f64(y), _f64(C, d)
+    P = _f64(np.zeros((0, d)) if pending is None else pending, d)
+    ei = np.zeros(C.shape[0])
+    choice = ctypes.c_int32()
+    check(load().kl_bo_suggest(n, d, X.ctypes.data, y.ctypes.data, P.shape[0],
+                               P.ctypes.data if P.shape[0] else None, C.shape[0], C.ctypes.data,
+                               xi, length_scale, noise, ctypes.byref(choice), ei.ctypes.data))
+    return choice.value, ei
 
 
 def kl_wisdom_select(path, device, cc_major, cc_minor, zbc, nx, ny, nz):

@@ -155,8 +155,33 @@ def test_tune_resumes_from_its_log(ctx, tmp_path):
 def test_tune_rejects_bad_options(ctx, tmp_path):
     from paper_2303_12374_gb300 import kl
     with pytest.raises(kl.KLError) as e:
-        kl.kl_tune(ctx, str(tmp_path / "none.klcap"), "strategy=bayes", str(tmp_path / "w"))
+        kl.kl_tune(ctx, str(tmp_path / "none.klcap"), "strategy=annealing", str(tmp_path / "w"))
     assert e.value.status == -1
     with pytest.raises(kl.KLError) as e:
         kl.kl_tune(ctx, str(tmp_path / "none.klcap"), "strategy=random", str(tmp_path / "w"))
     assert e.value.status == -4
+
+
+@pytest.mark.parametrize("family", ["zpack", "all"])
+def test_bayes_tuning(ctx, tmp_path, family):
+    """strategy=bayes: an initial random design of 8, then one surrogate-chosen
+    candidate per evaluation; nothing is evaluated twice, every candidate is
+    verified, and the record names the strategy."""
+    from paper_2303_12374_gb300 import kl
+    f, (p, bufs, outs, rin) = _problem(ctx)
+    op = kl.Op(5, 1, p.dtype, 0)
+    cap = str(tmp_path / "c.klcap")
+    kl.kl_capture(ctx, op, p.grid, _fields(p, bufs, outs, 1), cap)
+    log = str(tmp_path / "tune.jsonl")
+    w = str(tmp_path / "w.wisdom")
+    kl.kl_tune(ctx, cap, f"strategy=bayes family={family} max_evals=20 budget_s=120 seed=7 "
+                         f"log={log}", w)
+    evals = [json.loads(l) for l in open(log)]
+    confs = [e["config"] for e in evals]
+    assert len(confs) == 20 and len(set(confs)) == 20
+    assert sum(e["ok"] for e in evals) >= 15
+    assert all(e["err"] <= 1e-4 for e in evals if e["ok"])     # the tuner's f32 tolerance
+    if family == "zpack":
+        assert all(c.startswith("zpack:") for c in confs)
+    lines = [l for l in open(w) if not l.startswith("#")]
+    assert len(lines) == 1 and "strategy=bayes" in lines[0]
