@@ -6,8 +6,10 @@ Bayesian optimisation and reports how long the latter takes to come within
 runs the same comparison with kl_tune's `random` and `bayes` strategies on
 one seeded workload: every session replays the same capture, logs every
 evaluation, and the summary gives, per strategy and seed, the best time, the
-evaluations and seconds until the best is within 10 % and 5 % of the optimum,
-and the spread of the evaluated times.  The optimum is the best evaluation of
+evaluations and seconds until the best is within 10 %, 5 % and 2 % of the
+optimum, and the median evaluated time (how strongly the search prefers fast
+configurations).  Each session runs in a fresh context, so no compiled kernel
+carries over from one session to the next.  The optimum is the best evaluation of
 all sessions, or a given reference time (an exhaustive search) if lower.
 
     python -m paper_2303_12374_gb300.tune_compare --family zpack --evals 100 \
@@ -107,8 +109,14 @@ def main(argv=None):
             for seed in (int(s) for s in args.seeds.split(",")):
                 log = os.path.join(work, f"{strategy}_{seed}.jsonl")
                 wis = os.path.join(work, f"{strategy}_{seed}.wisdom")
-                kl.kl_tune(ctx, cap, f"strategy={strategy} family={args.family} seed={seed} "
-                                     f"max_evals={args.evals} budget_s={args.budget_s} log={log}", wis)
+                # a fresh context per session: no compiled kernel carries over
+                tctx = kl.kl_create(0, None)
+                try:
+                    kl.kl_tune(tctx, cap, f"strategy={strategy} family={args.family} seed={seed} "
+                                          f"max_evals={args.evals} budget_s={args.budget_s} log={log}",
+                               wis)
+                finally:
+                    kl.kl_destroy(tctx)
                 runs[(strategy, seed)] = read_log(log)
                 print(f"{strategy} seed {seed}: {len(runs[(strategy, seed)])} evals, best "
                       f"{min(us for _, us in runs[(strategy, seed)]):.1f} us", flush=True)
