@@ -89,7 +89,7 @@ def test_tendency_parity_configs(ctx, oracle_mod, config, dtype):
     from paper_2303_12374_gb300 import kl
     f = make_inputs(nx, ny, nz, seed=7, walls=True, stretch=2.0, var_nu=True)
     ran = 0
-    for adv, diff in ((5, 1), (5, 2), (2, 1)):
+    for adv, diff in ((5, 1), (5, 2), (2, 1), (5, 0), (0, 2)):
         try:   # the space's constraints (e.g. shared memory) may exclude an op
             kl.kl_config_normalize(kl.Op(adv, diff, dtype, 0), config)
         except kl.KLError:
