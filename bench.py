@@ -22,9 +22,11 @@ import argparse
 import json
 import math
 import os
+import shutil
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -482,9 +484,29 @@ def launch_overhead(local, wisdom, device, calls=1000):
             kl.kl_launch(ctx, op, p.grid, fl)
         host_us = (time.perf_counter() - t0) / calls * 1e6
         torch.cuda.synchronize()
-        return {"first_launch_ms": first_ms, "stage_ms": stages,
-                "cached_launch_host_us": host_us,
-                "note": "host time per kl_launch call through the ctypes binding, 32^3 grid"}
+        res = {"first_launch_ms": first_ms, "stage_ms": stages,
+               "cached_launch_host_us": host_us,
+               "note": "host time per kl_launch call through the ctypes binding, 32^3 grid"}
+        # the same first launch with an on-disk cubin cache: an empty directory
+        # (NVRTC, then the cubin is written) and a second context that reads it
+        d = tempfile.mkdtemp()
+        try:
+            for which in ("empty", "filled"):
+                c2 = kl.kl_create(local, wisdom)
+                try:
+                    kl.kl_set_cache_dir(c2, d)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    kl.kl_launch(c2, op, p.grid, fl)
+                    res[f"first_launch_ms_disk_cache_{which}"] = (time.perf_counter() - t0) * 1e3
+                    st = json.loads(kl.kl_stats(c2))
+                    res[f"stage_ms_disk_cache_{which}"] = dict(st["stage_ms"],
+                                                               disk_read=st["disk_cache"]["read_ms"])
+                finally:
+                    kl.kl_destroy(c2)
+        finally:
+            shutil.rmtree(d, ignore_errors=True)
+        return res
     finally:
         kl.kl_destroy(ctx)
 

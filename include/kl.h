@@ -307,6 +307,33 @@ kl_status kl_bo_suggest(int32_t n, int32_t d, const double *X, const double *y, 
                         const double *P, int32_t m, const double *C, double xi,
                         double length_scale, double noise, int32_t *choice, double *ei);
 
+/*
+ * On-disk cubin cache.  The first launch of a configuration costs an NVRTC
+ * compile (tens of ms; Sec. 5.6 measures the paper's first-launch stages).
+ * With a cache directory, a context reads the cubin of every variant it
+ * needs from <dir>/kl_<hash>.cubin when present and writes each one it
+ * compiles.  A file records the identity of its variant (hash of the kernel
+ * source, NVRTC version, target, compile defines) and a checksum; a file
+ * that does not match is ignored and rewritten.  Files are written under a
+ * temporary name and renamed, so processes may share a directory.  The
+ * tuner's candidates are not cached.
+ *
+ * kl_set_cache_dir: use dir (host string, an existing directory) from now
+ * on; NULL or "" turns the cache off.  A context starts with $KL_CACHE_DIR
+ * (off if unset).  KL_ERR_IO if dir is not a directory.
+ *
+ * kl_cache_prepare (host only, no GPU): compile one configuration for op
+ * (same configuration text as kl_compile_only, "batch+" prefix for the
+ * batched variant) into dir unless it is already there; *hit (host) is 1 if
+ * it was.  This is the variant a context with the default wait limit
+ * launches, so a cache can be filled ahead of time from the wisdom records.
+ * KL_ERR_INVALID_ARG for a bad op or configuration, KL_ERR_IO if dir is not
+ * a writable directory, KL_ERR_NVRTC if compilation fails.
+ */
+kl_status kl_set_cache_dir(kl_ctx *ctx, const char *dir);
+kl_status kl_cache_prepare(const char *dir, const kl_op *op, const char *config, int32_t zbc,
+                           int32_t zuni, int32_t *hit);
+
 /* Compile a configuration with NVRTC for sm_103a without loading it; the
  * compiler log (with ptxas register/spill lines) goes to log (host, n). */
 kl_status kl_compile_only(const kl_op *op, const char *config, int32_t zbc, int32_t zuni,

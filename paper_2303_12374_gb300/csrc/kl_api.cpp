@@ -9,6 +9,10 @@
 #include <cstring>
 #include <mutex>
 #include <sstream>
+#include <thread>
+
+#include <sys/stat.h>
+#include <unistd.h>
 
 #include "kl_internal.h"
 
@@ -118,6 +122,89 @@ kl_status nvrtc_compile(const std::string &defines, bool verbose, Compiled *out)
     return KL_OK;
 }
 
+// ------------------------------------------------- on-disk cubin cache
+//
+// One file per compiled variant, <dir>/kl_<16 hex digits>.cubin: the line
+// "KLCUBIN1 <identity bytes> <cubin bytes> <cubin FNV-1a>\n", the identity,
+// then the cubin.  The identity names everything the cubin depends on: the
+// FNV-1a hash of the NVRTC source, the NVRTC version, the target and the
+// compile defines; the file name is the FNV-1a hash of the identity.  A file
+// whose identity differs (another source or compiler, a name collision),
+// whose length or checksum does not match, is not used and is rewritten.
+// Writes go to a unique temporary name and are renamed into place, so a
+// reader never sees a partial file and concurrent writers of one variant
+// leave one whole copy.
+
+static uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull)
+{
+    const unsigned char *b = (const unsigned char *)p;
+    for (size_t q = 0; q < n; ++q) h = (h ^ b[q]) * 1099511628211ull;
+    return h;
+}
+
+static std::string cache_identity(const std::string &defines)
+{
+    static const uint64_t src = fnv1a(kSource, strlen(kSource));
+    int M = 0, m = 0;
+    nvrtcVersion(&M, &m);
+    char b[128];
+    snprintf(b, sizeof b, "source=%016llx nvrtc=%d.%d arch=sm_103a defines=", (unsigned long long)src,
+             M, m);
+    return b + defines;
+}
+
+static std::string cache_path(const std::string &dir, const std::string &ident)
+{
+    char b[40];
+    snprintf(b, sizeof b, "kl_%016llx.cubin", (unsigned long long)fnv1a(ident.data(), ident.size()));
+    return dir + "/" + b;
+}
+
+bool cache_read(const std::string &dir, const std::string &defines, Compiled *out)
+{
+    std::string ident = cache_identity(defines);
+    FILE *f = fopen(cache_path(dir, ident).c_str(), "rb");
+    if (!f) return false;
+    bool ok = false;
+    char head[96];
+    size_t ni = 0, nc = 0;
+    unsigned long long sum = 0;
+    if (fgets(head, sizeof head, f) &&
+        sscanf(head, "KLCUBIN1 %zu %zu %llx", &ni, &nc, &sum) == 3 && ni == ident.size() && nc > 0 &&
+        nc < ((size_t)1 << 30)) {
+        std::string id(ni, '\0');
+        std::vector<char> cubin(nc);
+        char extra;
+        if (fread(&id[0], 1, ni, f) == ni && id == ident && fread(cubin.data(), 1, nc, f) == nc &&
+            fread(&extra, 1, 1, f) == 0 && fnv1a(cubin.data(), nc) == sum) {
+            out->cubin.swap(cubin);
+            ok = true;
+        }
+    }
+    fclose(f);
+    return ok;
+}
+
+bool cache_write(const std::string &dir, const std::string &defines, const Compiled &c)
+{
+    std::string ident = cache_identity(defines);
+    std::string path = cache_path(dir, ident);
+    std::string tmp = path + "." + std::to_string((long long)getpid()) + "." +
+                      std::to_string(std::hash<std::thread::id>()(std::this_thread::get_id())) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "wb");
+    if (!f) return false;
+    bool ok = fprintf(f, "KLCUBIN1 %zu %zu %016llx\n", ident.size(), c.cubin.size(),
+                      (unsigned long long)fnv1a(c.cubin.data(), c.cubin.size())) > 0 &&
+              fwrite(ident.data(), 1, ident.size(), f) == ident.size() &&
+              fwrite(c.cubin.data(), 1, c.cubin.size(), f) == c.cubin.size();
+    ok = fclose(f) == 0 && ok;
+    if (!ok || rename(tmp.c_str(), path.c_str()) != 0) {
+        remove(tmp.c_str());
+        return false;
+    }
+    return true;
+}
+
 // ------------------------------------------------------ kernel cache
 
 kl_status load_compiled(kl_ctx *ctx, const kl_op &op, const Config &cfg, const std::string &key,
@@ -173,9 +260,20 @@ kl_status get_kernel(kl_ctx *ctx, const kl_op &op, const Config &cfg, int zbc, i
     }
     auto t0 = std::chrono::steady_clock::now();
     Compiled c;
+    if (!ctx->cache_dir.empty() && cache_read(ctx->cache_dir, key, &c)) {
+        ctx->t_disk_ms += ms_since(t0);
+        kl_status st = load_compiled(ctx, op, cfg, key, c, out);
+        if (st == KL_OK) {
+            ctx->disk_hits++;
+            return KL_OK;
+        }
+        cudaGetLastError();   // an unusable file: compile it again below and replace it
+        t0 = std::chrono::steady_clock::now();
+    }
     kl_status st = nvrtc_compile(key, false, &c);
     if (st) return st;
     ctx->t_nvrtc_ms += ms_since(t0);
+    if (!ctx->cache_dir.empty() && cache_write(ctx->cache_dir, key, c)) ctx->disk_writes++;
     return load_compiled(ctx, op, cfg, key, c, out);
 }
 
@@ -528,6 +626,7 @@ kl_status kl_create(kl_ctx **out, int device, const char *wisdom_dir)
     c->name = prop.name;
     if (wisdom_dir) c->wisdom_dir = wisdom_dir;
     else if (const char *w = getenv("KL_WISDOM_DIR")) c->wisdom_dir = w;
+    if (const char *cd = getenv("KL_CACHE_DIR")) c->cache_dir = cd;
     kl_status st = driver_load(&c->drv);
     if (st) {
         delete c;
@@ -789,12 +888,14 @@ kl_status kl_stats(kl_ctx *ctx, char *buf, size_t n)
                      "\"cache_hits\":%lld,\"cache_misses\":%lld,\"modules\":%zu,"
                      "\"stage_ms\":{\"wisdom\":%.3f,\"nvrtc\":%.3f,\"module_load\":%.3f,"
                      "\"launch\":%.3f},\"last_config\":\"%s\",\"rules\":{%s},\"note\":\"%s\","
-                     "\"tables\":%zu,\"graphs\":%zu,\"graph_replays\":%lld}",
+                     "\"tables\":%zu,\"graphs\":%zu,\"graph_replays\":%lld,"
+                     "\"disk_cache\":{\"on\":%s,\"hits\":%lld,\"writes\":%lld,\"read_ms\":%.3f}}",
                      ctx->name.c_str(), ctx->cc_major, ctx->cc_minor, ctx->nsm, ctx->launches,
                      ctx->cache_hits, ctx->cache_misses, ctx->kernels.size(), ctx->t_wisdom_ms,
                      ctx->t_nvrtc_ms, ctx->t_load_ms, ctx->t_launch_ms, ctx->last_config.c_str(),
                      rules.c_str(), ctx->last_rule_text.c_str(), ctx->tables.size(),
-                     ctx->graphs.size(), ctx->graph_replays);
+                     ctx->graphs.size(), ctx->graph_replays, ctx->cache_dir.empty() ? "false" : "true",
+                     ctx->disk_hits, ctx->disk_writes, ctx->t_disk_ms);
     if (m < 0 || (size_t)m >= n) return fail(KL_ERR_INVALID_ARG, "stats buffer too small");
     return KL_OK;
 }
@@ -860,6 +961,48 @@ kl_status kl_compile_only(const kl_op *op, const char *config, int32_t zbc, int3
         log[m] = '\0';
     }
     return st;
+}
+
+kl_status kl_set_cache_dir(kl_ctx *ctx, const char *dir)
+{
+    if (!ctx) return fail(KL_ERR_INVALID_ARG, "NULL context");
+    if (!dir || !*dir) {
+        ctx->cache_dir.clear();
+        return KL_OK;
+    }
+    struct stat sb;
+    if (stat(dir, &sb) != 0 || !S_ISDIR(sb.st_mode))
+        return fail(KL_ERR_IO, std::string("cache directory does not exist: ") + dir);
+    ctx->cache_dir = dir;
+    return KL_OK;
+}
+
+kl_status kl_cache_prepare(const char *dir, const kl_op *op, const char *config, int32_t zbc,
+                           int32_t zuni, int32_t *hit)
+{
+    kl_status st = check_op(op);
+    if (st) return st;
+    if (!dir || !*dir || !config || !hit) return fail(KL_ERR_INVALID_ARG, "NULL argument");
+    struct stat sb;
+    if (stat(dir, &sb) != 0 || !S_ISDIR(sb.st_mode))
+        return fail(KL_ERR_IO, std::string("cache directory does not exist: ") + dir);
+    Config c;
+    std::string err, text = config;
+    bool batch = text.rfind("batch+", 0) == 0;
+    if (batch) text = text.substr(6);
+    if (!config_parse(text, &c, &err) || !config_check(*op, c, &err))
+        return fail(KL_ERR_INVALID_ARG, "configuration: " + err);
+    std::string key = compile_defines(*op, c, zbc, zuni) + (batch ? " -DKL_BATCH=1" : "");
+    Compiled out;
+    if (cache_read(dir, key, &out)) {
+        *hit = 1;
+        return KL_OK;
+    }
+    *hit = 0;
+    st = nvrtc_compile(key, false, &out);
+    if (st) return st;
+    if (!cache_write(dir, key, out)) return fail(KL_ERR_IO, std::string("cannot write into ") + dir);
+    return KL_OK;
 }
 
 kl_status kl_wisdom_select(const char *path, const char *device, int32_t cc_major,

@@ -198,6 +198,10 @@ struct kl_ctx {
     long long launches = 0, cache_hits = 0, cache_misses = 0;
     double t_wisdom_ms = 0, t_nvrtc_ms = 0, t_load_ms = 0, t_launch_ms = 0;
     double last_first_launch_ms = 0;
+    // on-disk cubin cache (empty: off; $KL_CACHE_DIR at creation)
+    std::string cache_dir;
+    long long disk_hits = 0, disk_writes = 0;
+    double t_disk_ms = 0;
     std::string last_config, last_rule_text;
 };
 

@@ -92,6 +92,9 @@ SIGNATURES = {
                         ctypes.c_int),
     "kl_bo_suggest": ([_I32, _I32, _P, _P, _I32, _P, _I32, _P, _D, _D, _D,
                        ctypes.POINTER(_I32), _P], ctypes.c_int),
+    "kl_set_cache_dir": ([_P, _S], ctypes.c_int),
+    "kl_cache_prepare": ([_S, ctypes.POINTER(Op), _S, _I32, _I32, ctypes.POINTER(_I32)],
+                         ctypes.c_int),
     "kl_version": ([], _S),
 }
 
@@ -249,6 +252,18 @@ def kl_compile_only(op: Op, config: str, zbc: int = 0, zuni: int = 1) -> str:
     buf = ctypes.create_string_buffer(65536)
     check(load().kl_compile_only(ctypes.byref(op), _b(config), zbc, zuni, buf, len(buf)))
     return buf.value.decode()
+
+
+def kl_set_cache_dir(ctx, path) -> None:
+    check(load().kl_set_cache_dir(ctx, _b(path)))
+
+
+def kl_cache_prepare(path: str, op: Op, config: str, zbc: int = 0, zuni: int = 1) -> bool:
+    """Compile config into the cubin cache at path; True if it was already there."""
+    hit = ctypes.c_int32()
+    check(load().kl_cache_prepare(_b(path), ctypes.byref(op), _b(config), zbc, zuni,
+                                  ctypes.byref(hit)))
+    return bool(hit.value)
 
 
 def _f64(a, cols=None):

@@ -221,3 +221,68 @@ def test_layout_alignment(dtype, es):
 def test_layout_rejects_huge():
     with pytest.raises(kl.KLError):
         kl.kl_layout(4096, 4096, 200, 3, 0)
+
+
+# ------------------------------------------------------------- cubin cache
+
+def _cubins(d):
+    return sorted(p for p in os.listdir(d) if p.endswith(".cubin"))
+
+
+def test_cache_prepare_writes_once_and_reuses(tmp_path):
+    d = str(tmp_path)
+    op = kl.Op(5, 1, 1, 0)
+    cfg = "zpack:w=4,ly=2,kc=16,ns=8,minb=1"
+    assert kl.kl_cache_prepare(d, op, cfg, 1, 1) is False
+    files = _cubins(d)
+    assert len(files) == 1 and files[0].startswith("kl_")
+    assert kl.kl_cache_prepare(d, op, cfg, 1, 1) is True
+    # the same configuration text in another spelling is the same variant
+    assert kl.kl_cache_prepare(d, op, kl.kl_config_normalize(op, cfg), 1, 1) is True
+    # anything that changes the compile defines is another file
+    assert kl.kl_cache_prepare(d, op, cfg, 0, 1) is False
+    assert kl.kl_cache_prepare(d, op, "batch+" + cfg, 1, 1) is False
+    assert kl.kl_cache_prepare(d, kl.Op(5, 1, 0, 0), "default", 1, 1) is False
+    assert len(_cubins(d)) == 4
+    assert not [p for p in os.listdir(d) if p.endswith(".tmp")]
+    head = open(os.path.join(d, files[0]), "rb").readline().decode()
+    assert head.startswith("KLCUBIN1 ")
+
+
+def test_cache_rejects_damaged_or_foreign_files(tmp_path):
+    d = str(tmp_path)
+    op = kl.Op(5, 1, 1, 0)
+    kl.kl_cache_prepare(d, op, "default", 1, 1)
+    (f,) = _cubins(d)
+    path = os.path.join(d, f)
+    good = open(path, "rb").read()
+    # a flipped byte in the cubin fails the checksum: recompiled and rewritten
+    bad = bytearray(good)
+    bad[-100] ^= 0x5A
+    open(path, "wb").write(bytes(bad))
+    assert kl.kl_cache_prepare(d, op, "default", 1, 1) is False
+    assert open(path, "rb").read() == good
+    # truncated, and with trailing bytes
+    open(path, "wb").write(good[:-10])
+    assert kl.kl_cache_prepare(d, op, "default", 1, 1) is False
+    open(path, "wb").write(good + b"x")
+    assert kl.kl_cache_prepare(d, op, "default", 1, 1) is False
+    # another variant's file under this name (identity mismatch)
+    kl.kl_cache_prepare(d, op, "direct:bx=64", 1, 1)
+    other = [p for p in _cubins(d) if p != f][0]
+    open(path, "wb").write(open(os.path.join(d, other), "rb").read())
+    assert kl.kl_cache_prepare(d, op, "default", 1, 1) is False
+    assert kl.kl_cache_prepare(d, op, "default", 1, 1) is True
+
+
+def test_cache_argument_errors(tmp_path):
+    op = kl.Op(5, 1, 1, 0)
+    with pytest.raises(kl.KLError) as e:
+        kl.kl_cache_prepare(str(tmp_path / "missing"), op, "default", 1, 1)
+    assert e.value.status == -4
+    with pytest.raises(kl.KLError) as e:
+        kl.kl_cache_prepare(str(tmp_path), op, "direct:bx=7", 1, 1)
+    assert e.value.status == -1
+    with pytest.raises(kl.KLError) as e:
+        kl.kl_set_cache_dir(None, str(tmp_path))
+    assert e.value.status == -1
