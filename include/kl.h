@@ -334,6 +334,110 @@ kl_status kl_set_cache_dir(kl_ctx *ctx, const char *dir);
 kl_status kl_cache_prepare(const char *dir, const kl_op *op, const char *config, int32_t zbc,
                            int32_t zuni, int32_t *hit);
 
+/* ---- user-defined tunable kernels (Sec. 4.1 for any kernel) ------------ */
+
+/*
+ * A kernel definition: CUDA source text (host string, compiled by NVRTC for
+ * sm_103a with -std=c++17), the name of its __global__ function (an
+ * extern "C" name or a C++ name expression such as "scale<float>"), and a
+ * name (a C identifier) that names its wisdom file <wisdom dir>/<name>.wisdom.
+ * Tunable parameters, restrictions, geometry and extra compile options are
+ * added with the calls below.  The definition owns copies of all strings;
+ * it is host data, usable with any context.
+ */
+typedef struct kl_def kl_def;
+
+/* One launch argument.  kind 0: a scalar, ptr points to its value (host),
+ * bytes its size (1..64).  kind 1 input, 2 output, 3 input and output: a
+ * device buffer at ptr of `bytes` bytes; dtype says how tuning compares its
+ * contents (0 f64, 1 f32, 2 bf16, 3 f16: relative to the largest reference
+ * magnitude; 4 i32, 5 raw bytes: exactly).  Arguments are passed to the
+ * kernel in order, buffers as their device pointer. */
+typedef struct {
+    const void *ptr;
+    int64_t bytes;
+    int32_t kind;
+    int32_t dtype;
+} kl_arg;
+
+kl_status kl_def_create(kl_def **out, const char *name, const char *source, const char *function);
+void      kl_def_destroy(kl_def *def);
+
+/* A tunable parameter: name (a C identifier; problem_x/y/z are reserved),
+ * n distinct values (host) and the default, one of them.  Each compiled
+ * variant gets -D<name>=<value> for every parameter.  The raw space is the
+ * product of the value lists; its index runs over the first parameter
+ * fastest. */
+kl_status kl_def_param(kl_def *def, const char *name, int32_t n, const int64_t *values,
+                       int64_t default_value);
+
+/* A restriction: an integer expression over the declared parameters (C
+ * syntax: + - * / % comparisons && || ! ?: and min, max, div_ceil, round_up)
+ * that every configuration must make non-zero. */
+kl_status kl_def_restrict(kl_def *def, const char *expr);
+
+/* Launch geometry as integer expressions over the parameters and the
+ * problem size problem_x, problem_y, problem_z: block[3], grid[3] (each may
+ * be NULL or "") and the dynamic shared memory in bytes.  Defaults: block 1,
+ * grid div_ceil(problem, block), no shared memory.  A configuration whose
+ * block exceeds 1024 threads, whose grid is below 1 or above the device
+ * limits, or whose shared memory exceeds 227 KB does not apply to that
+ * problem. */
+kl_status kl_def_geometry(kl_def *def, const char *const block[3], const char *const grid[3],
+                          const char *shared_memory);
+
+/* Extra NVRTC options (host string, space-separated; e.g. "-DT=float"). */
+kl_status kl_def_options(kl_def *def, const char *options);
+
+/* Host-only queries (no GPU): raw space size and the number of
+ * configurations that satisfy the restrictions (-1 above 10^7 raw points);
+ * the idx-th raw configuration as text "p=v,...", KL_ERR_INVALID_ARG if it
+ * violates a restriction (text still written); the normalised text of a
+ * configuration ("default" or p=v pairs; unnamed parameters keep their
+ * defaults); the geometry {block x,y,z, grid x,y,z, shared bytes} of a
+ * configuration for a problem; an NVRTC compile with the ptxas log. */
+kl_status kl_def_space_size(const kl_def *def, int64_t *raw, int64_t *valid);
+kl_status kl_def_config_at(const kl_def *def, int64_t idx, char *buf, size_t n);
+kl_status kl_def_normalize(const kl_def *def, const char *config, char *buf, size_t n);
+kl_status kl_def_launch_geometry(const kl_def *def, const char *config, const int64_t problem[3],
+                                 int64_t out[7]);
+kl_status kl_def_compile_only(const kl_def *def, const char *config, char *log, size_t n);
+
+/*
+ * Launch (Sec. 4.5): select the record of <wisdom dir>/<name>.wisdom for
+ * this device and problem size (problem[3], host) by the rules of
+ * kl_wisdom_select (zbc 0), falling back to the default when no record
+ * applies to the problem; compile it with NVRTC once per context (or read it
+ * from the context's cubin cache) and launch on `stream` with the nargs
+ * arguments (host array).  The selection is made once per context, wisdom
+ * directory and problem size.  kl_def_launch_config launches a given
+ * configuration.  kl_def_selected: the configuration of the last launch and
+ * the rule (1..5) of the last selection.
+ */
+kl_status kl_def_launch(kl_ctx *ctx, kl_def *def, const int64_t problem[3], int32_t nargs,
+                        const kl_arg *args, void *stream);
+kl_status kl_def_launch_config(kl_ctx *ctx, kl_def *def, const char *config,
+                               const int64_t problem[3], int32_t nargs, const kl_arg *args,
+                               void *stream);
+kl_status kl_def_selected(const kl_def *def, char *buf, size_t n, int32_t *rule);
+
+/*
+ * Capture (Sec. 4.2): synchronise `stream`, then write the problem size,
+ * the argument list and the contents of every scalar, input and in/out
+ * buffer to `path` (outputs: size only).  kl_def_tune replays it: the
+ * default configuration's outputs are the reference, every candidate runs
+ * from the captured inputs (in/out buffers restored, outputs filled with
+ * 0xff bytes) and must match it (verify_tol, else 1e-12 f64, 1e-5 f32, 1e-2
+ * 16-bit, exact for i32/bytes); options as kl_tune (strategy=random|
+ * exhaustive|bayes, budget_s, max_evals, seed, verify_tol, log, reps, warm,
+ * threads).  The fastest of the three best candidates and the default,
+ * re-timed, is appended to wisdom_path.  Synchronous; its own device buffers.
+ */
+kl_status kl_def_capture(kl_ctx *ctx, const kl_def *def, const int64_t problem[3], int32_t nargs,
+                         const kl_arg *args, const char *path, void *stream);
+kl_status kl_def_tune(kl_ctx *ctx, kl_def *def, const char *capture_path, const char *opts,
+                      const char *wisdom_path);
+
 /* Compile a configuration with NVRTC for sm_103a without loading it; the
  * compiler log (with ptxas register/spill lines) goes to log (host, n). */
 kl_status kl_compile_only(const kl_op *op, const char *config, int32_t zbc, int32_t zuni,

@@ -21,7 +21,7 @@ LIB = os.path.join(OUT, "libkl.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 CUDA_LIB = "/usr/local/cuda/lib64"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kl_api.cpp", "kl_config.cpp", "kl_tune.cpp", "kl_bayes.cpp", "kl_device.cu"]
+SOURCES = ["kl_api.cpp", "kl_config.cpp", "kl_tune.cpp", "kl_bayes.cpp", "kl_def.cpp", "kl_device.cu"]
 
 
 def _embed_source() -> str:

@@ -125,32 +125,37 @@ kl_status nvrtc_compile(const std::string &defines, bool verbose, Compiled *out)
 // ------------------------------------------------- on-disk cubin cache
 //
 // One file per compiled variant, <dir>/kl_<16 hex digits>.cubin: the line
-// "KLCUBIN1 <identity bytes> <cubin bytes> <cubin FNV-1a>\n", the identity,
-// then the cubin.  The identity names everything the cubin depends on: the
-// FNV-1a hash of the NVRTC source, the NVRTC version, the target and the
-// compile defines; the file name is the FNV-1a hash of the identity.  A file
-// whose identity differs (another source or compiler, a name collision),
-// whose length or checksum does not match, is not used and is rewritten.
-// Writes go to a unique temporary name and are renamed into place, so a
-// reader never sees a partial file and concurrent writers of one variant
-// leave one whole copy.
+// "KLCUBIN1 <identity bytes> <symbol bytes> <cubin bytes> <cubin FNV-1a>\n",
+// the identity, the kernel's symbol name, then the cubin.  The identity names
+// everything the cubin depends on: the FNV-1a hash of the source, the NVRTC
+// version, the target and the compile options; the file name is the FNV-1a
+// hash of the identity.  A file whose identity differs (another source or
+// compiler, a name collision), whose lengths or checksum do not match, is not
+// used and is rewritten.  Writes go to a unique temporary name and are
+// renamed into place, so a reader never sees a partial file and concurrent
+// writers of one variant leave one whole copy.
 
-static uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull)
+uint64_t fnv1a(const void *p, size_t n, uint64_t h)
 {
     const unsigned char *b = (const unsigned char *)p;
     for (size_t q = 0; q < n; ++q) h = (h ^ b[q]) * 1099511628211ull;
     return h;
 }
 
-static std::string cache_identity(const std::string &defines)
+std::string cache_identity(uint64_t source_hash, const std::string &options)
 {
-    static const uint64_t src = fnv1a(kSource, strlen(kSource));
     int M = 0, m = 0;
     nvrtcVersion(&M, &m);
     char b[128];
-    snprintf(b, sizeof b, "source=%016llx nvrtc=%d.%d arch=sm_103a defines=", (unsigned long long)src,
-             M, m);
-    return b + defines;
+    snprintf(b, sizeof b, "source=%016llx nvrtc=%d.%d arch=sm_103a options=",
+             (unsigned long long)source_hash, M, m);
+    return b + options;
+}
+
+static std::string stencil_identity(const std::string &defines)
+{
+    static const uint64_t src = fnv1a(kSource, strlen(kSource));
+    return cache_identity(src, defines);
 }
 
 static std::string cache_path(const std::string &dir, const std::string &ident)
@@ -160,24 +165,25 @@ static std::string cache_path(const std::string &dir, const std::string &ident)
     return dir + "/" + b;
 }
 
-bool cache_read(const std::string &dir, const std::string &defines, Compiled *out)
+bool cache_read(const std::string &dir, const std::string &ident, Compiled *out)
 {
-    std::string ident = cache_identity(defines);
     FILE *f = fopen(cache_path(dir, ident).c_str(), "rb");
     if (!f) return false;
     bool ok = false;
-    char head[96];
-    size_t ni = 0, nc = 0;
+    char head[128];
+    size_t ni = 0, ns = 0, nc = 0;
     unsigned long long sum = 0;
     if (fgets(head, sizeof head, f) &&
-        sscanf(head, "KLCUBIN1 %zu %zu %llx", &ni, &nc, &sum) == 3 && ni == ident.size() && nc > 0 &&
-        nc < ((size_t)1 << 30)) {
-        std::string id(ni, '\0');
+        sscanf(head, "KLCUBIN1 %zu %zu %zu %llx", &ni, &ns, &nc, &sum) == 4 && ni == ident.size() &&
+        ns < 4096 && nc > 0 && nc < ((size_t)1 << 30)) {
+        std::string id(ni, '\0'), sym(ns, '\0');
         std::vector<char> cubin(nc);
         char extra;
-        if (fread(&id[0], 1, ni, f) == ni && id == ident && fread(cubin.data(), 1, nc, f) == nc &&
-            fread(&extra, 1, 1, f) == 0 && fnv1a(cubin.data(), nc) == sum) {
+        if (fread(&id[0], 1, ni, f) == ni && id == ident && fread(&sym[0], 1, ns, f) == ns &&
+            fread(cubin.data(), 1, nc, f) == nc && fread(&extra, 1, 1, f) == 0 &&
+            fnv1a(cubin.data(), nc) == sum) {
             out->cubin.swap(cubin);
+            out->symbol = sym;
             ok = true;
         }
     }
@@ -185,17 +191,17 @@ bool cache_read(const std::string &dir, const std::string &defines, Compiled *ou
     return ok;
 }
 
-bool cache_write(const std::string &dir, const std::string &defines, const Compiled &c)
+bool cache_write(const std::string &dir, const std::string &ident, const Compiled &c)
 {
-    std::string ident = cache_identity(defines);
     std::string path = cache_path(dir, ident);
     std::string tmp = path + "." + std::to_string((long long)getpid()) + "." +
                       std::to_string(std::hash<std::thread::id>()(std::this_thread::get_id())) + ".tmp";
     FILE *f = fopen(tmp.c_str(), "wb");
     if (!f) return false;
-    bool ok = fprintf(f, "KLCUBIN1 %zu %zu %016llx\n", ident.size(), c.cubin.size(),
-                      (unsigned long long)fnv1a(c.cubin.data(), c.cubin.size())) > 0 &&
+    bool ok = fprintf(f, "KLCUBIN1 %zu %zu %zu %016llx\n", ident.size(), c.symbol.size(),
+                      c.cubin.size(), (unsigned long long)fnv1a(c.cubin.data(), c.cubin.size())) > 0 &&
               fwrite(ident.data(), 1, ident.size(), f) == ident.size() &&
+              fwrite(c.symbol.data(), 1, c.symbol.size(), f) == c.symbol.size() &&
               fwrite(c.cubin.data(), 1, c.cubin.size(), f) == c.cubin.size();
     ok = fclose(f) == 0 && ok;
     if (!ok || rename(tmp.c_str(), path.c_str()) != 0) {
@@ -260,7 +266,7 @@ kl_status get_kernel(kl_ctx *ctx, const kl_op &op, const Config &cfg, int zbc, i
     }
     auto t0 = std::chrono::steady_clock::now();
     Compiled c;
-    if (!ctx->cache_dir.empty() && cache_read(ctx->cache_dir, key, &c)) {
+    if (!ctx->cache_dir.empty() && cache_read(ctx->cache_dir, stencil_identity(key), &c)) {
         ctx->t_disk_ms += ms_since(t0);
         kl_status st = load_compiled(ctx, op, cfg, key, c, out);
         if (st == KL_OK) {
@@ -273,7 +279,8 @@ kl_status get_kernel(kl_ctx *ctx, const kl_op &op, const Config &cfg, int zbc, i
     kl_status st = nvrtc_compile(key, false, &c);
     if (st) return st;
     ctx->t_nvrtc_ms += ms_since(t0);
-    if (!ctx->cache_dir.empty() && cache_write(ctx->cache_dir, key, c)) ctx->disk_writes++;
+    if (!ctx->cache_dir.empty() && cache_write(ctx->cache_dir, stencil_identity(key), c))
+        ctx->disk_writes++;
     return load_compiled(ctx, op, cfg, key, c, out);
 }
 
@@ -650,6 +657,7 @@ void kl_destroy(kl_ctx *c)
     cudaDeviceSynchronize();
     for (auto &p : c->kernels)
         if (p.second.mod) c->drv.ModuleUnload(p.second.mod);
+    def_kernels_unload(c);
     for (auto &p : c->profiles) {
         cudaFree(p.second.d64);
         cudaFree(p.second.d32);
@@ -994,14 +1002,15 @@ kl_status kl_cache_prepare(const char *dir, const kl_op *op, const char *config,
         return fail(KL_ERR_INVALID_ARG, "configuration: " + err);
     std::string key = compile_defines(*op, c, zbc, zuni) + (batch ? " -DKL_BATCH=1" : "");
     Compiled out;
-    if (cache_read(dir, key, &out)) {
+    if (cache_read(dir, stencil_identity(key), &out)) {
         *hit = 1;
         return KL_OK;
     }
     *hit = 0;
     st = nvrtc_compile(key, false, &out);
     if (st) return st;
-    if (!cache_write(dir, key, out)) return fail(KL_ERR_IO, std::string("cannot write into ") + dir);
+    if (!cache_write(dir, stencil_identity(key), out))
+        return fail(KL_ERR_IO, std::string("cannot write into ") + dir);
     return KL_OK;
 }
 

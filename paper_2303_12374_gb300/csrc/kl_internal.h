@@ -104,7 +104,14 @@ bool wisdom_append(const std::string &path, const WisdomRecord &r, std::string *
 struct Compiled {
     std::vector<char> cubin;
     std::string log;
+    std::string symbol;      // lowered name of the kernel function (user definitions)
 };
+// on-disk cubin cache (kl_api.cpp): identity of a variant from its source
+// hash and compile options; read/write one variant's file in dir
+uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull);
+std::string cache_identity(uint64_t source_hash, const std::string &options);
+bool cache_read(const std::string &dir, const std::string &ident, Compiled *out);
+bool cache_write(const std::string &dir, const std::string &ident, const Compiled &c);
 std::string compile_defines(const kl_op &op, const Config &c, int zbc, int zuni);
 kl_status nvrtc_compile(const std::string &defines, bool verbose, Compiled *out);
 
@@ -150,6 +157,14 @@ struct Kernel {
     int nregs = 0;
     int local_bytes = 0;
 };
+
+// a compiled user-defined kernel in a context (kl_def.cpp)
+struct DefKernel {
+    CUmodule mod = nullptr;
+    CUfunction fn = nullptr;
+    int smem_attr = 0;          // dynamic shared memory the function is opted in to
+};
+void def_kernels_unload(kl_ctx *ctx);
 
 struct Profile {
     double *d64 = nullptr;   // dzi | dzhi, each nz + 2g, f64
@@ -201,6 +216,8 @@ struct kl_ctx {
     // on-disk cubin cache (empty: off; $KL_CACHE_DIR at creation)
     std::string cache_dir;
     long long disk_hits = 0, disk_writes = 0;
+    // user-defined kernels, keyed by their cache identity
+    std::map<std::string, kl::DefKernel> def_kernels;
     double t_disk_ms = 0;
     std::string last_config, last_rule_text;
 };

@@ -95,6 +95,23 @@ SIGNATURES = {
     "kl_set_cache_dir": ([_P, _S], ctypes.c_int),
     "kl_cache_prepare": ([_S, ctypes.POINTER(Op), _S, _I32, _I32, ctypes.POINTER(_I32)],
                          ctypes.c_int),
+    "kl_def_create": ([ctypes.POINTER(_P), _S, _S, _S], ctypes.c_int),
+    "kl_def_destroy": ([_P], None),
+    "kl_def_param": ([_P, _S, _I32, ctypes.POINTER(_I64), _I64], ctypes.c_int),
+    "kl_def_restrict": ([_P, _S], ctypes.c_int),
+    "kl_def_geometry": ([_P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_char_p), _S],
+                        ctypes.c_int),
+    "kl_def_options": ([_P, _S], ctypes.c_int),
+    "kl_def_space_size": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
+    "kl_def_config_at": ([_P, _I64, ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
+    "kl_def_normalize": ([_P, _S, ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
+    "kl_def_launch_geometry": ([_P, _S, ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
+    "kl_def_compile_only": ([_P, _S, ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
+    "kl_def_launch": ([_P, _P, ctypes.POINTER(_I64), _I32, _P, _P], ctypes.c_int),
+    "kl_def_launch_config": ([_P, _P, _S, ctypes.POINTER(_I64), _I32, _P, _P], ctypes.c_int),
+    "kl_def_selected": ([_P, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(_I32)], ctypes.c_int),
+    "kl_def_capture": ([_P, _P, ctypes.POINTER(_I64), _I32, _P, _S, _P], ctypes.c_int),
+    "kl_def_tune": ([_P, _P, _S, _S, _S], ctypes.c_int),
     "kl_version": ([], _S),
 }
 
@@ -320,3 +337,133 @@ def kl_wisdom_append(path, device, cc_major, cc_minor, zbc, nx, ny, nz, config, 
 
 def kl_version() -> str:
     return load().kl_version().decode()
+
+
+# ------------------------------------------------------------ user-defined kernels
+
+class Arg(ctypes.Structure):
+    """kl_arg: kind 0 scalar (ptr to the host value), 1 in, 2 out, 3 in/out device buffer."""
+    _fields_ = [("ptr", ctypes.c_void_p), ("bytes", ctypes.c_int64), ("kind", ctypes.c_int32),
+                ("dtype", ctypes.c_int32)]
+
+
+_SCALARS = {"i32": ctypes.c_int32, "i64": ctypes.c_int64, "u32": ctypes.c_uint32,
+            "f32": ctypes.c_float, "f64": ctypes.c_double}
+_KINDS = {"in": 1, "out": 2, "inout": 3}
+
+
+def _buffer_dtype(t) -> int:
+    import torch
+    return {torch.float64: 0, torch.float32: 1, torch.bfloat16: 2, torch.float16: 3,
+            torch.int32: 4}.get(t.dtype, 5)
+
+
+def make_args(args):
+    """kl_arg array from [(kind, value)]: kind "i32"/"i64"/"u32"/"f32"/"f64" with a
+    Python number, or "in"/"out"/"inout" with a contiguous device tensor.
+    Returns (array, keep-alive list)."""
+    keep, out = [], []
+    for kind, v in args:
+        if kind in _SCALARS:
+            c = _SCALARS[kind](v)
+            keep.append(c)
+            out.append(Arg(ctypes.addressof(c), ctypes.sizeof(c), 0, 0))
+        elif kind in _KINDS:
+            assert v.is_contiguous()
+            out.append(Arg(v.data_ptr(), v.numel() * v.element_size(), _KINDS[kind],
+                           _buffer_dtype(v)))
+        else:
+            raise ValueError(f"unknown argument kind {kind!r}")
+    arr = (Arg * max(1, len(out)))(*out)
+    return arr, keep
+
+
+def _problem(p):
+    p = list(p) + [1] * (3 - len(p))
+    return (ctypes.c_int64 * 3)(*p)
+
+
+class KernelDef:
+    """A user-defined tunable kernel: argument marshalling over the kl_def_* calls."""
+
+    def __init__(self, name: str, source: str, function: str):
+        h = ctypes.c_void_p()
+        check(load().kl_def_create(ctypes.byref(h), _b(name), _b(source), _b(function)))
+        self.h = h.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().kl_def_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def param(self, name, values, default=None):
+        vals = (ctypes.c_int64 * len(values))(*values)
+        check(load().kl_def_param(self.h, _b(name), len(values), vals,
+                                  values[0] if default is None else default))
+        return self
+
+    def restrict(self, expr):
+        check(load().kl_def_restrict(self.h, _b(expr)))
+        return self
+
+    def geometry(self, block=(), grid=(), shared_memory=None):
+        arr = lambda xs: (ctypes.c_char_p * 3)(*[_b(x) for x in (list(xs) + [None] * 3)[:3]])
+        check(load().kl_def_geometry(self.h, arr(block), arr(grid), _b(shared_memory)))
+        return self
+
+    def options(self, opts):
+        check(load().kl_def_options(self.h, _b(opts)))
+        return self
+
+    def space_size(self):
+        raw, valid = ctypes.c_int64(), ctypes.c_int64()
+        check(load().kl_def_space_size(self.h, ctypes.byref(raw), ctypes.byref(valid)))
+        return raw.value, valid.value
+
+    def config_at(self, idx):
+        buf = ctypes.create_string_buffer(4096)
+        st = load().kl_def_config_at(self.h, idx, buf, len(buf))
+        if st not in (KL_OK, -1) or not buf.value:
+            check(st)
+        return buf.value.decode(), st == KL_OK
+
+    def normalize(self, config):
+        buf = ctypes.create_string_buffer(4096)
+        check(load().kl_def_normalize(self.h, _b(config), buf, len(buf)))
+        return buf.value.decode()
+
+    def launch_geometry(self, config, problem):
+        out = (ctypes.c_int64 * 7)()
+        check(load().kl_def_launch_geometry(self.h, _b(config), _problem(problem), out))
+        return list(out)
+
+    def compile_only(self, config="default"):
+        buf = ctypes.create_string_buffer(65536)
+        check(load().kl_def_compile_only(self.h, _b(config), buf, len(buf)))
+        return buf.value.decode()
+
+    def launch(self, ctx, problem, args, stream=None):
+        arr, keep = make_args(args)
+        check(load().kl_def_launch(ctx, self.h, _problem(problem), len(args), arr, stream))
+
+    def launch_config(self, ctx, config, problem, args, stream=None):
+        arr, keep = make_args(args)
+        check(load().kl_def_launch_config(ctx, self.h, _b(config), _problem(problem), len(args),
+                                          arr, stream))
+
+    def selected(self):
+        buf = ctypes.create_string_buffer(4096)
+        rule = ctypes.c_int32()
+        check(load().kl_def_selected(self.h, buf, len(buf), ctypes.byref(rule)))
+        return buf.value.decode(), rule.value
+
+    def capture(self, ctx, problem, args, path, stream=None):
+        arr, keep = make_args(args)
+        check(load().kl_def_capture(ctx, self.h, _problem(problem), len(args), arr, _b(path),
+                                    stream))
+
+    def tune(self, ctx, capture_path, opts, wisdom_path):
+        check(load().kl_def_tune(ctx, self.h, _b(capture_path), _b(opts), _b(wisdom_path)))
