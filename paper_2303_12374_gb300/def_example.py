@@ -1,5 +1,5 @@
 """A user-defined tunable kernel end to end (Sec. 4.1-4.5 for any kernel):
-define a vector add with two tunable parameters and a restriction, capture
+define a vector add with three tunable parameters and a restriction, capture
 one launch, tune it, and launch it again through run-time selection of the
 wisdom record; report default and tuned times against the HBM roofline.
 
