@@ -1,4 +1,5 @@
-"""FP64 CPU oracle of the stencil tendencies (test infrastructure only).
+"""FP64 CPU oracle of the stencil tendencies and the Smagorinsky viscosity
+(test infrastructure only).
 
 Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may import
 this package.  The product path (paper_2303_12374_gb300) never does; the two
@@ -45,6 +46,8 @@ def _load():
                                     + [ctypes.c_int] * 2 + [ctypes.c_double] + [dp] * 4
                                     + [ctypes.c_int] * 2 + [dp] * 3)
         lib.or_diag.argtypes = [ctypes.c_size_t, dp, dp, dp, dp]
+        lib.or_smagorinsky.argtypes = ([ctypes.c_int] * 4 + [ctypes.c_double] * 2 + [dp, dp]
+                                       + [ctypes.c_double] + [dp] * 3 + [ctypes.c_int] * 2 + [dp])
         _lib = lib
     return _lib
 
@@ -96,6 +99,32 @@ def tendencies(u, v, w, *, adv: int, diff: int, g: int, walls: bool, dx: float,
     lib.or_tendency(nx, ny, nz, g, int(walls), dx, dy, _p(dz), _p(dzh), adv, diff, nu,
                     _p(up), _p(vp), _p(wp), _p(np_), k0, k1, _p(ut), _p(vt), _p(wt))
     return ut, vt, wt
+
+
+def smagorinsky_padded(up, vp, wp, *, g: int, dx: float, dy: float, dz: np.ndarray,
+                       dzh: np.ndarray, cs: float, levels=None):
+    """Smagorinsky nu at the interior cell centres from padded u, v, w whose
+    ghosts the caller has set (any values: analytic fields may fill them)."""
+    lib = _load()
+    nzp, nyp, nxp = up.shape
+    nz, ny, nx = nzp - 2 * g, nyp - 2 * g, nxp - 2 * g
+    k0, k1 = (0, nz) if levels is None else levels
+    assert 0 <= k0 < k1 <= nz and g >= 1
+    up, vp, wp = (np.ascontiguousarray(x, dtype=np.float64) for x in (up, vp, wp))
+    dz, dzh = (np.ascontiguousarray(x, dtype=np.float64) for x in (dz, dzh))
+    out = np.empty((k1 - k0, ny, nx))
+    lib.or_smagorinsky(nx, ny, nz, g, dx, dy, _p(dz), _p(dzh), cs, _p(up), _p(vp), _p(wp),
+                       k0, k1, _p(out))
+    return out
+
+
+def smagorinsky(u, v, w, *, g: int, walls: bool, dx: float, dy: float, zh: np.ndarray,
+                cs: float, levels=None):
+    """Smagorinsky nu on the interior from interior u, v, w (ghosts by the fill rules)."""
+    nz = u.shape[0]
+    up, vp, wp = pad(u, g, walls, False), pad(v, g, walls, False), pad(w, g, walls, True)
+    dz, dzh = zprofile(nz, g, walls, zh)
+    return smagorinsky_padded(up, vp, wp, g=g, dx=dx, dy=dy, dz=dz, dzh=dzh, cs=cs, levels=levels)
 
 
 def diag(t: np.ndarray, ref: np.ndarray | None = None, wgt: np.ndarray | None = None):

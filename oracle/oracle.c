@@ -21,7 +21,9 @@
  *   diffusion   diff = 1: nu * Laplacian with constant nu;
  *               diff = 2: stress divergence d_j[nu (d_j u_i + d_i u_j)] with a
  *               cell-centred eddy viscosity nu, 4-point averages of nu on
- *               cell edges.
+ *               cell edges;
+ *   eddy viscosity  or_smagorinsky: nu = (cs delta)^2 sqrt(2 S_ij S_ij) of the
+ *               Smagorinsky model, the nu that diff = 2 takes as input.
  *
  * Grid: interior i in [0,nx), j in [0,ny), k in [0,nz), g ghost cells on every
  * side.  u(i,j,k) sits at (i dx, (j+1/2) dy, z_k), v at ((i+1/2) dx, j dy, z_k),
@@ -363,6 +365,71 @@ void or_tendency(int nx, int ny, int nz, int g, int zbc, double dx, double dy,
                 vt[o] = tv;
                 wt[o] = tw;
             }
+}
+
+/* ------------------------------------------------- Smagorinsky viscosity */
+
+/*
+ * Eddy viscosity of the Smagorinsky model at cell centres of interior levels
+ * k0 <= k < k1 (array of (k1-k0)*ny*nx, x fastest), from padded u, v, w
+ * whose ghosts are filled (one ghost cell suffices):
+ *
+ *   nu = (cs * delta_k)^2 * sqrt(2 S_ij S_ij),  delta_k = (dx dy dz_k)^(1/3),
+ *   S_ij = (d_i u_j + d_j u_i) / 2.
+ *
+ * The paper names the model ("Smagorinsky diffusion", Sec. 5.2) but prints no
+ * formula; this is the textbook model discretised on the C grid.  The normal
+ * strains live at the cell centre.  Each shear strain lives on cell edges
+ * (Sxy on (xh, yh, z), Sxz on (xh, y, zh), Syz on (x, yh, zh)); its square
+ * enters as the mean over the four edges of the cell, so that
+ *
+ *   2 S_ij S_ij = 2 (Sxx^2 + Syy^2 + Szz^2) + 4 (<Sxy^2> + <Sxz^2> + <Syz^2>).
+ */
+static double exy(const dctx *D, int i, int j, int k)  /* Sxy on (xh_i, yh_j, z_k) */
+{
+    return 0.5 * ((DU(i, j, k) - DU(i, j - 1, k)) / D->G->dy +
+                  (DV(i, j, k) - DV(i - 1, j, k)) / D->G->dx);
+}
+static double exz(const dctx *D, int i, int j, int k)  /* Sxz on (xh_i, y_j, zh_k) */
+{
+    return 0.5 * ((DU(i, j, k) - DU(i, j, k - 1)) / D->G->dzh[k + D->G->g] +
+                  (DW(i, j, k) - DW(i - 1, j, k)) / D->G->dx);
+}
+static double eyz(const dctx *D, int i, int j, int k)  /* Syz on (x_i, yh_j, zh_k) */
+{
+    return 0.5 * ((DV(i, j, k) - DV(i, j, k - 1)) / D->G->dzh[k + D->G->g] +
+                  (DW(i, j, k) - DW(i, j - 1, k)) / D->G->dy);
+}
+
+void or_smagorinsky(int nx, int ny, int nz, int g, double dx, double dy, const double *dz,
+                    const double *dzh, double cs, const double *u, const double *v,
+                    const double *w, int k0, int k1, double *nu)
+{
+    ogrid G = {nx, ny, nz, g, 0, dx, dy, dz, dzh};
+    dctx Dc = {&G, u, v, w, NULL};
+    const dctx *D = &Dc;
+    for (int k = k0; k < k1; ++k) {
+        double delta = cbrt(dx * dy * dz[k + g]);
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                double sxx = (DU(i + 1, j, k) - DU(i, j, k)) / dx;
+                double syy = (DV(i, j + 1, k) - DV(i, j, k)) / dy;
+                double szz = (DW(i, j, k + 1) - DW(i, j, k)) / dz[k + g];
+                double mxy = 0.0, mxz = 0.0, myz = 0.0;
+                for (int a = 0; a < 2; ++a)
+                    for (int b = 0; b < 2; ++b) {
+                        double e1 = exy(D, i + a, j + b, k);
+                        double e2 = exz(D, i + a, j, k + b);
+                        double e3 = eyz(D, i, j + a, k + b);
+                        mxy += e1 * e1 / 4.0;
+                        mxz += e2 * e2 / 4.0;
+                        myz += e3 * e3 / 4.0;
+                    }
+                double s2 = 2.0 * (sxx * sxx + syy * syy + szz * szz) + 4.0 * (mxy + mxz + myz);
+                size_t o = (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * (size_t)(k - k0));
+                nu[o] = (cs * delta) * (cs * delta) * sqrt(s2);
+            }
+    }
 }
 
 /* ------------------------------------------------------------ diagnostics */
