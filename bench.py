@@ -408,6 +408,48 @@ def diag_timing(ctx, p, outs, stream, reps=20, ins=None):
     return res
 
 
+def les_step(ctx, stream, peak_gbs, reps=20, cs=0.1):
+    """The LES step on the 1024x1024x64 stretched workload, f32: ghost fill of
+    u, v, w, Smagorinsky nu (with its own ghost fill), then 5th-order advection
+    + variable-nu diffusion with that nu.  The nu kernel alone is reported
+    against its roofline: 16 B/pt (read u, v, w, write nu)."""
+    import torch
+    from paper_2303_12374_gb300 import kl
+    from paper_2303_12374_gb300.tune_cli import build_problem
+    p, op, bufs, outs, fl = build_problem("les1024x1024x64_stretched_varnu", "f32")
+    pts = p.nx * p.ny * p.nz
+    sp = stream.cuda_stream
+    uvw = [bufs[k].data_ptr() for k in ("u", "v", "w")]
+    nu = bufs["nu"].data_ptr()
+    parts = {
+        "smagorinsky": lambda: kl.kl_smagorinsky(ctx, p.dtype, p.grid, cs, *uvw, nu, False, sp),
+        "tendency": lambda: kl.kl_launch(ctx, op, p.grid, fl, sp),
+        "step": lambda: (kl.kl_fill_ghosts(ctx, p.dtype, p.grid, *uvw, None, sp),
+                         kl.kl_smagorinsky(ctx, p.dtype, p.grid, cs, *uvw, nu, True, sp),
+                         kl.kl_launch(ctx, op, p.grid, fl, sp)),
+    }
+    res = {"grid": f"{p.nx}x{p.ny}x{p.nz}", "dtype": "f32", "cs": cs, "points": pts}
+    with torch.cuda.stream(stream):
+        kl.kl_fill_ghosts(ctx, p.dtype, p.grid, *uvw, None, sp)
+        for name, fn in parts.items():
+            for _ in range(3):
+                fn()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            res[name + "_us"] = a.elapsed_time(b) / reps * 1e3
+    res["smagorinsky_gbs"] = 16 * pts / res["smagorinsky_us"] / 1e3
+    res["smagorinsky_frac"] = res["smagorinsky_gbs"] / peak_gbs
+    res["step_gpts"] = pts / res["step_us"] / 1e3
+    res["tendency_config"] = json.loads(kl.kl_stats(ctx))["last_config"]
+    del bufs, outs
+    torch.cuda.empty_cache()
+    return res
+
+
 def batched_run(ctx, device, stream, reps=20):
     """64 uneven grids: one batched call (tuned size classes) vs 64 default launches."""
     import torch
@@ -611,6 +653,7 @@ def main():
         extras["workloads"] = workload_sweep(ctx, device, stream, max(20, args.steps // 20))
         extras["launch_overhead"] = launch_overhead(local, wisdom, device)
         extras["diag"] = diag_timing(ctx, p, outs, stream, ins=ins)
+        extras["les_step"] = les_step(ctx, stream, peak_gbs)
 
     # --- end to end through the public API with pinned host buffers (every rank)
     # three repeats each, the median reported: the host link and host memory

@@ -255,6 +255,23 @@ kl_status kl_dot(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, int32_t level,
 kl_status kl_diag_noalloc(int32_t dtype, const kl_grid *grid, const void *t, const double *ref,
                           const double *wz, double out[6], void *stream);
 
+/*
+ * Smagorinsky eddy viscosity, the nu that diff = 2 takes (the "Smagorinsky
+ * diffusion" of Sec. 5.2): on `stream`, for every interior cell centre,
+ *   nu = (cs * delta_k)^2 * sqrt(2 S_ij S_ij),  delta_k = (dx dy dz_k)^(1/3),
+ * S_ij = (d_i u_j + d_j u_i)/2 on the staggered grid: the normal strains at
+ * the centre, each shear strain squared on the four edges around the cell and
+ * averaged.  u, v, w (device, layout grid, type dtype, ghosts filled; one
+ * ghost cell is enough) are read; nu (device, same layout and type, not
+ * aliasing them) gets the interior, and with fill_ghosts != 0 also its ghost
+ * cells by the rules of kl_fill_ghosts (even mirror at walls).  Arithmetic
+ * in f64 for f64 storage, else f32.  KL_ERR_INVALID_ARG for NULL or
+ * misaligned fields, a bad dtype or a negative or non-finite cs.
+ */
+kl_status kl_smagorinsky(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, double cs,
+                         const void *u, const void *v, const void *w, void *nu,
+                         int32_t fill_ghosts, void *stream);
+
 /* Context statistics as JSON into buf (host, n bytes): cache hits/misses,
  * the four first-launch stage times of Sec. 5.6 (wisdom read, NVRTC,
  * module load, launch), launches, and the last selected record. */

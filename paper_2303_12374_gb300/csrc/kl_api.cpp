@@ -860,6 +860,34 @@ kl_status kl_dot(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, int32_t level,
     return KL_OK;
 }
 
+kl_status kl_smagorinsky(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, double cs,
+                         const void *u, const void *v, const void *w, void *nu,
+                         int32_t fill_ghosts, void *stream)
+{
+    if (!ctx || !u || !v || !w || !nu) return fail(KL_ERR_INVALID_ARG, "ctx, u, v, w and nu must not be NULL");
+    if (dtype < 0 || dtype > 3) return fail(KL_ERR_INVALID_ARG, "bad dtype");
+    if (!(cs >= 0) || !std::isfinite(cs)) return fail(KL_ERR_INVALID_ARG, "cs must be finite and >= 0");
+    kl_status st = check_grid(grid, 1, nullptr);
+    if (st) return st;
+    const int es = esize_of(dtype);
+    for (const void *p : {u, v, w, (const void *)nu})
+        if ((uintptr_t)p % (uintptr_t)es) return fail(KL_ERR_INVALID_ARG, "field not aligned to its element size");
+    if (u == nu || v == nu || w == nu) return fail(KL_ERR_INVALID_ARG, "nu must not alias u, v or w");
+    Profile *prof = nullptr;
+    st = get_profile(ctx, *grid, &prof);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = smag_launch(dtype, *grid, cs, u, v, w, nu, prof->d64, prof->d32, prof->n, s);
+    if (e != cudaSuccess) return cuda_fail(e, "smagorinsky launch");
+    ctx->launches++;
+    if (fill_ghosts) {
+        e = fill_ghosts_launch(es, *grid, nullptr, nullptr, nullptr, nu, s, true);
+        if (e != cudaSuccess) return cuda_fail(e, "nu ghost fill");
+        ctx->launches++;
+    }
+    return KL_OK;
+}
+
 kl_status kl_set_wait_limit(kl_ctx *ctx, int64_t cycles)
 {
     if (!ctx || cycles < 0) return fail(KL_ERR_INVALID_ARG, "ctx is NULL or cycles < 0");

@@ -29,7 +29,7 @@ namespace {
 constexpr int FILL_T = 256, FILL_W = FILL_T / 32, FILL_RU = 9, FILL_U = 4;
 
 struct FillArgs {
-    char *f[4];              // u, v, w, nu at interior (0,0,0); nu may be NULL
+    char *f[4];              // u, v, w, nu at interior (0,0,0); NULL: not filled
     long long sj, sk;
     int nx, ny, nz, zbc;
     int rows_z, rows_y;      // rows of the z-plane group (2g x padded ny), y-row group (2g x nz)
@@ -80,7 +80,7 @@ __device__ __forceinline__ void fill_row(const FillArgs &a, int j, int k, int la
             const int si = wrapi(i, a.nx);
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
-                if (f != 2 && !a.f[f]) continue;
+                if (!a.f[f]) continue;
                 const B *p = (const B *)a.f[f];
                 if (f != 2) val[c][f] = p[src0 + si];
                 else if (!wzero) val[c][f] = p[srcw0 + si];
@@ -92,7 +92,7 @@ __device__ __forceinline__ void fill_row(const FillArgs &a, int j, int k, int la
             if (i >= a.nx + G) continue;
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
-                if (f != 2 && !a.f[f]) continue;
+                if (!a.f[f]) continue;
                 ((B *)a.f[f])[dst0 + i] = f != 2 ? val[c][f] : fill_w<B>(val[c][f], wzero, wneg);
             }
         }
@@ -141,14 +141,14 @@ __global__ void __launch_bounds__(FILL_T) fill_kernel(FillArgs a)
         if (!live[c]) continue;
 #pragma unroll
         for (int f = 0; f < 4; ++f)
-            if (f == 2 || a.f[f]) val[c][f] = ((const B *)a.f[f])[f == 2 ? srcw[c] : src[c]];
+            if (a.f[f]) val[c][f] = ((const B *)a.f[f])[f == 2 ? srcw[c] : src[c]];
     }
 #pragma unroll
     for (int c = 0; c < FILL_U; ++c) {
         if (!live[c]) continue;
 #pragma unroll
         for (int f = 0; f < 4; ++f)
-            if (f == 2 || a.f[f]) ((B *)a.f[f])[dst[c]] = val[c][f];
+            if (a.f[f]) ((B *)a.f[f])[dst[c]] = val[c][f];
     }
 }
 
@@ -399,9 +399,9 @@ cudaError_t fill_ghosts_launch(int esize, const kl_grid &g, void *u, void *v, vo
     if (g.g < 1 || g.g > 4) return cudaErrorInvalidValue;
     FillArgs a;
     size_t off = (size_t)g.origin * esize;
-    a.f[0] = (char *)u + off;
-    a.f[1] = (char *)v + off;
-    a.f[2] = (char *)w + off;
+    a.f[0] = u ? (char *)u + off : nullptr;     // any field may be absent
+    a.f[1] = v ? (char *)v + off : nullptr;
+    a.f[2] = w ? (char *)w + off : nullptr;
     a.f[3] = nu ? (char *)nu + off : nullptr;
     a.sj = g.sj;
     a.sk = g.sk;
@@ -668,6 +668,156 @@ cudaError_t compare_launch(int dtype, const kl_grid &g, const void *a, const voi
     case KL_F32: compare_kernel<float><<<nb, 256, 0, s>>>((const float *)pa, (const float *)pb, g.sj, g.sk, g.nx, g.ny, n, dout); break;
     case KL_BF16: compare_kernel<__nv_bfloat16><<<nb, 256, 0, s>>>((const __nv_bfloat16 *)pa, (const __nv_bfloat16 *)pb, g.sj, g.sk, g.nx, g.ny, n, dout); break;
     default: compare_kernel<__half><<<nb, 256, 0, s>>>((const __half *)pa, (const __half *)pb, g.sj, g.sk, g.nx, g.ny, n, dout); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace kl
+
+namespace {
+
+// ------------------------------------------------- Smagorinsky viscosity
+//
+// nu = (cs delta_k)^2 sqrt(2 S_ij S_ij) at the interior cell centres,
+// delta_k = (dx dy dz_k)^(1/3); the normal strains at the centre, each shear
+// strain squared on the four edges around the cell and averaged, so
+//   2 S_ij S_ij = 2 (Sxx^2 + Syy^2 + Szz^2) + sum over the 12 edges of e^2,
+// e = (d_i u_j + d_j u_i)/2 on the edge.  One thread per (i, j) column marches
+// up SMAG_KC levels: the values of its own column at the current level and the
+// two vertical-edge strains above it carry into the next level, so each level
+// reads 17 values (9 at k+1, 8 neighbours at k), all coalesced along x.
+// HBM-bound: u, v, w read once from memory, nu written once.
+
+constexpr int SMAG_BX = 32, SMAG_BY = 8;
+
+struct SmagArgs {
+    const void *u, *v, *w;   // at interior (0,0,0)
+    void *nu;
+    const double *dzi64, *dzhi64, *dz64;   // index k + g
+    const float *dzi32, *dzhi32;
+    long long sj, sk;
+    int nx, ny, nz, g, kc;
+    double dxi, dyi, dxdy, cs;
+};
+
+template <typename T> __device__ __forceinline__ float ldf(const T *p) { return (float)*p; }
+template <> __device__ __forceinline__ float ldf<__nv_bfloat16>(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+template <> __device__ __forceinline__ float ldf<__half>(const __half *p) { return __half2float(*p); }
+template <typename T> __device__ __forceinline__ void stf(T *p, float x) { *p = (T)x; }
+template <> __device__ __forceinline__ void stf<__nv_bfloat16>(__nv_bfloat16 *p, float x) { *p = __float2bfloat16_rn(x); }
+template <> __device__ __forceinline__ void stf<__half>(__half *p, float x) { *p = __float2half_rn(x); }
+
+// compute type C: double for f64 storage, float otherwise
+template <typename T, typename C>
+__device__ __forceinline__ C ldc(const T *p) { return (C)ldf<T>(p); }
+template <>
+__device__ __forceinline__ double ldc<double, double>(const double *p) { return *p; }
+
+template <typename T, typename C>
+__global__ void __launch_bounds__(SMAG_BX * SMAG_BY) smag_kernel(SmagArgs a)
+{
+    const int i = blockIdx.x * SMAG_BX + threadIdx.x;
+    const int j = blockIdx.y * SMAG_BY + threadIdx.y;
+    const int k0 = blockIdx.z * a.kc;
+    if (i >= a.nx || j >= a.ny || k0 >= a.nz) return;
+    const int k1 = min(k0 + a.kc, a.nz);
+    const T *u = (const T *)a.u, *v = (const T *)a.v, *w = (const T *)a.w;
+    T *nu = (T *)a.nu;
+    const long long sj = a.sj, sk = a.sk;
+    const C dxi = (C)a.dxi, dyi = (C)a.dyi, half = (C)0.5;
+    auto dzi = [&](int k) { return sizeof(C) == 8 ? (C)a.dzi64[k + a.g] : (C)a.dzi32[k + a.g]; };
+    auto dzhi = [&](int k) { return sizeof(C) == 8 ? (C)a.dzhi64[k + a.g] : (C)a.dzhi32[k + a.g]; };
+
+    long long o = i + j * sj + (long long)k0 * sk;
+    // own column at level k0, and the vertical-edge strains on the face below
+    C u0 = ldc<T, C>(u + o), u1 = ldc<T, C>(u + o + 1);
+    C v0 = ldc<T, C>(v + o), v1 = ldc<T, C>(v + o + sj);
+    C w0 = ldc<T, C>(w + o);
+    C exz0, exz1, eyz0, eyz1;
+    {
+        const C zi = dzhi(k0);
+        exz0 = half * ((u0 - ldc<T, C>(u + o - sk)) * zi + (w0 - ldc<T, C>(w + o - 1)) * dxi);
+        exz1 = half * ((u1 - ldc<T, C>(u + o + 1 - sk)) * zi + (ldc<T, C>(w + o + 1) - w0) * dxi);
+        eyz0 = half * ((v0 - ldc<T, C>(v + o - sk)) * zi + (w0 - ldc<T, C>(w + o - sj)) * dyi);
+        eyz1 = half * ((v1 - ldc<T, C>(v + o + sj - sk)) * zi + (ldc<T, C>(w + o + sj) - w0) * dyi);
+    }
+    for (int k = k0; k < k1; ++k, o += sk) {
+        const long long p = o + sk;
+        // level k + 1: own column and the faces above
+        const C u0n = ldc<T, C>(u + p), u1n = ldc<T, C>(u + p + 1);
+        const C v0n = ldc<T, C>(v + p), v1n = ldc<T, C>(v + p + sj);
+        const C w0n = ldc<T, C>(w + p);
+        const C wxm = ldc<T, C>(w + p - 1), wxp = ldc<T, C>(w + p + 1);
+        const C wym = ldc<T, C>(w + p - sj), wyp = ldc<T, C>(w + p + sj);
+        // level k: the neighbours of the horizontal edges
+        const C uym0 = ldc<T, C>(u + o - sj), uym1 = ldc<T, C>(u + o + 1 - sj);
+        const C uyp0 = ldc<T, C>(u + o + sj), uyp1 = ldc<T, C>(u + o + 1 + sj);
+        const C vxm0 = ldc<T, C>(v + o - 1), vxp0 = ldc<T, C>(v + o + 1);
+        const C vxm1 = ldc<T, C>(v + o - 1 + sj), vxp1 = ldc<T, C>(v + o + 1 + sj);
+
+        const C zi = dzhi(k + 1);
+        const C exz0n = half * ((u0n - u0) * zi + (w0n - wxm) * dxi);
+        const C exz1n = half * ((u1n - u1) * zi + (wxp - w0n) * dxi);
+        const C eyz0n = half * ((v0n - v0) * zi + (w0n - wym) * dyi);
+        const C eyz1n = half * ((v1n - v1) * zi + (wyp - w0n) * dyi);
+        const C sxx = (u1 - u0) * dxi, syy = (v1 - v0) * dyi, szz = (w0n - w0) * dzi(k);
+        const C e00 = half * ((u0 - uym0) * dyi + (v0 - vxm0) * dxi);
+        const C e10 = half * ((u1 - uym1) * dyi + (vxp0 - v0) * dxi);
+        const C e01 = half * ((uyp0 - u0) * dyi + (v1 - vxm1) * dxi);
+        const C e11 = half * ((uyp1 - u1) * dyi + (vxp1 - v1) * dxi);
+        C s2 = (C)2 * (sxx * sxx + syy * syy + szz * szz);
+        s2 += e00 * e00 + e10 * e10 + e01 * e01 + e11 * e11;
+        s2 += exz0 * exz0 + exz1 * exz1 + exz0n * exz0n + exz1n * exz1n;
+        s2 += eyz0 * eyz0 + eyz1 * eyz1 + eyz0n * eyz0n + eyz1n * eyz1n;
+        const C delta = cbrt((C)a.dxdy * (sizeof(C) == 8 ? (C)a.dz64[k + a.g] : (C)1 / dzi(k)));
+        const C cd = (C)a.cs * delta;
+        const C val = cd * cd * sqrt(s2);
+        if (sizeof(C) == 8) ((double *)nu)[o] = (double)val;
+        else stf<T>(nu + o, (float)val);
+        u0 = u0n; u1 = u1n; v0 = v0n; v1 = v1n; w0 = w0n;
+        exz0 = exz0n; exz1 = exz1n; eyz0 = eyz0n; eyz1 = eyz1n;
+    }
+}
+
+}  // namespace
+
+namespace kl {
+
+cudaError_t smag_launch(int dtype, const kl_grid &g, double cs, const void *u, const void *v,
+                        const void *w, void *nu, const double *d64, const float *d32, int nprof,
+                        cudaStream_t s)
+{
+    const int es = esize_of(dtype);
+    const size_t off = (size_t)g.origin * es;
+    SmagArgs a;
+    a.u = (const char *)u + off;
+    a.v = (const char *)v + off;
+    a.w = (const char *)w + off;
+    a.nu = (char *)nu + off;
+    a.dzi64 = d64;
+    a.dzhi64 = d64 + nprof;
+    a.dz64 = d64 + 2 * nprof;
+    a.dzi32 = d32;
+    a.dzhi32 = d32 + nprof;
+    a.sj = g.sj;
+    a.sk = g.sk;
+    a.nx = g.nx;
+    a.ny = g.ny;
+    a.nz = g.nz;
+    a.g = g.g;
+    a.kc = 16;
+    a.dxi = 1.0 / g.dx;
+    a.dyi = 1.0 / g.dy;
+    a.dxdy = g.dx * g.dy;
+    a.cs = cs;
+    dim3 block(SMAG_BX, SMAG_BY);
+    dim3 grid((g.nx + SMAG_BX - 1) / SMAG_BX, (g.ny + SMAG_BY - 1) / SMAG_BY, (g.nz + a.kc - 1) / a.kc);
+    if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
+    switch (dtype) {
+    case KL_F64: smag_kernel<double, double><<<grid, block, 0, s>>>(a); break;
+    case KL_F32: smag_kernel<float, float><<<grid, block, 0, s>>>(a); break;
+    case KL_BF16: smag_kernel<__nv_bfloat16, float><<<grid, block, 0, s>>>(a); break;
+    default: smag_kernel<__half, float><<<grid, block, 0, s>>>(a); break;
     }
     return cudaGetLastError();
 }

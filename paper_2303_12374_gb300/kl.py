@@ -112,6 +112,8 @@ SIGNATURES = {
     "kl_def_selected": ([_P, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(_I32)], ctypes.c_int),
     "kl_def_capture": ([_P, _P, ctypes.POINTER(_I64), _I32, _P, _S, _P], ctypes.c_int),
     "kl_def_tune": ([_P, _P, _S, _S, _S], ctypes.c_int),
+    "kl_smagorinsky": ([_P, _I32, ctypes.POINTER(Grid), _D, _P, _P, _P, _P, _I32, _P],
+                       ctypes.c_int),
     "kl_version": ([], _S),
 }
 
@@ -269,6 +271,11 @@ def kl_compile_only(op: Op, config: str, zbc: int = 0, zuni: int = 1) -> str:
     buf = ctypes.create_string_buffer(65536)
     check(load().kl_compile_only(ctypes.byref(op), _b(config), zbc, zuni, buf, len(buf)))
     return buf.value.decode()
+
+
+def kl_smagorinsky(ctx, dtype, grid: Grid, cs, u, v, w, nu, fill_ghosts=True, stream=None) -> None:
+    check(load().kl_smagorinsky(ctx, dtype, ctypes.byref(grid), cs, u, v, w, nu,
+                                1 if fill_ghosts else 0, stream))
 
 
 def kl_set_cache_dir(ctx, path) -> None:
