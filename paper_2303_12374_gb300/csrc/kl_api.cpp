@@ -876,8 +876,36 @@ kl_status kl_smagorinsky(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, double
     Profile *prof = nullptr;
     st = get_profile(ctx, *grid, &prof);
     if (st) return st;
+    // (cs delta_k)^2 per level, f64 then f32, one table per z grid, dx, dy and cs
+    std::vector<double> dzi, dzhi;
+    zprofile_host(grid->nz, grid->g, grid->zbc, grid->zh, grid->dz, &dzi, &dzhi);
+    std::vector<double> c64((size_t)grid->nz);
+    for (int k = 0; k < grid->nz; ++k) {
+        const double cd = cs * std::cbrt(grid->dx * grid->dy / dzi[(size_t)(k + grid->g)]);
+        c64[(size_t)k] = cd * cd;
+    }
+    std::string key = "smag:" + std::to_string(fnv1a(c64.data(), c64.size() * sizeof(double)));
+    auto it = ctx->tables.find(key);
+    if (it == ctx->tables.end()) {
+        size_t nb = c64.size() * (sizeof(double) + sizeof(float));
+        std::vector<char> h(nb);
+        memcpy(h.data(), c64.data(), c64.size() * sizeof(double));
+        for (size_t k = 0; k < c64.size(); ++k) {
+            float f = (float)c64[k];
+            memcpy(h.data() + c64.size() * sizeof(double) + k * sizeof(float), &f, sizeof f);
+        }
+        void *d = nullptr;
+        if (cudaMalloc(&d, nb) != cudaSuccess) return fail(KL_ERR_OOM, "cudaMalloc(smagorinsky table)");
+        if (cudaMemcpy(d, h.data(), nb, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(d);
+            return fail(KL_ERR_CUDA, "smagorinsky table upload");
+        }
+        it = ctx->tables.emplace(key, std::make_pair(d, nb)).first;
+    }
+    const double *cc64 = (const double *)it->second.first;
+    const float *cc32 = (const float *)(cc64 + grid->nz);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = smag_launch(dtype, *grid, cs, u, v, w, nu, prof->d64, prof->d32, prof->n, s);
+    cudaError_t e = smag_launch(dtype, *grid, u, v, w, nu, prof->d64, prof->d32, prof->n, cc64, cc32, s);
     if (e != cudaSuccess) return cuda_fail(e, "smagorinsky launch");
     ctx->launches++;
     if (fill_ghosts) {

@@ -679,7 +679,7 @@ namespace {
 // ------------------------------------------------- Smagorinsky viscosity
 //
 // nu = (cs delta_k)^2 sqrt(2 S_ij S_ij) at the interior cell centres,
-// delta_k = (dx dy dz_k)^(1/3); the normal strains at the centre, each shear
+// delta_k = (dx dy dz_k)^(1/3), the factor per level from a table; the normal strains at the centre, each shear
 // strain squared on the four edges around the cell and averaged, so
 //   2 S_ij S_ij = 2 (Sxx^2 + Syy^2 + Szz^2) + sum over the 12 edges of e^2,
 // e = (d_i u_j + d_j u_i)/2 on the edge.  One thread per (i, j) column marches
@@ -693,11 +693,13 @@ constexpr int SMAG_BX = 32, SMAG_BY = 8;
 struct SmagArgs {
     const void *u, *v, *w;   // at interior (0,0,0)
     void *nu;
-    const double *dzi64, *dzhi64, *dz64;   // index k + g
+    const double *dzi64, *dzhi64;          // index k + g
     const float *dzi32, *dzhi32;
+    const double *cc64;                    // (cs delta_k)^2, index k
+    const float *cc32;
     long long sj, sk;
     int nx, ny, nz, g, kc;
-    double dxi, dyi, dxdy, cs;
+    double dxi, dyi;
 };
 
 template <typename T> __device__ __forceinline__ float ldf(const T *p) { return (float)*p; }
@@ -769,9 +771,8 @@ __global__ void __launch_bounds__(SMAG_BX * SMAG_BY) smag_kernel(SmagArgs a)
         s2 += e00 * e00 + e10 * e10 + e01 * e01 + e11 * e11;
         s2 += exz0 * exz0 + exz1 * exz1 + exz0n * exz0n + exz1n * exz1n;
         s2 += eyz0 * eyz0 + eyz1 * eyz1 + eyz0n * eyz0n + eyz1n * eyz1n;
-        const C delta = cbrt((C)a.dxdy * (sizeof(C) == 8 ? (C)a.dz64[k + a.g] : (C)1 / dzi(k)));
-        const C cd = (C)a.cs * delta;
-        const C val = cd * cd * sqrt(s2);
+        const C cc = sizeof(C) == 8 ? (C)a.cc64[k] : (C)a.cc32[k];
+        const C val = cc * sqrt(s2);
         if (sizeof(C) == 8) ((double *)nu)[o] = (double)val;
         else stf<T>(nu + o, (float)val);
         u0 = u0n; u1 = u1n; v0 = v0n; v1 = v1n; w0 = w0n;
@@ -779,13 +780,187 @@ __global__ void __launch_bounds__(SMAG_BX * SMAG_BY) smag_kernel(SmagArgs a)
     }
 }
 
+// Four x-points per thread (i = 4t .. 4t+3) with 4-wide loads: used when nx,
+// the interior origin and both strides are multiples of 4 elements and the
+// fields are aligned to 4 elements, so every 4-wide access starts inside
+// the interior row and the single-element x neighbours (i - 1, i + 4) are
+// interior points or the first ghost.  The vertical-edge strains of the five
+// x-edges and of the two y-edges of the four points carry from one level to
+// the next, and each horizontal edge strain serves the two points beside it.
+
+template <typename T, typename C> struct Quad;
+template <> struct Quad<float, float> {
+    static __device__ __forceinline__ void ld(const float *p, float o[4])
+    {
+        const float4 x = *(const float4 *)p;
+        o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w;
+    }
+    static __device__ __forceinline__ void st(float *p, const float o[4])
+    {
+        *(float4 *)p = make_float4(o[0], o[1], o[2], o[3]);
+    }
+};
+template <> struct Quad<double, double> {
+    static __device__ __forceinline__ void ld(const double *p, double o[4])
+    {
+        const double2 a = ((const double2 *)p)[0], b = ((const double2 *)p)[1];
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+    }
+    static __device__ __forceinline__ void st(double *p, const double o[4])
+    {
+        ((double2 *)p)[0] = make_double2(o[0], o[1]);
+        ((double2 *)p)[1] = make_double2(o[2], o[3]);
+    }
+};
+template <> struct Quad<__nv_bfloat16, float> {
+    static __device__ __forceinline__ void ld(const __nv_bfloat16 *p, float o[4])
+    {
+        const __nv_bfloat162 *q = (const __nv_bfloat162 *)p;
+        const float2 a = __bfloat1622float2(q[0]), b = __bfloat1622float2(q[1]);
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, const float o[4])
+    {
+        __nv_bfloat162 *q = (__nv_bfloat162 *)p;
+        q[0] = __float22bfloat162_rn(make_float2(o[0], o[1]));
+        q[1] = __float22bfloat162_rn(make_float2(o[2], o[3]));
+    }
+};
+template <> struct Quad<__half, float> {
+    static __device__ __forceinline__ void ld(const __half *p, float o[4])
+    {
+        const __half2 *q = (const __half2 *)p;
+        const float2 a = __half22float2(q[0]), b = __half22float2(q[1]);
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+    }
+    static __device__ __forceinline__ void st(__half *p, const float o[4])
+    {
+        __half2 *q = (__half2 *)p;
+        q[0] = __float22half2_rn(make_float2(o[0], o[1]));
+        q[1] = __float22half2_rn(make_float2(o[2], o[3]));
+    }
+};
+
+template <typename T, typename C>
+__global__ void __launch_bounds__(SMAG_BX * SMAG_BY, sizeof(C) == 8 ? 1 : 3) smag_kernel4(SmagArgs a)
+{
+    using Q = Quad<T, C>;
+    const int i = 4 * (blockIdx.x * SMAG_BX + threadIdx.x);
+    const int j = blockIdx.y * SMAG_BY + threadIdx.y;
+    const int k0 = blockIdx.z * a.kc;
+    if (i >= a.nx || j >= a.ny || k0 >= a.nz) return;
+    const int k1 = min(k0 + a.kc, a.nz);
+    const T *u = (const T *)a.u, *v = (const T *)a.v, *w = (const T *)a.w;
+    T *nu = (T *)a.nu;
+    const long long sj = a.sj, sk = a.sk;
+    const C dxi = (C)a.dxi, dyi = (C)a.dyi, half = (C)0.5;
+    auto dzi = [&](int k) { return sizeof(C) == 8 ? (C)a.dzi64[k + a.g] : (C)a.dzi32[k + a.g]; };
+    auto dzhi = [&](int k) { return sizeof(C) == 8 ? (C)a.dzhi64[k + a.g] : (C)a.dzhi32[k + a.g]; };
+
+    long long o = i + j * sj + (long long)k0 * sk;
+    // level k0: u at x = i .. i+4, v at rows j and j+1, w; then the edge
+    // strains on the face below (x-edges at i .. i+4, y-edges at j and j+1)
+    C U[5], V0[4], V1[4], W[4], EXZ[5], EYZ0[4], EYZ1[4];
+    {
+        C Ub[5], V0b[4], V1b[4], Wx[6], Wjm[4], Wjp[4];
+        Q::ld(u + o, U);
+        U[4] = ldc<T, C>(u + o + 4);
+        Q::ld(v + o, V0);
+        Q::ld(v + o + sj, V1);
+        Q::ld(w + o, W);
+        Q::ld(u + o - sk, Ub);
+        Ub[4] = ldc<T, C>(u + o + 4 - sk);
+        Q::ld(v + o - sk, V0b);
+        Q::ld(v + o + sj - sk, V1b);
+        Wx[0] = ldc<T, C>(w + o - 1);
+        Wx[5] = ldc<T, C>(w + o + 4);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Wx[q + 1] = W[q];
+        Q::ld(w + o - sj, Wjm);
+        Q::ld(w + o + sj, Wjp);
+        const C zi = dzhi(k0);
+#pragma unroll
+        for (int e = 0; e < 5; ++e) EXZ[e] = half * ((U[e] - Ub[e]) * zi + (Wx[e + 1] - Wx[e]) * dxi);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            EYZ0[q] = half * ((V0[q] - V0b[q]) * zi + (W[q] - Wjm[q]) * dyi);
+            EYZ1[q] = half * ((V1[q] - V1b[q]) * zi + (Wjp[q] - W[q]) * dyi);
+        }
+    }
+    for (int k = k0; k < k1; ++k, o += sk) {
+        const long long p = o + sk;
+        C Un[5], V0n[4], V1n[4], Wn[4], Wx[6], Wjm[4], Wjp[4];
+        Q::ld(u + p, Un);
+        Un[4] = ldc<T, C>(u + p + 4);
+        Q::ld(v + p, V0n);
+        Q::ld(v + p + sj, V1n);
+        Q::ld(w + p, Wn);
+        Wx[0] = ldc<T, C>(w + p - 1);
+        Wx[5] = ldc<T, C>(w + p + 4);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Wx[q + 1] = Wn[q];
+        Q::ld(w + p - sj, Wjm);
+        Q::ld(w + p + sj, Wjp);
+        // level k: u in rows j - 1 and j + 1, v at x = i - 1 and i + 4
+        C Ujm[5], Ujp[5];
+        Q::ld(u + o - sj, Ujm);
+        Ujm[4] = ldc<T, C>(u + o + 4 - sj);
+        Q::ld(u + o + sj, Ujp);
+        Ujp[4] = ldc<T, C>(u + o + 4 + sj);
+        const C v0m = ldc<T, C>(v + o - 1), v0p = ldc<T, C>(v + o + 4);
+        const C v1m = ldc<T, C>(v + o - 1 + sj), v1p = ldc<T, C>(v + o + 4 + sj);
+
+        const C zi = dzhi(k + 1), dzik = dzi(k);
+        C EXZn[5], EYZ0n[4], EYZ1n[4], E0[5], E1[5];
+#pragma unroll
+        for (int e = 0; e < 5; ++e) {
+            EXZn[e] = half * ((Un[e] - U[e]) * zi + (Wx[e + 1] - Wx[e]) * dxi);
+            const C v0l = e == 0 ? v0m : V0[e - 1], v0r = e == 4 ? v0p : V0[e];
+            const C v1l = e == 0 ? v1m : V1[e - 1], v1r = e == 4 ? v1p : V1[e];
+            E0[e] = half * ((U[e] - Ujm[e]) * dyi + (v0r - v0l) * dxi);
+            E1[e] = half * ((Ujp[e] - U[e]) * dyi + (v1r - v1l) * dxi);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            EYZ0n[q] = half * ((V0n[q] - V0[q]) * zi + (Wn[q] - Wjm[q]) * dyi);
+            EYZ1n[q] = half * ((V1n[q] - V1[q]) * zi + (Wjp[q] - Wn[q]) * dyi);
+        }
+        const C cc = sizeof(C) == 8 ? (C)a.cc64[k] : (C)a.cc32[k];
+        C out[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const C sxx = (U[q + 1] - U[q]) * dxi, syy = (V1[q] - V0[q]) * dyi;
+            const C szz = (Wn[q] - W[q]) * dzik;
+            C s2 = (C)2 * (sxx * sxx + syy * syy + szz * szz);
+            s2 += E0[q] * E0[q] + E0[q + 1] * E0[q + 1] + E1[q] * E1[q] + E1[q + 1] * E1[q + 1];
+            s2 += EXZ[q] * EXZ[q] + EXZ[q + 1] * EXZ[q + 1] + EXZn[q] * EXZn[q] + EXZn[q + 1] * EXZn[q + 1];
+            s2 += EYZ0[q] * EYZ0[q] + EYZ1[q] * EYZ1[q] + EYZ0n[q] * EYZ0n[q] + EYZ1n[q] * EYZ1n[q];
+            out[q] = cc * sqrt(s2);
+        }
+        Q::st(nu + o, out);
+#pragma unroll
+        for (int e = 0; e < 5; ++e) {
+            U[e] = Un[e];
+            EXZ[e] = EXZn[e];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            V0[q] = V0n[q];
+            V1[q] = V1n[q];
+            W[q] = Wn[q];
+            EYZ0[q] = EYZ0n[q];
+            EYZ1[q] = EYZ1n[q];
+        }
+    }
+}
+
 }  // namespace
 
 namespace kl {
 
-cudaError_t smag_launch(int dtype, const kl_grid &g, double cs, const void *u, const void *v,
-                        const void *w, void *nu, const double *d64, const float *d32, int nprof,
-                        cudaStream_t s)
+cudaError_t smag_launch(int dtype, const kl_grid &g, const void *u, const void *v, const void *w,
+                        void *nu, const double *d64, const float *d32, int nprof,
+                        const double *cc64, const float *cc32, cudaStream_t s)
 {
     const int es = esize_of(dtype);
     const size_t off = (size_t)g.origin * es;
@@ -796,9 +971,10 @@ cudaError_t smag_launch(int dtype, const kl_grid &g, double cs, const void *u, c
     a.nu = (char *)nu + off;
     a.dzi64 = d64;
     a.dzhi64 = d64 + nprof;
-    a.dz64 = d64 + 2 * nprof;
     a.dzi32 = d32;
     a.dzhi32 = d32 + nprof;
+    a.cc64 = cc64;
+    a.cc32 = cc32;
     a.sj = g.sj;
     a.sk = g.sk;
     a.nx = g.nx;
@@ -808,9 +984,23 @@ cudaError_t smag_launch(int dtype, const kl_grid &g, double cs, const void *u, c
     a.kc = 16;
     a.dxi = 1.0 / g.dx;
     a.dyi = 1.0 / g.dy;
-    a.dxdy = g.dx * g.dy;
-    a.cs = cs;
     dim3 block(SMAG_BX, SMAG_BY);
+    const uintptr_t al = 4 * (uintptr_t)es;
+    const bool quad = g.nx % 4 == 0 && g.origin % 4 == 0 && g.sj % 4 == 0 && g.sk % 4 == 0 &&
+                      (uintptr_t)u % al == 0 && (uintptr_t)v % al == 0 && (uintptr_t)w % al == 0 &&
+                      (uintptr_t)nu % al == 0;
+    if (quad) {
+        dim3 grid((g.nx / 4 + SMAG_BX - 1) / SMAG_BX, (g.ny + SMAG_BY - 1) / SMAG_BY,
+                  (g.nz + a.kc - 1) / a.kc);
+        if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
+        switch (dtype) {
+        case KL_F64: smag_kernel4<double, double><<<grid, block, 0, s>>>(a); break;
+        case KL_F32: smag_kernel4<float, float><<<grid, block, 0, s>>>(a); break;
+        case KL_BF16: smag_kernel4<__nv_bfloat16, float><<<grid, block, 0, s>>>(a); break;
+        default: smag_kernel4<__half, float><<<grid, block, 0, s>>>(a); break;
+        }
+        return cudaGetLastError();
+    }
     dim3 grid((g.nx + SMAG_BX - 1) / SMAG_BX, (g.ny + SMAG_BY - 1) / SMAG_BY, (g.nz + a.kc - 1) / a.kc);
     if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
     switch (dtype) {

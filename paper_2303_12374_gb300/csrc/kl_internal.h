@@ -257,9 +257,9 @@ cudaError_t dot_launch(int dtype, const kl_grid &g, const void *x, const void *y
 cudaError_t compare_launch(int dtype, const kl_grid &g, const void *a, const void *b,
                            unsigned long long *dout, int nsm, cudaStream_t s);
 // Smagorinsky viscosity at the interior cell centres (profile arrays of get_profile)
-cudaError_t smag_launch(int dtype, const kl_grid &g, double cs, const void *u, const void *v,
-                        const void *w, void *nu, const double *d64, const float *d32, int nprof,
-                        cudaStream_t s);
+cudaError_t smag_launch(int dtype, const kl_grid &g, const void *u, const void *v, const void *w,
+                        void *nu, const double *d64, const float *d32, int nprof,
+                        const double *cc64, const float *cc32, cudaStream_t s);
 // load a compiled cubin into the context's cache under its compile key
 kl_status load_compiled(kl_ctx *ctx, const kl_op &op, const Config &cfg, const std::string &key,
                         const Compiled &c, Kernel **out);
