@@ -360,7 +360,9 @@ kl_status kl_cache_prepare(const char *dir, const kl_op *op, const char *config,
  * name (a C identifier) that names its wisdom file <wisdom dir>/<name>.wisdom.
  * Tunable parameters, restrictions, geometry and extra compile options are
  * added with the calls below.  The definition owns copies of all strings;
- * it is host data, usable with any context.
+ * it is host data, usable with any context.  Like a context, one definition
+ * must not be used by two host threads at once (launches record their
+ * selection in it).
  */
 typedef struct kl_def kl_def;
 

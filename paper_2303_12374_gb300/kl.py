@@ -404,7 +404,10 @@ class KernelDef:
             self.h = None
 
     def __del__(self):
-        self.close()
+        try:
+            self.close()
+        except Exception:       # interpreter shutdown: the library may be gone
+            pass
 
     def param(self, name, values, default=None):
         vals = (ctypes.c_int64 * len(values))(*values)
