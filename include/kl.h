@@ -192,6 +192,21 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
                             const kl_fields *fields, void *stream);
 
 /*
+ * Shard a batch across `world` ranks with no communication (independent
+ * grids, one rank per GPU): longest-processing-time bin packing by interior
+ * point count.  Grids go in decreasing order of points[q] (host, n values;
+ * ties by index) each to the rank with the least load so far (ties to the
+ * lower rank), so every rank computes the same assignment.  The largest rank
+ * load is at most (4/3 - 1/(3 world)) times the best possible (Graham's bound
+ * for this rule) and at most the mean load plus the largest grid.  Writes
+ * the indices owned by `rank`, ascending, to
+ * out (host, room for n), their number to *count and their total points to
+ * *load (may be NULL).  Host only.
+ */
+kl_status kl_batch_shard(int32_t n, const int64_t *points, int32_t world, int32_t rank,
+                         int32_t *out, int32_t *count, int64_t *load);
+
+/*
  * Capture (Sec. 4.2): synchronise `stream`, copy every input buffer of the
  * launch device->host and write the definition, problem, layout, scalars and
  * data to `path` (host string).  The launch can then be replayed by kl_tune.

@@ -927,6 +927,35 @@ kl_status kl_tune(kl_ctx *ctx, const char *capture_path, const char *opts, const
     return KL_OK;
 }
 
+kl_status kl_batch_shard(int32_t n, const int64_t *points, int32_t world, int32_t rank,
+                         int32_t *out, int32_t *count, int64_t *load)
+{
+    if (n < 0 || world < 1 || rank < 0 || rank >= world || (n > 0 && (!points || !out)) || !count)
+        return fail(KL_ERR_INVALID_ARG, "batch shard: bad arguments");
+    for (int32_t q = 0; q < n; ++q)
+        if (points[q] < 0) return fail(KL_ERR_INVALID_ARG, "batch shard: negative point count");
+    // longest processing time first: grids by points, largest first (ties by
+    // index), each to the rank with the least load so far (ties to the lower
+    // rank).  Every rank computes the same assignment without communication.
+    std::vector<int32_t> order((size_t)n);
+    for (int32_t q = 0; q < n; ++q) order[(size_t)q] = q;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return points[a] > points[b]; });
+    std::vector<int64_t> loads((size_t)world, 0);
+    std::vector<int32_t> owner((size_t)n);
+    for (int32_t q : order) {
+        int32_t r = (int32_t)(std::min_element(loads.begin(), loads.end()) - loads.begin());
+        owner[(size_t)q] = r;
+        loads[(size_t)r] += points[q];
+    }
+    int32_t m = 0;
+    for (int32_t q = 0; q < n; ++q)
+        if (owner[(size_t)q] == rank) out[m++] = q;       // ascending grid index
+    *count = m;
+    if (load) *load = loads[(size_t)rank];
+    return KL_OK;
+}
+
 kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_grid *grids,
                             const kl_fields *fields, void *stream)
 {

@@ -114,6 +114,8 @@ SIGNATURES = {
     "kl_def_tune": ([_P, _P, _S, _S, _S], ctypes.c_int),
     "kl_smagorinsky": ([_P, _I32, ctypes.POINTER(Grid), _D, _P, _P, _P, _P, _I32, _P],
                        ctypes.c_int),
+    "kl_batch_shard": ([_I32, ctypes.POINTER(_I64), _I32, _I32, ctypes.POINTER(_I32),
+                        ctypes.POINTER(_I32), ctypes.POINTER(_I64)], ctypes.c_int),
     "kl_version": ([], _S),
 }
 
@@ -276,6 +278,17 @@ def kl_compile_only(op: Op, config: str, zbc: int = 0, zuni: int = 1) -> str:
 def kl_smagorinsky(ctx, dtype, grid: Grid, cs, u, v, w, nu, fill_ghosts=True, stream=None) -> None:
     check(load().kl_smagorinsky(ctx, dtype, ctypes.byref(grid), cs, u, v, w, nu,
                                 1 if fill_ghosts else 0, stream))
+
+
+def kl_batch_shard(points, world: int, rank: int):
+    """(indices of the grids `rank` owns, their total points) under LPT bin packing."""
+    n = len(points)
+    pts = (ctypes.c_int64 * max(1, n))(*points)
+    out = (ctypes.c_int32 * max(1, n))()
+    count, load_ = ctypes.c_int32(), ctypes.c_int64()
+    check(load().kl_batch_shard(n, pts, world, rank, out, ctypes.byref(count),
+                                ctypes.byref(load_)))
+    return list(out[:count.value]), load_.value
 
 
 def kl_set_cache_dir(ctx, path) -> None:
