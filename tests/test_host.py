@@ -286,3 +286,20 @@ def test_cache_argument_errors(tmp_path):
     with pytest.raises(kl.KLError) as e:
         kl.kl_set_cache_dir(None, str(tmp_path))
     assert e.value.status == -1
+
+
+def test_c_abi_from_plain_c(tmp_path):
+    """The boundary is a C ABI: a C program built with gcc against include/kl.h
+    and linked to libkl.so calls the host-only entry points."""
+    import subprocess
+    from paper_2303_12374_gb300 import build as kbuild
+    lib = kbuild.build()
+    exe = str(tmp_path / "abi_host")
+    subprocess.check_call(["gcc", "-std=c11", "-O1", "-Wall", "-Werror",
+                           "-I", os.path.join(ROOT, "include"),
+                           os.path.join(ROOT, "tests", "c", "abi_host.c"), "-o", exe,
+                           "-L", os.path.dirname(lib), "-lkl", "-lm",
+                           "-Wl,-rpath," + os.path.dirname(lib)])
+    r = subprocess.run([exe, str(tmp_path)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.strip().endswith("all ok")
