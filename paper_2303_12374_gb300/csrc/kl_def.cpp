@@ -649,6 +649,13 @@ static kl_status def_launch_values(kl_ctx *ctx, kl_def *d, const Values &v, cons
     return KL_OK;
 }
 
+// a problem extent as the 32-bit size of a wisdom record (nearest-size
+// selection only needs the magnitude)
+static int wisdom_extent(int64_t x)
+{
+    return (int)std::max<int64_t>(0, std::min<int64_t>(x, 2147483647));
+}
+
 static std::string def_wisdom_path(const kl_ctx *ctx, const kl_def &d)
 {
     return (ctx->wisdom_dir.empty() ? std::string(".") : ctx->wisdom_dir) + "/" + d.name + ".wisdom";
@@ -999,8 +1006,9 @@ kl_status kl_def_launch(kl_ctx *ctx, kl_def *d, const int64_t problem[3], int32_
         std::string err, text = "default";
         int rule = 5;
         if (wisdom_read(def_wisdom_path(ctx, *d), &recs, &err) && !recs.empty())
-            rule = wisdom_select(recs, ctx->name, ctx->cc_major, ctx->cc_minor, 0, (int)problem[0],
-                                 (int)problem[1], (int)problem[2], &text);
+            rule = wisdom_select(recs, ctx->name, ctx->cc_major, ctx->cc_minor, 0,
+                                 wisdom_extent(problem[0]), wisdom_extent(problem[1]),
+                                 wisdom_extent(problem[2]), &text);
         Values v;
         int64_t geo[7];
         if (!parse_config(*d, text, &v, &err) || !restrictions_hold(*d, v, &err) ||
@@ -1360,9 +1368,9 @@ kl_status kl_def_tune(kl_ctx *ctx, kl_def *d, const char *capture_path, const ch
     rec.cc_major = ctx->cc_major;
     rec.cc_minor = ctx->cc_minor;
     rec.zbc = 0;
-    rec.nx = (int)C.problem[0];
-    rec.ny = (int)C.problem[1];
-    rec.nz = (int)C.problem[2];
+    rec.nx = wisdom_extent(C.problem[0]);
+    rec.ny = wisdom_extent(C.problem[1]);
+    rec.nz = wisdom_extent(C.problem[2]);
     rec.config = config_text(*d, best);
     rec.time_us = best_us;
     char buf[64];
