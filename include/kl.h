@@ -279,8 +279,8 @@ kl_status kl_diag_noalloc(int32_t dtype, const kl_grid *grid, const void *t, con
  * averaged.  u, v, w (device, layout grid, type dtype) are read with every
  * ghost cell filled as kl_fill_ghosts fills them (one ghost cell is enough).
  * The fill of kl_step and kl_fill_ghosts_op may leave the x ghosts of
- * interior rows unfilled (a zpack configuration wraps x itself), so call
- * kl_fill_ghosts before this after those.  nu (device, same layout and type, not
+ * interior rows unfilled (a zpack configuration wraps x itself), so a caller
+ * coming from those calls kl_fill_ghosts first.  nu (device, same layout and type, not
  * aliasing them) gets the interior, and with fill_ghosts != 0 also its ghost
  * cells by the rules of kl_fill_ghosts (even mirror at walls).  Arithmetic
  * in f64 for f64 storage, else f32.  KL_ERR_INVALID_ARG for NULL or
