@@ -150,3 +150,26 @@ def test_nvrtc_compiles_definitions():
     with pytest.raises(kl.KLError) as e:
         bad.compile_only()
     assert e.value.status == -3
+
+
+def test_argument_marshalling():
+    """kl_arg records from (kind, value) pairs: scalars point at their value
+    with its size, buffers carry pointer, byte size, direction and dtype."""
+    import ctypes
+    import torch
+    a = torch.zeros(10, dtype=torch.float32)
+    b = torch.zeros(3, dtype=torch.float64)
+    c = torch.zeros(6, dtype=torch.int32)
+    d = torch.zeros(4, dtype=torch.bfloat16)
+    e = torch.zeros(5, dtype=torch.int8)
+    arr, keep = kl.make_args([("in", a), ("out", b), ("inout", c), ("in", d), ("out", e),
+                              ("i32", -7), ("f64", 2.5), ("i64", 1 << 40)])
+    got = [(x.ptr, x.bytes, x.kind, x.dtype) for x in arr]
+    assert got[:5] == [(a.data_ptr(), 40, 1, 1), (b.data_ptr(), 24, 2, 0), (c.data_ptr(), 24, 3, 4),
+                       (d.data_ptr(), 8, 1, 2), (e.data_ptr(), 5, 2, 5)]
+    assert [x[1:] for x in got[5:]] == [(4, 0, 0), (8, 0, 0), (8, 0, 0)]
+    assert ctypes.c_int32.from_address(got[5][0]).value == -7
+    assert ctypes.c_double.from_address(got[6][0]).value == 2.5
+    assert ctypes.c_int64.from_address(got[7][0]).value == 1 << 40
+    with pytest.raises(ValueError):
+        kl.make_args([("half", 1.0)])
