@@ -118,3 +118,24 @@ def test_second_order_convergence(oracle_mod):
         errs.append(np.abs(s2 - _exact_s2(X, Y, Z)).max())
     rates = [np.log2(errs[q] / errs[q + 1]) for q in range(2)]
     assert all(r > 1.8 for r in rates), (errs, rates)
+
+
+def test_wall_mirror_symmetry(oracle_mod):
+    """Free-slip walls: reflecting the flow about the mid-plane (u, v even,
+    w odd, faces k <-> nz - k) reflects nu level by level, so the bottom and
+    top wall ghosts are handled alike."""
+    rng = np.random.default_rng(9)
+    nz, ny, nx = 7, 6, 8
+    u, v = rng.standard_normal((nz, ny, nx)), rng.standard_normal((nz, ny, nx))
+    w = rng.standard_normal((nz, ny, nx))
+    w[0] = 0.0                                    # the bottom wall face
+    um, vm = u[::-1].copy(), v[::-1].copy()
+    wm = np.zeros_like(w)
+    wm[1:] = -w[1:][::-1]                         # face k of the mirror = -face nz-k
+    zh = np.linspace(0.0, 1.0, nz + 1)
+    kw = dict(g=1, walls=True, dx=1 / nx, dy=1 / ny, zh=zh, cs=0.15)
+    a = oracle_mod.smagorinsky(u, v, w, **kw)
+    b = oracle_mod.smagorinsky(um, vm, wm, **kw)
+    assert np.allclose(b, a[::-1], rtol=1e-13, atol=0)
+    # and the mirror is not trivially equal to the original
+    assert not np.allclose(a, a[::-1])
