@@ -139,3 +139,89 @@ def test_wall_mirror_symmetry(oracle_mod):
     assert np.allclose(b, a[::-1], rtol=1e-13, atol=0)
     # and the mirror is not trivially equal to the original
     assert not np.allclose(a, a[::-1])
+
+
+# ------------------------------------------------- planted mistakes
+# Each mutant plants one plausible mistake in a copy of oracle.c (built on
+# the CPU); a fast subset of the pins above must reject it, and the
+# unmodified source must pass the same subset.
+
+SMAG_MUTANTS = [
+    ("half factor", "return 0.5 * ((DU(i, j, k) - DU(i, j - 1, k)) / D->G->dy +",
+     "return 1.0 * ((DU(i, j, k) - DU(i, j - 1, k)) / D->G->dy +"),
+    ("edge mean", "mxy += e1 * e1 / 4.0;", "mxy += e1 * e1 / 2.0;"),
+    ("edge level", "double e2 = exz(D, i + a, j, k + b);", "double e2 = exz(D, i + a, j, k + b - 1);"),
+    ("szz metric", "double szz = (DW(i, j, k + 1) - DW(i, j, k)) / dz[k + g];",
+     "double szz = (DW(i, j, k + 1) - DW(i, j, k)) / dzh[k + g];"),
+    ("delta metric", "double delta = cbrt(dx * dy * dz[k + g]);",
+     "double delta = cbrt(dx * dy * dzh[k + g]);"),
+    ("normal weight", "double s2 = 2.0 * (sxx * sxx + syy * syy + szz * szz)",
+     "double s2 = 1.0 * (sxx * sxx + syy * syy + szz * szz)"),
+    ("cross index", "return 0.5 * ((DV(i, j, k) - DV(i, j, k - 1)) / D->G->dzh[k + D->G->g] +\n"
+                    "                  (DW(i, j, k) - DW(i, j - 1, k)) / D->G->dy);",
+     "return 0.5 * ((DV(i, j, k) - DV(i, j, k - 1)) / D->G->dzh[k + D->G->g] +\n"
+     "                  (DW(i, j, k) - DW(i - 1, j, k)) / D->G->dy);"),
+]
+
+
+def _smag_pins_pass(mod) -> bool:
+    try:
+        for seed in range(2):
+            test_linear_field_is_exact(mod, seed)
+        test_rotation_has_no_strain(mod)
+        test_wall_mirror_symmetry(mod)
+        errs = []
+        for n in (16, 32):
+            h = 1.0 / n
+            xc = (np.arange(n) + 0.5) * h
+            u = np.sin(2 * np.pi * xc)[None, :, None] * np.cos(2 * np.pi * xc)[:, None, None] \
+                + np.zeros((1, 1, n))
+            v = np.broadcast_to(np.sin(2 * np.pi * xc)[None, None, :], (n, n, n)).copy()
+            w = np.broadcast_to(0.5 * np.cos(2 * np.pi * xc)[None, None, :], (n, n, n)).copy()
+            nu = mod.smagorinsky(u, v, w, g=1, walls=False, dx=h, dy=h, zh=np.linspace(0, 1, n + 1),
+                                 cs=0.2)
+            Z, Y, X = np.meshgrid(xc, xc, xc, indexing="ij")
+            errs.append(np.abs(nu ** 2 / (0.2 * h) ** 4 - _exact_s2(X, Y, Z)).max())
+        return np.log2(errs[0] / errs[1]) > 1.7
+    except AssertionError:
+        return False
+
+
+@pytest.fixture()
+def swap_lib(oracle_mod):
+    saved = oracle_mod._lib
+    yield
+    oracle_mod._lib = saved
+
+
+def _use_source(oracle_mod, tmp_path, text):
+    import ctypes
+    import subprocess
+    c, so = tmp_path / "m.c", tmp_path / "m.so"
+    c.write_text(text)
+    subprocess.check_call(["gcc", "-O1", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(so),
+                           str(c), "-lm"])
+    lib = ctypes.CDLL(str(so))
+    ref = oracle_mod._load()
+    for name in ("or_zprofile", "or_fill_ghosts", "or_tendency", "or_diag", "or_smagorinsky"):
+        getattr(lib, name).argtypes = getattr(ref, name).argtypes
+    oracle_mod._lib = lib
+
+
+def _source(oracle_mod):
+    import os
+    return open(os.path.join(os.path.dirname(oracle_mod.__file__), "oracle.c")).read()
+
+
+def test_unmodified_source_passes_the_subset(oracle_mod, tmp_path, swap_lib):
+    _use_source(oracle_mod, tmp_path, _source(oracle_mod))
+    assert _smag_pins_pass(oracle_mod)
+
+
+@pytest.mark.parametrize("name,old,new", SMAG_MUTANTS, ids=[m[0] for m in SMAG_MUTANTS])
+def test_planted_mistake_is_caught(oracle_mod, tmp_path, swap_lib, name, old, new):
+    text = _source(oracle_mod)
+    assert text.count(old) == 1, name
+    _use_source(oracle_mod, tmp_path, text.replace(old, new))
+    with np.errstate(all="ignore"):
+        assert not _smag_pins_pass(oracle_mod), f"mutant '{name}' passed every pin"
