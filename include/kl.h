@@ -50,8 +50,8 @@ typedef enum { KL_F64 = 0, KL_F32 = 1, KL_BF16 = 2, KL_F16 = 3 } kl_dtype;
 
 /*
  * What to compute.  adv: 0 none, 2 centred 2nd-order, 5 upwind-biased
- * 5th-order interpolation in flux-form momentum advection ("second order
- * advection scheme with fifth order interpolation", Sec. 5.2).  diff: 0 none,
+ * 5th-order interpolation in flux-form momentum advection (the 2nd-order
+ * scheme with 5th-order face values of Sec. 5.2).  diff: 0 none,
  * 1 constant-nu Laplacian, 2 variable-nu stress divergence (the Smagorinsky
  * diffusion of Sec. 5.2 with a given nu field).  dtype: storage type of every
  * field; f64 computes in f64, the others in f32.  accumulate: 0 writes

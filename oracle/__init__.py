@@ -3,7 +3,10 @@
 
 Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may import
 this package.  The product path (paper_2303_12374_gb300) never does; the two
-share no code.  `build()` compiles oracle.c with gcc into oracle/_build/.
+share no code.  `build()` compiles oracle.c with gcc into oracle/_build/:
+liboracle.so, the serial build every test pins, and liboracle_omp.so, the same
+source with -fopenmp (the tendency loop split over the host cores), used only
+to time the oracle on all cores (`tendencies(..., threads=n)`).
 
 Arrays are numpy float64 in (nz, ny, nx) order (x fastest), interior only,
 unless a name says "padded".
@@ -19,19 +22,62 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "_build", "liboracle.so")
+_SO_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
 _lib = None
+_lib_omp = None
+
+
+def _compile(out: str, extra) -> None:
+    src = os.path.join(_HERE, "oracle.c")
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    tmp = out + f".{os.getpid()}.tmp"
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                           "-shared", *extra, "-o", tmp, src, "-lm"])
+    os.replace(tmp, out)
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c (plain C, FP64, no FMA contraction) into a shared library."""
+    """Compile oracle.c (plain C, FP64, no FMA contraction) into a shared
+    library, and its OpenMP timing build when gcc supports -fopenmp."""
     src = os.path.join(_HERE, "oracle.c")
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
-        os.makedirs(os.path.dirname(_SO), exist_ok=True)
-        tmp = _SO + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                               "-shared", "-o", tmp, src, "-lm"])
-        os.replace(tmp, _SO)
+    for out, extra in ((_SO, []), (_SO_OMP, ["-fopenmp"])):
+        if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
+            try:
+                _compile(out, extra)
+            except (subprocess.CalledProcessError, OSError):
+                if out == _SO:
+                    raise
     return _SO
+
+
+def _declare(lib):
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.or_zprofile.argtypes = [ctypes.c_int] * 3 + [dp, dp, dp]
+    lib.or_fill_ghosts.argtypes = [ctypes.c_int] * 6 + [dp]
+    lib.or_tendency.argtypes = ([ctypes.c_int] * 5 + [ctypes.c_double] * 2 + [dp, dp]
+                                + [ctypes.c_int] * 2 + [ctypes.c_double] + [dp] * 4
+                                + [ctypes.c_int] * 2 + [dp] * 3)
+    lib.or_diag.argtypes = [ctypes.c_size_t, dp, dp, dp, dp]
+    lib.or_smagorinsky.argtypes = ([ctypes.c_int] * 4 + [ctypes.c_double] * 2 + [dp, dp]
+                                   + [ctypes.c_double] + [dp] * 3 + [ctypes.c_int] * 2 + [dp])
+    lib.or_set_threads.argtypes = [ctypes.c_int]
+    lib.or_set_threads.restype = ctypes.c_int
+    return lib
+
+
+def _load_omp():
+    """The OpenMP timing build, or None where it could not be built."""
+    global _lib_omp
+    if _lib_omp is None:
+        build()
+        if not os.path.exists(_SO_OMP):
+            return None
+        _lib_omp = _declare(ctypes.CDLL(_SO_OMP))
+    return _lib_omp
+
+
+def omp_available() -> bool:
+    return _load_omp() is not None
 
 
 def _load():
@@ -48,6 +94,8 @@ def _load():
         lib.or_diag.argtypes = [ctypes.c_size_t, dp, dp, dp, dp]
         lib.or_smagorinsky.argtypes = ([ctypes.c_int] * 4 + [ctypes.c_double] * 2 + [dp, dp]
                                        + [ctypes.c_double] + [dp] * 3 + [ctypes.c_int] * 2 + [dp])
+        lib.or_set_threads.argtypes = [ctypes.c_int]
+        lib.or_set_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -80,13 +128,22 @@ def pad(a: np.ndarray, g: int, walls: bool, odd: bool) -> np.ndarray:
 
 
 def tendencies(u, v, w, *, adv: int, diff: int, g: int, walls: bool, dx: float,
-               dy: float, zh: np.ndarray, nu: float = 0.0, nu_field=None, levels=None):
+               dy: float, zh: np.ndarray, nu: float = 0.0, nu_field=None, levels=None,
+               threads: int = 1):
     """(ut, vt, wt) on the interior; inputs are interior fields (nz, ny, nx).
 
     levels=(k0, k1) computes only interior levels k0 <= k < k1 (outputs of
-    shape (k1-k0, ny, nx)); the default is every level.
+    shape (k1-k0, ny, nx)); the default is every level.  threads > 1 runs the
+    tendency loop of the OpenMP timing build on that many threads (same
+    results); it raises if that build is unavailable.
     """
-    lib = _load()
+    if threads > 1:
+        lib = _load_omp()
+        if lib is None:
+            raise RuntimeError("the OpenMP build of the oracle is unavailable")
+        lib.or_set_threads(threads)
+    else:
+        lib = _load()
     nz, ny, nx = u.shape
     u, v, w = (np.ascontiguousarray(x, dtype=np.float64) for x in (u, v, w))
     up, vp, wp = pad(u, g, walls, False), pad(v, g, walls, False), pad(w, g, walls, True)

@@ -6,10 +6,11 @@
  * baseline leg.  It shares no code, header or table with the CUDA path.
  *
  * What it computes.  The paper (Sec. 5.2) tunes two MicroHH kernels: advec_u,
- * "part of the second order advection scheme with fifth order interpolation",
- * and diff_uvw, "part of the second order Smagorinsky diffusion".  It prints no
- * formulas, so this file writes out the standard staggered-grid (Arakawa C)
- * flux-form finite differences those names denote:
+ * the momentum-advection kernel whose face values use 5th-order
+ * interpolation inside a 2nd-order scheme, and diff_uvw, the kernel of the
+ * 2nd-order Smagorinsky diffusion.  It prints no formulas, so this file
+ * writes out the standard staggered-grid (Arakawa C) flux-form finite
+ * differences those names denote:
  *
  *   advection   tendency = -div(u_j u_i), face fluxes F = U * a_face, with the
  *               advecting velocity U averaged to the face (2nd order) and the
@@ -37,6 +38,9 @@
  * needs it.  Built with -ffp-contract=off so no fused multiply-add is formed.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -325,6 +329,10 @@ void or_tendency(int nx, int ny, int nz, int g, int zbc, double dx, double dy,
     actx A = {&G, u, v, w, adv};
     dctx D = {&G, u, v, w, nuf};
     const actx *C = &A;
+    /* Only the timing build (-fopenmp, liboracle_omp) splits the rows among
+     * threads; every point is computed by the same code in either build, so
+     * the results are identical. */
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = k0; k < k1; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -458,4 +466,16 @@ void or_diag(size_t n, const double *t, const double *r, const double *wgt, doub
     out[3] = n ? sqrt(r2 / (double)n) : 0.0;
     out[4] = s;
     out[5] = sw;
+}
+
+/* Threads of the OpenMP timing build (the serial build has one). */
+int or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
