@@ -1,19 +1,23 @@
 """Throughput of the stencil tendency path on GB300.
 
-One step = ghost fill + fused u, v, w tendency (kl_step = kl_fill_ghosts_op
-followed by kl_launch; timed as those two calls so the kernel has its own events)
-over one grid: 256^3 interior, 3 ghost cells, periodic x and y, free-slip
-walls in z, 5th-order upwind-biased flux-form advection + constant-nu
-diffusion (nu = 1e-3), f32 storage and arithmetic, seeded synthetic Fourier +
-noise fields.  The configuration comes from the committed wisdom files
-(tuned); the untuned default of Table 2 and the f64 build are timed beside it.
+One step = kl_step (the ghost fill the selected configuration reads, then the
+fused u, v, w tendency kernel; timed as kl_fill_ghosts_op + kl_launch so that
+the kernel has its own events) over one grid: 512 x 512 x 256 interior points
+(67.1 M), 3 ghost cells, periodic x and y, free-slip walls in z, 5th-order
+upwind-biased flux-form advection + constant-nu diffusion (nu = 1e-3), f32
+storage and arithmetic, seeded synthetic Fourier + noise fields.  It is the
+largest single grid of the workloads (the 1024 x 1024 x 64 LES grid has the
+same point count; it is reported in the extras).  The configuration comes from
+the committed wisdom files (tuned); the untuned default of Table 2, the other
+storage types, the other workloads and the batch are timed beside it.
 
 Prints ONE JSON line.  Under torchrun (N > 1) every rank runs its own
 replica of the grid (weak scaling, no collective on the data path); the time
 is the maximum over ranks.
 
---impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload (the reference arm: there is no reference implementation to run).
+--impl reference times the FP64 CPU oracle on the host cores, on bounded
+samples of z levels of the same workload (the reference arm: there is no
+reference implementation to run).
 """
 
 from __future__ import annotations
@@ -35,11 +39,21 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Gpts/s & HBM GB/s vs ~8 TB/s: tuned vs default, FP64/FP32/16-bit-store"
-WORKLOAD = "walls256_adv5_diff"
-NX = NY = NZ = 256
+WORKLOAD = "walls512x512x256_precision"
 G = 3
 NU = 1e-3
 REF_SECONDS = 120.0      # reference arm: CPU time of warm-up + timed samples
+# FP32 (or FP64) operations per interior point of the fused tendency with each
+# face flux formed once, an FMA counted as one: 9 faces x 14 (advecting
+# velocity 1, the upwind differences and sums 5, I6 3, D6 2, U*I6 + |U|*D6 2,
+# folded diffusion 1) + 3 tendencies x 6 (3 differences, 1 product, 2 FMAs)
+OPS_PER_POINT = 144
+
+
+def extents(workload=None):
+    from paper_2303_12374_gb300 import synth
+    spec = synth.WORKLOADS[workload or WORKLOAD]
+    return spec["nx"], spec["ny"], spec["nz"]
 
 
 def kernel_source_hash() -> str:
@@ -51,12 +65,12 @@ def kernel_source_hash() -> str:
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="kl", choices=["kl", "reference"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64", "bf16", "f16"])
     ap.add_argument("--no-extras", action="store_true", help="skip default/f64 side timings")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     return ap.parse_args()
 
 
@@ -151,13 +165,19 @@ class Clocks:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def setup(dtype_name, device):
+def workload_fields(workload=None):
+    from paper_2303_12374_gb300 import synth
+    spec = synth.WORKLOADS[workload or WORKLOAD]
+    nx, ny, nz = extents(workload)
+    return synth.velocity_fields(nx, ny, nz, seed=synth.seed_of(spec["index"]), walls=True)
+
+
+def setup(dtype_name, device, f=None):
     import torch
-    from paper_2303_12374_gb300 import kl, synth
     from paper_2303_12374_gb300.problem import Problem
-    spec = synth.WORKLOADS[WORKLOAD]
-    f = synth.velocity_fields(NX, NY, NZ, seed=synth.seed_of(spec["index"]), walls=True)
-    p = Problem(NX, NY, NZ, g=G, dtype=dtype_name, walls=True, dz=1.0 / NZ, nu=NU,
+    nx, ny, nz = extents()
+    f = f if f is not None else workload_fields()
+    p = Problem(nx, ny, nz, g=G, dtype=dtype_name, walls=True, dz=1.0 / nz, nu=NU,
                 device=device)
     ins = [p.upload(f[k]) for k in ("u", "v", "w")]
     outs = [p.empty() for _ in range(3)]
@@ -209,38 +229,55 @@ class OracleSample:
 
     Levels [k0, k0 + L) with 3 <= k0 and k0 + L <= nz - 3 are computed from a
     slab of the fields with the stencil's 3-level reach on each side, so only
-    the slab is padded; the result is the full grid's on those levels."""
+    the slab is padded; the result is the full grid's on those levels.
+    threads > 1 runs the oracle's OpenMP timing build (same results)."""
 
-    def __init__(self):
+    def __init__(self, f=None):
         import oracle
         from paper_2303_12374_gb300 import synth
         oracle.build()
         self.oracle, self.synth = oracle, synth
-        spec = synth.WORKLOADS[WORKLOAD]
-        self.f = synth.velocity_fields(NX, NY, NZ, seed=synth.seed_of(spec["index"]), walls=True)
+        self.nx, self.ny, self.nz = extents()
+        self.f = f if f is not None else workload_fields()
 
-    def run(self, k0, nlev):
+    def run(self, k0, nlev, threads=1):
         """Seconds the oracle takes for interior levels [k0, k0 + nlev)."""
-        assert G <= k0 and k0 + nlev <= NZ - G
+        assert G <= k0 and k0 + nlev <= self.nz - G
         lo, hi = k0 - G, k0 + nlev + G
         sl = {k: np.ascontiguousarray(self.f[k][lo:hi]) for k in ("u", "v", "w")}
-        zh = self.synth.zfaces(hi - lo, (hi - lo) / NZ)
+        zh = self.synth.zfaces(hi - lo, (hi - lo) / self.nz)
         t = time.perf_counter()
         self.oracle.tendencies(sl["u"], sl["v"], sl["w"], adv=5, diff=1, g=G, walls=False,
-                               dx=1 / NX, dy=1 / NY, zh=zh, nu=NU, levels=(G, G + nlev))
+                               dx=1 / self.nx, dy=1 / self.ny, zh=zh, nu=NU,
+                               levels=(G, G + nlev), threads=threads)
         return time.perf_counter() - t
 
 
+def host_threads() -> int:
+    """Host cores the oracle's OpenMP build runs on (1 without that build)."""
+    import oracle
+    return (os.cpu_count() or 1) if oracle.omp_available() else 1
+
+
 def cpu_baseline(seconds_target, sampler=None):
-    """The oracle on a bounded sample (about seconds_target) of the workload."""
+    """The oracle on bounded samples (about seconds_target each) of the
+    workload: single-threaded, and on every host core (OpenMP build)."""
     sampler = sampler or OracleSample()
-    per_level = sampler.run(G, 2) / 2
-    levels = max(2, min(NZ - 2 * G, int(seconds_target / max(per_level, 1e-6))))
-    dt = sampler.run(G, levels)
-    pts = NX * NY * levels
-    return {"value": pts / dt / 1e9, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
-            "sample": f"levels {G}..{G + levels - 1} of the 256^3 grid ({pts} points, FP64, "
-                      f"single thread, {dt:.1f} s incl. padding of the slab)"}, dt
+    nx, ny, nz = sampler.nx, sampler.ny, sampler.nz
+    out = {}
+    for label, threads in (("single_thread", 1), ("all_cores", host_threads())):
+        per_level = sampler.run(G, 2, threads) / 2
+        levels = max(2, min(nz - 2 * G, int(seconds_target / max(per_level, 1e-6))))
+        dt = sampler.run(G, levels, threads)
+        pts = nx * ny * levels
+        out[label] = {"value": pts / dt / 1e9, "unit": "Gpts/s", "cores": threads,
+                      "sample": f"levels {G}..{G + levels - 1} of the {nx}x{ny}x{nz} grid "
+                                f"({pts} points, FP64, {threads} thread(s), {dt:.1f} s incl. "
+                                f"padding of the slab)"}
+    best = out["all_cores"]
+    return {"value": best["value"], "unit": "Gpts/s", "cores": best["cores"], "kind": "oracle",
+            "sample": best["sample"], "single_thread": out["single_thread"],
+            "host_cpus": os.cpu_count()}, None
 
 
 def e2e_run(ctx, p, f, op, device, steps, overlap=True):
@@ -304,42 +341,71 @@ def e2e_run(ctx, p, f, op, device, steps, overlap=True):
     return a.elapsed_time(b) / steps, 3 * p.nx * p.ny * p.nz * es
 
 
-def precision_sweep(ctx, f, device, stream, reps):
-    """Tuned and default kernel time per storage type on the same 256^3 fields."""
+def alu_peaks_live():
+    """FP32 (packed and scalar) and FP64 FMA rates measured now (alu_peaks)."""
+    from paper_2303_12374_gb300 import alu_peaks
+    out = {}
+    for kind in ("f32x2", "f64"):
+        r = alu_peaks.measure(kind, target_ms=20.0, reps=5)
+        out[kind] = {"tflops": r["tflops"], "fma_per_sm_per_clk": r.get("fma_per_sm_per_clk"),
+                     "sm_mhz": r["clocks"]["sm_mhz"]}
+    return out
+
+
+def roof(us, pts, nbytes, peak_gbs, op_peak):
+    """HBM and ALU roofline fractions of one kernel time.  op_peak: the FMA
+    pipe's measured rate in operations per second (an FMA is one operation)."""
+    gbs = nbytes / us / 1e3
+    ops = OPS_PER_POINT * pts / (us * 1e-6)
+    return {"hbm_gbs": gbs, "hbm_frac": gbs / peak_gbs,
+            "alu_tops": ops / 1e12, "alu_frac": ops / op_peak if op_peak else None}
+
+
+def precision_sweep(ctx, f, device, stream, reps, peak_gbs, op_peaks):
+    """Tuned and default kernel time per storage type on the bench grid, each
+    against both roofs: HBM at its bytes per point, and the FMA pipe of its
+    arithmetic (FP64 for f64 storage, FP32 otherwise)."""
     import torch
     from paper_2303_12374_gb300 import kl
     from paper_2303_12374_gb300.problem import Problem
+    nx, ny, nz = extents()
+    pts = nx * ny * nz
     out = {}
     for name in ("f64", "f32", "bf16", "f16"):
-        p = Problem(NX, NY, NZ, g=G, dtype=name, walls=True, dz=1.0 / NZ, nu=NU, device=device)
+        p = Problem(nx, ny, nz, g=G, dtype=name, walls=True, dz=1.0 / nz, nu=NU, device=device)
         ins = [p.upload(f[k]) for k in ("u", "v", "w")]
         outs = [p.empty() for _ in range(3)]
         op = kl.Op(5, 1, p.dtype, 0)
         es = {0: 8, 1: 4, 2: 2, 3: 2}[p.dtype]
         row = {"bytes_per_point": 6 * es}
-        n = reps if name != "f64" else max(3, reps // 20)
+        n = reps if name != "f64" else 3
+        op_peak = op_peaks.get("f64" if name == "f64" else "f32")
         for label, cfg in (("tuned", None), ("default", "default")):
             _, k_ms = time_steps(ctx, p, ins, outs, op, cfg, n, 2, stream)
-            row[label] = {"kernel_us": k_ms * 1e3, "gpts": NX * NY * NZ / (k_ms * 1e-3) / 1e9,
-                          "hbm_gbs": 6 * es * NX * NY * NZ / (k_ms * 1e-3) / 1e9}
+            us = k_ms * 1e3
+            row[label] = {"kernel_us": us, "gpts": pts / us / 1e3}
+            row[label].update(roof(us, pts, 6 * es * pts, peak_gbs, op_peak))
             if cfg is None:
                 row[label]["config"] = json.loads(kl.kl_stats(ctx))["last_config"]
         row["speedup"] = row["default"]["kernel_us"] / row["tuned"]["kernel_us"]
+        row["bound"] = ("alu" if row["tuned"]["alu_frac"] and
+                        row["tuned"]["alu_frac"] > row["tuned"]["hbm_frac"] else "hbm")
         out[name] = row
         del ins, outs
         torch.cuda.empty_cache()
     return out
 
 
-def workload_sweep(ctx, device, stream, reps):
+def workload_sweep(ctx, device, stream, reps, peak_gbs, op_peaks):
     """Kernel time, tuned (wisdom) vs default, on the other seeded workloads:
-    64^3 periodic 2nd order f64, 512x512x256 walls f32, 1024x1024x64 stretched
-    with variable nu f32 (ghosts filled once, then kernel launches only)."""
+    256^3 walls f32 (the grid of the paper's 256^3 tuning), 64^3 periodic 2nd
+    order f64, 1024x1024x64 stretched with variable nu f32 (ghosts filled
+    once, then kernel launches only)."""
     import torch
     from paper_2303_12374_gb300 import kl, synth
     from paper_2303_12374_gb300.tune_cli import build_problem
     out = {}
-    for wl, dt in (("periodic64_adv2_f64", "f64"), ("walls512x512x256_precision", "f32"),
+    for wl, dt in (("walls256_adv5_diff", "f32"), ("periodic64_adv2_f64", "f64"),
                    ("les1024x1024x64_stretched_varnu", "f32")):
         p, op, bufs, outs, fl = build_problem(wl, dt)
         spec = synth.WORKLOADS[wl]
@@ -370,8 +436,8 @@ def workload_sweep(ctx, device, stream, reps):
                 b.record(stream)
                 torch.cuda.synchronize()
                 us = a.elapsed_time(b) / n * 1e3
-                row[label] = {"kernel_us": us, "gpts": pts / us / 1e3,
-                              "hbm_gbs": nbytes / us / 1e3}
+                row[label] = {"kernel_us": us, "gpts": pts / us / 1e3, "hbm_gbs": nbytes / us / 1e3,
+                              "hbm_frac": nbytes / us / 1e3 / peak_gbs}
                 if cfg is None:
                     row[label]["config"] = json.loads(kl.kl_stats(ctx))["last_config"]
             row["speedup"] = row["default"]["kernel_us"] / row["tuned"]["kernel_us"]
@@ -450,8 +516,10 @@ def les_step(ctx, stream, peak_gbs, reps=20, cs=0.1):
     return res
 
 
-def batched_run(ctx, device, stream, reps=20):
-    """64 uneven grids: one batched call (tuned size classes) vs 64 default launches."""
+def batched_run(ctx, device, stream, peak_gbs, reps=20):
+    """64 uneven grids: one batched call (tuned size classes, one CUDA graph)
+    vs 64 separate launches with the same wisdom selection (tuned) and vs 64
+    separate default launches."""
     import torch
     from paper_2303_12374_gb300 import kl, synth
     from paper_2303_12374_gb300.problem import Problem
@@ -482,8 +550,13 @@ def batched_run(ctx, device, stream, reps=20):
             for p, bufs, outs, fl in probs:
                 kl.kl_launch_with_config(ctx, op, "default", p.grid, fl, sp)
 
+        def separate_tuned():
+            for p, bufs, outs, fl in probs:
+                kl.kl_launch(ctx, op, p.grid, fl, sp)
+
         res = {}
-        for label, fn in (("batched_tuned", batched), ("separate_default", separate)):
+        for label, fn in (("batched_tuned", batched), ("separate_tuned", separate_tuned),
+                          ("separate_default", separate)):
             for _ in range(3):
                 fn()
             torch.cuda.synchronize()
@@ -494,11 +567,13 @@ def batched_run(ctx, device, stream, reps=20):
             b.record(stream)
             torch.cuda.synchronize()
             ms = a.elapsed_time(b) / reps
-            res[label] = {"ms": ms, "gpts": pts / (ms * 1e-3) / 1e9,
-                          "hbm_gbs": 24 * pts / (ms * 1e-3) / 1e9}
+            gbs = 24 * pts / (ms * 1e-3) / 1e9
+            res[label] = {"ms": ms, "gpts": pts / (ms * 1e-3) / 1e9, "hbm_gbs": gbs,
+                          "hbm_frac": gbs / peak_gbs}
     res["grids"] = len(sizes)
     res["points"] = pts
     res["speedup"] = res["separate_default"]["ms"] / res["batched_tuned"]["ms"]
+    res["speedup_vs_separate_tuned"] = res["separate_tuned"]["ms"] / res["batched_tuned"]["ms"]
     return res
 
 
@@ -554,37 +629,50 @@ def launch_overhead(local, wisdom, device, calls=1000):
 
 
 def run_reference(args):
-    """The reference arm: the oracle on the host cores, each step a sample of
-    z levels of the workload sized so that warm-up plus timed steps take about
-    REF_SECONDS (one level at least); rank 0 only."""
+    """The reference arm: the oracle on the host cores (its OpenMP timing
+    build on every core), each step a sample of z levels of the workload sized
+    so that warm-up plus timed steps take about REF_SECONDS (one level at
+    least); rank 0 only."""
     rank = int(os.environ.get("RANK", 0))
     if rank != 0:
         return
     sampler = OracleSample()
-    per_level = sampler.run(G, 2) / 2
+    nx, ny, nz = sampler.nx, sampler.ny, sampler.nz
+    threads = host_threads()
+    per_level = sampler.run(G, 2, threads) / 2
     nsamp = max(1, args.steps + args.warmup)
-    nlev = max(1, min(NZ - 2 * G, int(REF_SECONDS / nsamp / max(per_level, 1e-6))))
-    span = NZ - 2 * G - nlev + 1
+    nlev = max(1, min(nz - 2 * G, int(REF_SECONDS / nsamp / max(per_level, 1e-6))))
+    span = nz - 2 * G - nlev + 1
     for s in range(args.warmup):
-        sampler.run(G + (s * nlev) % span, nlev)
+        sampler.run(G + (s * nlev) % span, nlev, threads)
     total = 0.0
     for s in range(args.steps):
-        total += sampler.run(G + (s * nlev) % span, nlev)
-    pts = NX * NY * nlev * args.steps
+        total += sampler.run(G + (s * nlev) % span, nlev, threads)
+    pts = nx * ny * nlev * args.steps
     value = pts / total / 1e9
-    cb = {"value": value, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
-          "sample": f"{args.steps} steps of {nlev} z level(s) of the 256^3 grid each "
-                    f"({pts} points, FP64, single thread, {total:.1f} s)"}
+    cb = {"value": value, "unit": "Gpts/s", "cores": threads, "kind": "oracle",
+          "sample": f"{args.steps} steps of {nlev} z level(s) of the {nx}x{ny}x{nz} grid each "
+                    f"({pts} points, FP64, {threads} thread(s), {total:.1f} s)"}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gpts/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": NX * NY * NZ / (value * 1e9) * 1e3, "higher_is_better": True,
+            "ms_per_step": nx * ny * nz / (value * 1e9) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": "256x256x256", "ghosts": G,
+            "config": {"workload": WORKLOAD, "grid": f"{nx}x{ny}x{nz}", "ghosts": G,
                        "bc": "periodic x,y; walls z", "op": "adv5 + const-nu diffusion"},
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "Gpts/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def committed_alu_peaks():
+    """The FMA rates of profiles/alu_peaks.json (measured by alu_peaks)."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "alu_peaks.json")))
+        return {k: {"tflops": d[k]["tflops"], "fma_per_sm_per_clk": d[k].get("fma_per_sm_per_clk"),
+                    "sm_mhz": d[k]["clocks"]["sm_mhz"]} for k in ("f32x2", "f64")}
+    except (OSError, KeyError, ValueError):
+        return {}
 
 
 def main():
@@ -602,9 +690,11 @@ def main():
     wisdom = os.path.join(ROOT, "paper_2303_12374_gb300", "wisdom")
     ctx = kl.kl_create(local, wisdom)
     stream = torch.cuda.Stream(device)
-    p, f, ins, outs = setup(args.dtype, device)
+    f = workload_fields()
+    p, f, ins, outs = setup(args.dtype, device, f)
     op = kl.Op(5, 1, p.dtype, 0)
-    pts = NX * NY * NZ
+    nx, ny, nz = extents()
+    pts = nx * ny * nz
     es = {0: 8, 1: 4, 2: 2, 3: 2}[p.dtype]
 
     def barrier():
@@ -639,18 +729,37 @@ def main():
         traffic = tr.get(key)
 
     extras = {}
+    alu = committed_alu_peaks()
+    alu_source = "profiles/alu_peaks.json (measured)" if alu else None
+    if not args.no_extras and rank == 0:
+        try:
+            alu = alu_peaks_live()
+            alu_source = "measured in this run (alu_peaks)"
+        except Exception as e:      # keep the committed figures
+            extras["alu_peaks_error"] = str(e)
+        extras["alu_peaks"] = alu
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    # FMA-pipe operation rates (an FMA is one operation) at the maximum clock
+    op_peaks = {}
+    if alu:
+        op_peaks["f32"] = alu["f32x2"]["tflops"] / 2 * 1e12
+        op_peaks["f64"] = alu["f64"]["tflops"] / 2 * 1e12
+
     if not args.no_extras and rank == 0:
         k2 = max(50, args.steps // 10)
         d_total, d_kern = time_steps(ctx, p, ins, outs, op, "default", k2, 5, stream)
         extras["default_config"] = {
             "config": "default (Table 2)", "value": pts * k2 / (d_total * 1e-3) / 1e9,
             "kernel_us": d_kern * 1e3,
-            "kernel_hbm_gbs": alg_bytes / (d_kern * 1e-3) / 1e9}
+            "kernel_hbm_gbs": alg_bytes / (d_kern * 1e-3) / 1e9,
+            "kernel_hbm_frac": alg_bytes / (d_kern * 1e-3) / 1e9 / peak_gbs}
         extras["tuned_config"] = {"config": tuned_cfg, "kernel_us": kern_ms * 1e3,
                                   "speedup_vs_default": d_kern / kern_ms}
-        extras["precision"] = precision_sweep(ctx, f, device, stream, max(20, args.steps // 20))
-        extras["batched"] = batched_run(ctx, device, stream)
-        extras["workloads"] = workload_sweep(ctx, device, stream, max(20, args.steps // 20))
+        extras["precision"] = precision_sweep(ctx, f, device, stream, max(20, args.steps // 30),
+                                              peak_gbs, op_peaks)
+        extras["workloads"] = workload_sweep(ctx, device, stream, max(20, args.steps // 30),
+                                             peak_gbs, op_peaks)
+        extras["batched"] = batched_run(ctx, device, stream, peak_gbs)
         extras["launch_overhead"] = launch_overhead(local, wisdom, device)
         extras["diag"] = diag_timing(ctx, p, outs, stream, ins=ins)
         extras["les_step"] = les_step(ctx, stream, peak_gbs)
@@ -659,9 +768,9 @@ def main():
     # three repeats each, the median reported: the host link and host memory
     # are shared with the other GPUs of the machine, so single runs vary
     barrier()
-    e_runs = [e2e_run(ctx, p, f, op, device, max(10, args.steps // 100), overlap=True)
+    e_runs = [e2e_run(ctx, p, f, op, device, max(10, args.steps // 60), overlap=True)
               for _ in range(3)]
-    s_runs = [e2e_run(ctx, p, f, op, device, max(5, args.steps // 400), overlap=False)
+    s_runs = [e2e_run(ctx, p, f, op, device, max(5, args.steps // 200), overlap=False)
               for _ in range(3)]
     barrier()
     e_ms, e_bytes = statistics.median(r[0] for r in e_runs), e_runs[0][1]
@@ -680,15 +789,24 @@ def main():
 
     cb = None
     if rank == 0 and world == 1:
-        cb, _ = cpu_baseline(args.cpu_seconds)
+        cb, _ = cpu_baseline(args.cpu_seconds, OracleSample(f))
 
     if rank == 0:
+        ops = OPS_PER_POINT * pts / (kern_ms * 1e-3)
+        alu_roof = None
+        if "f32" in op_peaks and args.dtype != "f64":
+            alu_roof = {"achieved": ops / 1e12, "peak": op_peaks["f32"] / 1e12, "unit": "Top/s",
+                        "frac": ops / op_peaks["f32"], "ops_per_point": OPS_PER_POINT,
+                        "peak_source": alu_source,
+                        "note": "FP32 FMA-pipe operations (an FMA is one) per point of the "
+                                "algorithm, each face flux formed once; peak = measured packed "
+                                "FMA rate"}
         line = {
             "metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": args.dtype, "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": "256x256x256", "ghosts": G,
+            "config": {"workload": WORKLOAD, "grid": f"{nx}x{ny}x{nz}", "ghosts": G,
                        "bc": "periodic x,y; free-slip walls z",
                        "op": "adv5 + const-nu diffusion, u,v,w fused",
                        "step": "kl_fill_ghosts_op + kl_launch (= kl_step)",
@@ -701,7 +819,8 @@ def main():
                          "kernel": "kl_tendency", "kernel_us": kern_ms * 1e3,
                          "alg_bytes_per_launch": alg_bytes,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"
-                                        if peaks.get("hbm_gbs") else "fallback"},
+                                        if peaks.get("hbm_gbs") else "fallback",
+                         "alu": alu_roof, "sms": sms},
             "clocks": clk.summary(),
             "gpu_launches": 2 * args.steps,
             "e2e": e2e,

@@ -76,11 +76,16 @@ typedef struct {
  * the number of elements of each buffer; every addressed element must lie in
  * [0, extent) and extent must be < 2^31.  Staggering is Arakawa C: u at
  * (i dx, (j+1/2) dy, z_k), v at ((i+1/2) dx, j dy, z_k), w at ((i+1/2) dx,
- * (j+1/2) dy, zh_k), nu at cell centres.  x and y are periodic; zbc = 0
- * periodic z, zbc = 1 free-slip walls at zh_0 and zh_nz (w = 0 there; the w
- * value stored at k = 0 must be 0).  zh (HOST, nz+1 face heights, increasing)
- * gives a stretched grid; zh = NULL means uniform spacing dz.  nu is the
- * constant viscosity for diff = 1.
+ * (j+1/2) dy, zh_k), nu at cell centres.  xybc = 0: x and y are periodic
+ * and the library forms their ghosts; xybc = 1: the grid is one block of a
+ * domain decomposed in x and y, whose x and y ghost cells the caller supplies
+ * (kl_halo_pack / kl_halo_unpack below): the ghost fills then write only the
+ * z ghost planes (over the padded x-y extent, from the same column) and every
+ * kernel reads the x and y ghosts from memory.  zbc = 0 periodic z, zbc = 1
+ * free-slip walls at zh_0 and zh_nz (w = 0 there; the w value stored at k = 0
+ * must be 0).  zh (HOST, nz+1 face heights, increasing) gives a stretched
+ * grid; zh = NULL means uniform spacing dz.  nu is the constant viscosity for
+ * diff = 1.
  */
 typedef struct {
     int32_t nx, ny, nz;
@@ -89,7 +94,7 @@ typedef struct {
     int64_t origin;
     int64_t extent;
     int32_t zbc;
-    int32_t reserved;
+    int32_t xybc;       /* 0 periodic x, y; 1 x, y ghosts supplied by the caller */
     double dx, dy, dz;
     double nu;
     const double *zh;
@@ -127,10 +132,48 @@ kl_status kl_layout(int32_t nx, int32_t ny, int32_t nz, int32_t g, int32_t dtype
  * pointers, layout `grid`, storage `dtype`): periodic copies in x and y (and z
  * for zbc = 0); at walls u, v, nu are mirrored evenly, w oddly with w = 0 on
  * the top wall face.  Every ghost point is copied straight from an interior
- * point, so edges and corners are filled in the same single launch.
+ * point, so edges and corners are filled in the same single launch.  With
+ * grid.xybc = 1 only the z ghost planes are written, each ghost from the same
+ * (x, y) column (x and y ghost columns included: they hold the exchanged
+ * halo), and the x and y ghosts of interior levels are left as they are.
  */
 kl_status kl_fill_ghosts(kl_ctx *ctx, int32_t dtype, const kl_grid *grid,
                          void *u, void *v, void *w, void *nu, void *stream);
+
+/*
+ * Halo exchange of an (x, y) domain decomposition.  MicroHH, the code whose
+ * kernels the paper tunes (Sec. 5.1-5.2), runs one grid split over many GPUs
+ * in x and y; each block (grid.xybc = 1) receives its x and y ghost cells
+ * from its neighbours.  The exchange runs in two phases so that corners need
+ * no diagonal messages: x first (strips of the interior rows), then y (strips
+ * that include the x ghosts just received).  These calls move one strip of
+ * `nf` fields (1..4; device pointers fields[0..nf-1], layout `grid`, storage
+ * dtype) between the padded arrays and a contiguous device buffer `buf`:
+ *
+ *   axis 0 (x): g columns x ny interior rows x nz interior levels.
+ *     pack   side 0: x in [0, g)        side 1: x in [nx - g, nx)
+ *     unpack side 0: x in [-g, 0)       side 1: x in [nx, nx + g)
+ *   axis 1 (y): nx + 2g columns (x in [-g, nx + g)) x g rows x nz levels.
+ *     pack   side 0: y in [0, g)        side 1: y in [ny - g, ny)
+ *     unpack side 0: y in [-g, 0)       side 1: y in [ny, ny + g)
+ *
+ * The buffer holds [field][k][row][column], column fastest; kl_halo_bytes
+ * gives its size.  A block sends its side-0 strip to the neighbour below it
+ * on that axis (which unpacks it on side 1) and its side-1 strip to the one
+ * above (unpacked on side 0); the transport between ranks is the caller's
+ * (NCCL send / recv, for instance).  Only interior levels move: after both
+ * phases, kl_fill_ghosts with xybc = 1 fills the z ghosts of every column,
+ * the received ones included.  Raw bits are copied.  Asynchronous on
+ * `stream`.  The buffer must not overlap the fields.
+ */
+kl_status kl_halo_bytes(const kl_grid *grid, int32_t dtype, int32_t axis, int32_t nf,
+                        int64_t *bytes);
+kl_status kl_halo_pack(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, int32_t axis,
+                       int32_t side, int32_t nf, const void *const *fields, void *buf,
+                       void *stream);
+kl_status kl_halo_unpack(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, int32_t axis,
+                         int32_t side, int32_t nf, void *const *fields, const void *buf,
+                         void *stream);
 
 /*
  * Tendencies ut, vt, wt of (u, v, w) on the interior (Sec. 5.2 stencils),

@@ -158,6 +158,24 @@ def tendencies(u, v, w, *, adv: int, diff: int, g: int, walls: bool, dx: float,
     return ut, vt, wt
 
 
+def tendencies_padded(up, vp, wp, *, adv: int, diff: int, g: int, walls: bool, dx: float,
+                      dy: float, zh: np.ndarray, nu: float = 0.0, np_=None):
+    """(ut, vt, wt) on the interior from padded u, v, w (and nu) whose ghosts
+    the caller has set, e.g. one block of a decomposed grid after its halo
+    exchange; dx, dy are the grid spacings, zh the block's nz+1 faces."""
+    lib = _load()
+    nzp, nyp, nxp = up.shape
+    nz, ny, nx = nzp - 2 * g, nyp - 2 * g, nxp - 2 * g
+    up, vp, wp = (np.ascontiguousarray(x, dtype=np.float64) for x in (up, vp, wp))
+    if np_ is not None:
+        np_ = np.ascontiguousarray(np_, dtype=np.float64)
+    dz, dzh = zprofile(nz, g, walls, zh)
+    ut, vt, wt = (np.empty((nz, ny, nx)) for _ in range(3))
+    lib.or_tendency(nx, ny, nz, g, int(walls), dx, dy, _p(dz), _p(dzh), adv, diff, nu,
+                    _p(up), _p(vp), _p(wp), _p(np_), 0, nz, _p(ut), _p(vt), _p(wt))
+    return ut, vt, wt
+
+
 def smagorinsky_padded(up, vp, wp, *, g: int, dx: float, dy: float, dz: np.ndarray,
                        dzh: np.ndarray, cs: float, levels=None):
     """Smagorinsky nu at the interior cell centres from padded u, v, w whose

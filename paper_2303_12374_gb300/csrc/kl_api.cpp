@@ -486,6 +486,7 @@ kl_status make_kargs(kl_ctx *ctx, const kl_op &op, const Config &cfg, const kl_g
     }
     a.err = ctx->d_err;
     a.wait_cycles = ctx->wait_cycles;
+    a.flags = g.xybc ? 1 : 0;
     a.sj = g.sj;
     a.sk = g.sk;
     a.nx = g.nx;
@@ -706,6 +707,60 @@ kl_status kl_fill_ghosts(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, void *
 }
 
 
+// ------------------------------------------------------- halo strips
+
+static kl_status halo_check(int32_t dtype, const kl_grid *grid, int32_t axis, int32_t side,
+                            int32_t nf)
+{
+    if (dtype < 0 || dtype > 3) return fail(KL_ERR_INVALID_ARG, "dtype must be 0..3");
+    if (axis != 0 && axis != 1) return fail(KL_ERR_INVALID_ARG, "axis must be 0 (x) or 1 (y)");
+    if (side != 0 && side != 1) return fail(KL_ERR_INVALID_ARG, "side must be 0 or 1");
+    if (nf < 1 || nf > 4) return fail(KL_ERR_INVALID_ARG, "nf must be 1..4");
+    return check_grid(grid, 1, nullptr);
+}
+
+kl_status kl_halo_bytes(const kl_grid *grid, int32_t dtype, int32_t axis, int32_t nf,
+                        int64_t *bytes)
+{
+    if (!bytes) return fail(KL_ERR_INVALID_ARG, "bytes is NULL");
+    kl_status st = halo_check(dtype, grid, axis, 0, nf);
+    if (st) return st;
+    int w, h;
+    halo_strip_shape(*grid, axis, &w, &h);
+    *bytes = (int64_t)w * h * grid->nz * nf * esize_of(dtype);
+    return KL_OK;
+}
+
+static kl_status halo_move(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, int32_t axis,
+                           int32_t side, int32_t nf, void *const *fields, void *buf, bool unpack,
+                           void *stream)
+{
+    if (!ctx || !fields || !buf) return fail(KL_ERR_INVALID_ARG, "ctx, fields and buf must not be NULL");
+    kl_status st = halo_check(dtype, grid, axis, side, nf);
+    if (st) return st;
+    for (int f = 0; f < nf; ++f)
+        if (!fields[f]) return fail(KL_ERR_INVALID_ARG, "a field pointer is NULL");
+    cudaError_t e = halo_launch(esize_of(dtype), *grid, axis, side, nf, fields, buf, unpack,
+                                (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, unpack ? "halo unpack launch" : "halo pack launch");
+    ctx->launches++;
+    return KL_OK;
+}
+
+kl_status kl_halo_pack(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, int32_t axis,
+                       int32_t side, int32_t nf, const void *const *fields, void *buf,
+                       void *stream)
+{
+    return halo_move(ctx, dtype, grid, axis, side, nf, (void *const *)fields, buf, false, stream);
+}
+
+kl_status kl_halo_unpack(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, int32_t axis,
+                         int32_t side, int32_t nf, void *const *fields, const void *buf,
+                         void *stream)
+{
+    return halo_move(ctx, dtype, grid, axis, side, nf, fields, (void *)buf, true, stream);
+}
+
 kl_status kl_capture_if_requested(kl_ctx *ctx, const kl_op *op, const kl_grid *grid,
                                   const kl_fields *fields, void *stream);
 
@@ -746,7 +801,8 @@ static kl_status fill_for_op(kl_ctx *ctx, const kl_op *op, const kl_grid *grid,
     if (st) return st;
     // the zpack kernel forms the x halo itself on grids with nx >= 64 + H
     // (constant nu)
-    const bool x_ghosts = !(cfg->family == 2 && op->diff != 2 && grid->nx >= 64 + halo_of(*op));
+    const bool x_ghosts = !(cfg->family == 2 && op->diff != 2 && grid->nx >= 64 + halo_of(*op)) &&
+                          !grid->xybc;
     cudaError_t e = fill_ghosts_launch(esize_of(op->dtype), *grid, (void *)fields->u,
                                        (void *)fields->v, (void *)fields->w, (void *)fields->nu,
                                        (cudaStream_t)stream, x_ghosts);

@@ -210,8 +210,8 @@ bool config_check(const kl_op &op, const Config &c, std::string *err)
             *err = "zmarch parameter outside the space";
             return false;
         }
-        if (c.family == 2 && (c.mbx != 32 || c.mpx != 2 || !in(c.mby, {1, 2, 4, 8, 16}) ||
-                              !in(c.mpy, {1, 2, 4, 8}))) {
+        if (c.family == 2 && (c.mbx != 32 || c.mpx != 2 || !in(c.mby, {1, 2, 3, 4, 6, 8, 16}) ||
+                              !in(c.mpy, {1, 2, 3, 4, 6, 8}))) {
             *err = "zpack parameter outside the space (w 1..16, ly 1..8)";
             return false;
         }
@@ -228,7 +228,8 @@ bool config_check(const kl_op &op, const Config &c, std::string *err)
             *err = "zpack with variable nu needs cs=0 and yx=0";
             return false;
         }
-        if (!in(c.kc, {4, 8, 16, 32, 64, 128, 256}) || !in(c.ns, {8, 9, 10, 12}) ||
+        if (!in(c.kc, {4, 8, 16, 32, 64, 128, 256}) ||
+            !(in(c.ns, {8, 9, 10, 12}) || (c.family == 2 && in(c.ns, {6, 7}))) ||
             c.mminb < 1 || c.mminb > 4) {
             *err = "z-march parameter outside the space";
             return false;
@@ -242,8 +243,12 @@ bool config_check(const kl_op &op, const Config &c, std::string *err)
             return false;
         }
         int reach = halo_of(op);
-        if (c.ns < 2 * reach + 2) {
-            *err = "plane ring needs at least 2R+2 slots";
+        // zpack with constant nu may carry plane k-2 in registers (ring of
+        // planes k-1 .. k+R plus one in flight: 2R slots)
+        const bool carry_ok = c.family == 2 && op.diff != 2 && !c.cs;
+        if (c.ns < 2 * reach + 2 && !(carry_ok && c.ns >= 2 * reach)) {
+            *err = carry_ok ? "plane ring needs at least 2R slots"
+                            : "plane ring needs at least 2R+2 slots";
             return false;
         }
         ZGeom z = zmarch_geometry(op, c);
@@ -268,13 +273,13 @@ static const int kBX[] = {16, 32, 64, 128, 256}, kBYZ[] = {1, 2, 4, 8, 16}, kT[]
 static const int kMBX[] = {32, 64, 128}, kMBY[] = {1, 2, 4, 8, 16}, kMP[] = {1, 2, 4},
                  kKC[] = {4, 8, 16, 32, 64, 128, 256}, kNS[] = {8, 9, 10, 12};
 
-static const int kW[] = {1, 2, 4, 8, 16}, kLY[] = {1, 2, 4, 8};
+static const int kW[] = {1, 2, 3, 4, 6, 8, 16}, kLY[] = {1, 2, 3, 4, 6, 8}, kNSP[] = {6, 7, 8, 9, 10, 12};
 
 int64_t space_size(int family)
 {
     if (family == 0) return 5LL * 5 * 5 * 27 * 8 * 8 * 6 * 6;
     if (family == 1) return 3LL * 5 * 3 * 3 * 7 * 4 * 4;
-    if (family == 2) return 5LL * 4 * 7 * 4 * 4 * 2 * 2;
+    if (family == 2) return 7LL * 6 * 7 * 6 * 4 * 2 * 2;
     return 0;
 }
 
@@ -302,10 +307,10 @@ bool space_config(int family, int64_t idx, Config *c)
     } else if (family == 2) {
         c->mbx = 32;
         c->mpx = 2;
-        c->mby = kW[take(5)];
-        c->mpy = kLY[take(4)];
+        c->mby = kW[take(7)];
+        c->mpy = kLY[take(6)];
         c->kc = kKC[take(7)];
-        c->ns = kNS[take(4)];
+        c->ns = kNSP[take(6)];
         c->mminb = 1 + take(4);
         c->yx = take(2);
         c->cs = take(2);
@@ -543,6 +548,7 @@ kl_status check_grid(const kl_grid *g, int need_g, Geom *geo)
     if (g->g > g->nx || g->g > g->ny || g->g >= g->nz + (g->zbc == 0 ? 1 : 0))
         return fail(KL_ERR_INVALID_ARG, "ghost width larger than the grid");
     if (g->zbc != 0 && g->zbc != 1) return fail(KL_ERR_INVALID_ARG, "zbc must be 0 or 1");
+    if (g->xybc != 0 && g->xybc != 1) return fail(KL_ERR_INVALID_ARG, "xybc must be 0 or 1");
     if (!(g->dx > 0) || !(g->dy > 0)) return fail(KL_ERR_INVALID_ARG, "dx, dy must be > 0");
     if (!g->zh && !(g->dz > 0)) return fail(KL_ERR_INVALID_ARG, "dz must be > 0 when zh is NULL");
     if (g->zh)

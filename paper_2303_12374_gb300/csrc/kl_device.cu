@@ -35,6 +35,8 @@ struct FillArgs {
     int rows_z, rows_y;      // rows of the z-plane group (2g x padded ny), y-row group (2g x nz)
     int nb_rows;             // blocks of the row groups
     unsigned n_x;            // cells of the x group (0: not filled)
+    int xyhalo;              // 1: x, y ghosts belong to the caller (z planes only,
+                             // each ghost from its own column, no x / y wrap)
 };
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
@@ -68,7 +70,7 @@ __device__ __forceinline__ void fill_row(const FillArgs &a, int j, int k, int la
     int ske, sko;
     bool wzero, wneg;
     fill_levels(a, k, ske, sko, wzero, wneg);
-    const long long sj = wrapi(j, a.ny);
+    const long long sj = a.xyhalo ? j : wrapi(j, a.ny);
     const long long dst0 = j * a.sj + k * a.sk;
     const long long src0 = sj * a.sj + ske * a.sk, srcw0 = sj * a.sj + sko * a.sk;
     for (int i0 = -G; i0 < a.nx + G; i0 += 32 * FILL_RU) {
@@ -77,7 +79,7 @@ __device__ __forceinline__ void fill_row(const FillArgs &a, int j, int k, int la
         for (int c = 0; c < FILL_RU; ++c) {
             const int i = i0 + lane + 32 * c;
             if (i >= a.nx + G) continue;
-            const int si = wrapi(i, a.nx);
+            const int si = a.xyhalo ? i : wrapi(i, a.nx);
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
                 if (!a.f[f]) continue;
@@ -164,6 +166,91 @@ static cudaError_t fill_dispatch(int g, unsigned grid, const FillArgs &a, cudaSt
     }
     return cudaGetLastError();
 }
+
+// ----------------------------------------------------- halo strips
+//
+// Pack / unpack of one halo strip of an x-y decomposed block (kl_halo_pack,
+// kl_halo_unpack): a box of W columns x H rows x nz levels at (x0, y0, 0) of
+// up to 4 fields <-> a contiguous buffer [field][k][row][column].  One thread
+// per element, raw bits (B = the storage word), x fastest so that the y
+// strips (whole padded rows) move in coalesced runs.
+
+struct HaloArgs {
+    char *f[4];              // fields at interior (0,0,0)
+    char *buf;
+    long long sj, sk;
+    int x0, y0, w, h, nz, nf;
+    int unpack;              // 0: fields -> buf, 1: buf -> fields
+};
+
+template <typename B>
+__global__ void __launch_bounds__(256) halo_kernel(HaloArgs a)
+{
+    const long long n = (long long)a.w * a.h * a.nz * a.nf;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x) {
+        long long r = q;
+        const int i = (int)(r % a.w);
+        r /= a.w;
+        const int j = (int)(r % a.h);
+        r /= a.h;
+        const int k = (int)(r % a.nz);
+        const int f = (int)(r / a.nz);
+        B *p = (B *)a.f[f] + ((long long)(a.x0 + i) + (long long)(a.y0 + j) * a.sj + (long long)k * a.sk);
+        B *b = (B *)a.buf + q;
+        if (a.unpack)
+            *p = *b;
+        else
+            *b = *p;
+    }
+}
+
+}  // namespace
+
+namespace kl {
+
+// W x H of the strip of `axis`
+void halo_strip_shape(const kl_grid &g, int axis, int *w, int *h)
+{
+    *w = axis == 0 ? g.g : g.nx + 2 * g.g;
+    *h = axis == 0 ? g.ny : g.g;
+}
+
+cudaError_t halo_launch(int esize, const kl_grid &g, int axis, int side, int nf, void *const *fields,
+                        void *buf, bool unpack, cudaStream_t s)
+{
+    HaloArgs a;
+    size_t off = (size_t)g.origin * esize;
+    for (int f = 0; f < 4; ++f) a.f[f] = f < nf ? (char *)fields[f] + off : nullptr;
+    a.buf = (char *)buf;
+    a.sj = g.sj;
+    a.sk = g.sk;
+    halo_strip_shape(g, axis, &a.w, &a.h);
+    a.nz = g.nz;
+    a.nf = nf;
+    a.unpack = unpack ? 1 : 0;
+    if (axis == 0) {
+        a.x0 = unpack ? (side ? g.nx : -g.g) : (side ? g.nx - g.g : 0);
+        a.y0 = 0;
+    } else {
+        a.x0 = -g.g;
+        a.y0 = unpack ? (side ? g.ny : -g.g) : (side ? g.ny - g.g : 0);
+    }
+    const long long n = (long long)a.w * a.h * a.nz * nf;
+    if (n == 0) return cudaSuccess;
+    const long long blocks = std::min<long long>((n + 255) / 256, 1LL << 20);
+    if (esize == 8)
+        halo_kernel<unsigned long long><<<(unsigned)blocks, 256, 0, s>>>(a);
+    else if (esize == 4)
+        halo_kernel<unsigned int><<<(unsigned)blocks, 256, 0, s>>>(a);
+    else
+        halo_kernel<unsigned short><<<(unsigned)blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace kl
+
+namespace {
 
 // ---------------------------------------------------------- diagnostics
 
@@ -409,8 +496,11 @@ cudaError_t fill_ghosts_launch(int esize, const kl_grid &g, void *u, void *v, vo
     a.ny = g.ny;
     a.nz = g.nz;
     a.zbc = g.zbc;
-    long long rows_z = 2LL * g.g * (g.ny + 2LL * g.g), rows_y = 2LL * g.g * g.nz;
-    long long n_x = x_ghosts ? 2LL * g.g * g.ny * g.nz : 0;
+    // a decomposed block (xybc = 1): the z planes only; its x and y ghosts
+    // hold the neighbours' halo
+    a.xyhalo = g.xybc ? 1 : 0;
+    long long rows_z = 2LL * g.g * (g.ny + 2LL * g.g), rows_y = g.xybc ? 0 : 2LL * g.g * g.nz;
+    long long n_x = x_ghosts && !g.xybc ? 2LL * g.g * g.ny * g.nz : 0;
     long long nb_rows = (rows_z + rows_y + FILL_W - 1) / FILL_W;
     long long nb_x = (n_x + FILL_T * FILL_U - 1) / (FILL_T * FILL_U);
     // 32-bit row and cell indices (the last x block's cells included)

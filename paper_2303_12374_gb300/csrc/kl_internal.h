@@ -147,6 +147,7 @@ struct KArgs {
     double cd[8];
     float cf[8];
     long long wait_cycles;
+    long long flags;            // bit 0: x, y ghosts supplied by the caller (grid.xybc)
 };
 
 struct Kernel {
@@ -245,6 +246,9 @@ bool config_fits(const kl_op &op, const Config &cfg, const kl_grid &g, const kl_
 // device kernels of kl_device.cu
 // x_ghosts false: leave the x ghosts of interior rows of interior levels as
 // they are (fill the y rows and z planes only)
+void halo_strip_shape(const kl_grid &g, int axis, int *w, int *h);
+cudaError_t halo_launch(int esize, const kl_grid &g, int axis, int side, int nf, void *const *fields,
+                        void *buf, bool unpack, cudaStream_t s);
 cudaError_t fill_ghosts_launch(int esize, const kl_grid &g, void *u, void *v, void *w,
                                void *nu, cudaStream_t s, bool x_ghosts = true);
 cudaError_t diag_launch(int dtype, const kl_grid &g, int level, const void *t,

@@ -92,6 +92,8 @@ struct kl_args {
     double cd[8];
     float cf[8];
     long long wait_cycles;        // limit of one device wait, SM clock cycles
+    long long flags;              // bit 0: x, y ghosts supplied by the caller (a block
+                                  // of an x-y decomposition): read them from memory
 };
 
 #if KL_DTYPE == 0
@@ -145,6 +147,42 @@ __device__ __forceinline__ void st(T *p, C v)
 #endif
 }
 
+// Global stores of tendencies for the ring families: plain st.global with no
+// memory clobber.  The tendencies never alias the shared-memory planes, and
+// without the clobber the compiler may keep plane values it has already
+// loaded across these stores (a generic store would force it to load them
+// again, since it could point into shared memory).
+__device__ __forceinline__ void kl_stg_b64(void *p, unsigned long long v)
+{
+    asm volatile("{\n .reg .u64 g;\n cvta.to.global.u64 g, %0;\n st.global.b64 [g], %1;\n}" ::"l"(p), "l"(v));
+}
+__device__ __forceinline__ void kl_stg_b32(void *p, unsigned v)
+{
+    asm volatile("{\n .reg .u64 g;\n cvta.to.global.u64 g, %0;\n st.global.b32 [g], %1;\n}" ::"l"(p), "r"(v));
+}
+__device__ __forceinline__ void kl_stg_b16(void *p, unsigned short v)
+{
+    asm volatile("{\n .reg .u64 g;\n cvta.to.global.u64 g, %0;\n st.global.b16 [g], %1;\n}" ::"l"(p), "h"(v));
+}
+__device__ __forceinline__ void kl_stg_v2f32(void *p, float a, float b)
+{
+    asm volatile("{\n .reg .u64 g;\n cvta.to.global.u64 g, %0;\n st.global.v2.f32 [g], {%1, %2};\n}"
+                 ::"l"(p), "f"(a), "f"(b));
+}
+__device__ __forceinline__ void kl_stg_v2f64(void *p, double a, double b)
+{
+    asm volatile("{\n .reg .u64 g;\n cvta.to.global.u64 g, %0;\n st.global.v2.f64 [g], {%1, %2};\n}"
+                 ::"l"(p), "d"(a), "d"(b));
+}
+__device__ __forceinline__ void kl_stg_f64(void *p, double v)
+{
+    asm volatile("{\n .reg .u64 g;\n cvta.to.global.u64 g, %0;\n st.global.f64 [g], %1;\n}" ::"l"(p), "d"(v));
+}
+__device__ __forceinline__ void kl_stg_f32(void *p, float v)
+{
+    asm volatile("{\n .reg .u64 g;\n cvta.to.global.u64 g, %0;\n st.global.f32 [g], %1;\n}" ::"l"(p), "f"(v));
+}
+
 #if KL_OF32
 __device__ __forceinline__ void out(TO *p, C v)
 {
@@ -162,6 +200,30 @@ __device__ __forceinline__ void out(T *p, C v)
     st(p, v);
 }
 #endif
+
+// one tendency value through the plain global stores above
+__device__ __forceinline__ void outg(TO *p, C v)
+{
+#if KL_OF32
+#if KL_ACC
+    v += *p;
+#endif
+    kl_stg_f32(p, v);
+#else
+#if KL_ACC
+    v += lds(p);
+#endif
+#if KL_DTYPE == 0
+    kl_stg_f64(p, v);
+#elif KL_DTYPE == 1
+    kl_stg_f32(p, v);
+#else
+    kl_u16 r;
+    st(&r, v);
+    kl_stg_b16(p, r);
+#endif
+#endif
+}
 
 // ------------------------------------------------------------ face fluxes
 //
@@ -520,7 +582,8 @@ kl_tendency(const kl_args a)
 #define KL_DEV_TIMEOUT 1
 #define KL_WAIT_LIMIT (1 << 22)
 
-static_assert(KL_NS >= 2 * KL_R + 2, "ring must hold the stencil planes plus one in flight");
+static_assert(KL_NS >= 2 * KL_R + 2 || (KL_FAMILY == 2 && KL_NS >= 2 * KL_R),
+              "ring must hold the stencil planes plus one in flight");
 static_assert(KL_PITCH <= 256 && KL_ROWS <= 256, "TMA box dimension above 256");
 
 struct __align__(64) kl_tmap { unsigned long long v[16]; };
@@ -815,10 +878,10 @@ __device__ __forceinline__ V vfma(V a, V b, V c) { return vmk(fma(a.lo, b.lo, c.
 #if KL_DTYPE == 0
 // aligned pair of consecutive elements at p (16-byte aligned)
 __device__ __forceinline__ V vld(const T *p) { double2 d = *(const double2 *)p; return vmk(d.x, d.y); }
-__device__ __forceinline__ void vst(T *p, V a) { *(double2 *)p = make_double2(a.lo, a.hi); }
+__device__ __forceinline__ void vst(T *p, V a) { kl_stg_v2f64(p, a.lo, a.hi); }
 #elif KL_DTYPE == 1
 __device__ __forceinline__ V vld(const T *p) { float2 d = *(const float2 *)p; return vmk(d.x, d.y); }
-__device__ __forceinline__ void vst(T *p, V a) { *(float2 *)p = make_float2(a.lo, a.hi); }
+__device__ __forceinline__ void vst(T *p, V a) { kl_stg_v2f32(p, a.lo, a.hi); }
 #else
 __device__ __forceinline__ V vld(const T *p)
 {
@@ -831,7 +894,7 @@ __device__ __forceinline__ void vst(T *p, V a)
     kl_u16 lo, hi;
     st(&lo, a.lo);
     st(&hi, a.hi);
-    *(unsigned *)p = (unsigned)lo | ((unsigned)hi << 16);
+    kl_stg_b32(p, (unsigned)lo | ((unsigned)hi << 16));
 }
 #endif
 __device__ __forceinline__ V vldg(const T *p) { return vld(p); }
@@ -866,7 +929,7 @@ __device__ __forceinline__ V vfma(V a, V b, V c)
 }
 #if KL_DTYPE == 1
 __device__ __forceinline__ V vld(const T *p) { V r; r.b = *(const unsigned long long *)p; return r; }
-__device__ __forceinline__ void vst(T *p, V a) { *(unsigned long long *)p = a.b; }
+__device__ __forceinline__ void vst(T *p, V a) { kl_stg_b64(p, a.b); }
 #else
 // two 16-bit values in one 32-bit word, widened to f32
 __device__ __forceinline__ V vld(const T *p)
@@ -880,7 +943,7 @@ __device__ __forceinline__ void vst(T *p, V a)
     kl_u16 lo, hi;
     st(&lo, vlo(a));
     st(&hi, vhi(a));
-    *(unsigned *)p = (unsigned)lo | ((unsigned)hi << 16);
+    kl_stg_b32(p, (unsigned)lo | ((unsigned)hi << 16));
 }
 #endif
 __device__ __forceinline__ V vldg(const T *p) { return vld(p); }
@@ -888,7 +951,7 @@ __device__ __forceinline__ V vldg(const T *p) { return vld(p); }
 __device__ __forceinline__ V vsplat(C a) { return vmk(a, a); }
 // aligned pair of tendencies (outputs): the storage type, or f32 (KL_OF32)
 #if KL_OF32
-__device__ __forceinline__ void vsto(TO *p, V a) { *(float2 *)p = make_float2(vlo(a), vhi(a)); }
+__device__ __forceinline__ void vsto(TO *p, V a) { kl_stg_v2f32(p, vlo(a), vhi(a)); }
 __device__ __forceinline__ V vldo(const TO *p) { float2 d = *(const float2 *)p; return vmk(d.x, d.y); }
 #else
 __device__ __forceinline__ void vsto(TO *p, V a) { vst(p, a); }
@@ -1079,7 +1142,7 @@ __device__ __forceinline__ void kl_cs_level(const kl_args &a, const kl_vk &K, co
 #endif
                 vsto(dst + o, t);
             } else if (c0 < (int)a.nx) {
-                out(dst + o, vlo(t));
+                outg(dst + o, vlo(t));
             }
         }
     }
@@ -1109,6 +1172,16 @@ __device__ __forceinline__ void kl_cs_level(const kl_args &a, const kl_vk &K, co
 #else
 #define KL_ZSLOT (3 * KL_PLANE_BYTES + 3 * KL_STRIP_BYTES)   // zpack ring slot
 #endif
+// carry mode: with constant nu and one warp group, a ring of fewer than 2R+2
+// slots holds planes k-1 .. k+R plus one in flight; the own-column values of
+// plane k-2 that the vertical windows still need were read at the level
+// before and stay in registers.  The first level's bottom faces, which reach
+// down to plane kb-R, are formed before the level loop while planes
+// kb-R .. kb+R-1 fill the ring.
+#define KL_CARRY (KL_NS < 2 * KL_R + 2)
+#if KL_CARRY && (KL_DIFF == 2 || KL_CS || KL_NS < 2 * KL_R || KL_R < 2)
+#error "a ring of fewer than 2R+2 slots needs constant nu, cs=0, R >= 2 and at least 2R slots"
+#endif
 #define KL_NT (32 * KL_MBY * (KL_CS ? 3 : 1))                // threads per block
 #define KL_XW_Q ((3 * KL_ROWS * KL_H + KL_NT - 1) / KL_NT)   // halo values per thread
 static_assert(KL_AL - 1 + KL_H - 1 < KL_XW_W, "a strip must hold the wrapped columns");
@@ -1136,7 +1209,10 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
     static_assert(KL_LPAD % 2 == 0 && KL_LPAD >= (KL_ADV == 5 ? 4 : 2), "left pad too small");
     static_assert(KL_PITCH >= KL_LPAD + 64 + (KL_ADV == 5 ? 3 : 1), "right pad too small");
     extern __shared__ unsigned char kl_smem_raw[];
-    unsigned char *ring = (unsigned char *)(((unsigned long long)kl_smem_raw + 127) & ~127ull);
+    // 128-byte aligned ring start, formed by pointer arithmetic on the shared
+    // array so that every access below stays a shared-memory access (an
+    // integer round trip would turn them into generic loads)
+    unsigned char *ring = kl_smem_raw + ((128u - (kl_smem_addr(kl_smem_raw) & 127u)) & 127u);
 #if KL_DIFF == 2
     unsigned char *nring = ring + KL_NS * KL_ZSLOT;
     unsigned long long *bars = (unsigned long long *)(nring + KL_NNS * KL_NPLANE);
@@ -1145,7 +1221,7 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
 #endif
 #if KL_YX
     // y-face exchange buffer after the barriers: [3 fields][warps][32 lanes]
-    V *xbuf = (V *)(((unsigned long long)(bars + KL_NS) + 15) & ~15ull);
+    V *xbuf = (V *)((unsigned char *)bars + KL_RUP(8 * KL_NS, 16));
 #endif
     const int lane = threadIdx.x;
     const int warp = KL_CS ? (int)threadIdx.y % KL_MBY : (int)threadIdx.y;
@@ -1164,7 +1240,7 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
     }
     __syncthreads();
     // x wrap (see above): which side this tile wraps, never both
-    const bool xw_on = KL_DIFF != 2 && nx >= 64 + KL_H;
+    const bool xw_on = KL_DIFF != 2 && nx >= 64 + KL_H && !(a.flags & 1);
     const bool need_l = xw_on && tx0 == 0, need_r = xw_on && tx0 + 64 + KL_H > nx;
     const bool xwrap = need_l || need_r;
     const int xs0 = need_l ? (nx - KL_H) / KL_AL * KL_AL : 0;   // first strip column
@@ -1220,7 +1296,7 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
         for (int t = 0; t < KL_XW_Q; ++t)
             if (xw_src[t] >= 0) *(T *)(slot + xw_dst[t]) = *(const T *)(slot + xw_src[t]);
     };
-    auto slot_of = [&](int p) { return ring + ((p - p_first) % KL_NS) * KL_ZSLOT; };
+    auto slot_of = [&](int p) { return ring + ((unsigned)(p - p_first) % KL_NS) * KL_ZSLOT; };
 
     // coefficients (f32 kernels read the f32 copies; no f64 arithmetic)
     const C dxi = KL_CO(a, 0), dyi = KL_CO(a, 1), nu = KL_CO(a, 4);
@@ -1250,9 +1326,58 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
     // planes of the first level; afterwards each level ends with the wait for
     // the next level's newest plane and one barrier that both releases the
     // slot of plane k-R and makes the time-out decision uniform
+#if KL_CARRY
+    V zc[KL_MPY][3];    // own values of plane k-2 (u, v, w) per row
+#endif
     {
         bool ok = true;
-        for (int q = p_first; q <= kb + KL_R && ok; ++q) {
+        const int q_last = KL_CARRY ? kb + KL_R - 1 : kb + KL_R;
+        for (int q = p_first; q <= q_last && ok; ++q) {
+            ok = kl_mbar_wait(kl_smem_addr(&bars[(q - p_first) % KL_NS]), ((q - p_first) / KL_NS) & 1,
+                              a.wait_cycles);
+            if (ok && xwrap) xw_copy(slot_of(q));
+        }
+        timed_out = __syncthreads_or(!ok);
+        if (!timed_out) p_waited = q_last;
+    }
+#if KL_CARRY
+    if (!timed_out) {
+        // bottom faces of level kb (planes kb-R .. kb+R-1) and the carried
+        // plane kb-2; then the slots of kb-R and kb-R+1 take the next planes
+        // and the first level waits for plane kb+R
+        const char *pl[2 * KL_R + 1];
+#pragma unroll
+        for (int d = -KL_R; d <= KL_R; ++d)        // d = R: not landed yet, never read here
+            pl[d + KL_R] = (const char *)(ring + ((unsigned)(kb + d - p_first) % KL_NS) * KL_ZSLOT);
+        const kl_zmetric Z = kl_make_z(a, kb);
+        const V kzu_b = vsplat(nu * Z.dzhi / KL_FS), kzw_b = vsplat(nu * Z.dzi_dn / KL_FS);
+#pragma unroll
+        for (int r = 0; r < KL_MPY; ++r) {
+            const int yr = r0 + r;
+            const V u_0 = kl_pr<0, 0, 0>(pl, lx, yr), v_0 = kl_pr<1, 0, 0>(pl, lx, yr),
+                    w_0 = kl_pr<2, 0, 0>(pl, lx, yr);
+            zb[r][0] = kl_vflux(K, vadd(vcross(kl_pr<2, 0, -2>(pl, lx, yr), w_0), w_0),
+                                kl_pr<0, -3, 0>(pl, lx, yr), kl_pr<0, -2, 0>(pl, lx, yr),
+                                kl_pr<0, -1, 0>(pl, lx, yr), u_0, kl_pr<0, 1, 0>(pl, lx, yr),
+                                kl_pr<0, 2, 0>(pl, lx, yr), kzu_b);
+            zb[r][1] = kl_vflux(K, vadd(kl_pr<2, 0, 0>(pl, lx, yr - 1), w_0),
+                                kl_pr<1, -3, 0>(pl, lx, yr), kl_pr<1, -2, 0>(pl, lx, yr),
+                                kl_pr<1, -1, 0>(pl, lx, yr), v_0, kl_pr<1, 1, 0>(pl, lx, yr),
+                                kl_pr<1, 2, 0>(pl, lx, yr), kzu_b);
+            zb[r][2] = kl_vflux(K, vadd(kl_pr<2, -1, 0>(pl, lx, yr), w_0),
+                                kl_pr<2, -3, 0>(pl, lx, yr), kl_pr<2, -2, 0>(pl, lx, yr),
+                                kl_pr<2, -1, 0>(pl, lx, yr), w_0, kl_pr<2, 1, 0>(pl, lx, yr),
+                                kl_pr<2, 2, 0>(pl, lx, yr), kzw_b);
+            zc[r][0] = kl_pr<0, -2, 0>(pl, lx, yr);
+            zc[r][1] = kl_pr<1, -2, 0>(pl, lx, yr);
+            zc[r][2] = kl_pr<2, -2, 0>(pl, lx, yr);
+        }
+        __syncthreads();                            // planes kb-R, kb-R+1 read for the last time
+        if (tid == 0)
+            for (int t = 0; t < 2 && p_next <= p_last; ++t) issue(p_next++);
+        bool ok = true;
+        {
+            const int q = kb + KL_R;
             ok = kl_mbar_wait(kl_smem_addr(&bars[(q - p_first) % KL_NS]), ((q - p_first) / KL_NS) & 1,
                               a.wait_cycles);
             if (ok && xwrap) xw_copy(slot_of(q));
@@ -1260,11 +1385,12 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
         timed_out = __syncthreads_or(!ok);
         if (!timed_out) p_waited = kb + KL_R;
     }
+#endif
     for (int k = kb; k < ke && !timed_out; ++k) {
         const char *pl[2 * KL_R + 1];
 #pragma unroll
         for (int d = -KL_R; d <= KL_R; ++d)
-            pl[d + KL_R] = (const char *)(ring + ((k + d - p_first) % KL_NS) * KL_ZSLOT);
+            pl[d + KL_R] = (const char *)(ring + ((unsigned)(k + d - p_first) % KL_NS) * KL_ZSLOT);
 #define KL_Q(f, dk, dx, row) kl_pr<f, dk, dx>(pl, lx, row)
 
         const kl_zmetric Z = kl_make_z(a, k);
@@ -1284,7 +1410,7 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
         const char *npl[3];
 #pragma unroll
         for (int d = -1; d <= 1; ++d)
-            npl[d + 1] = (const char *)(nring + ((k + d - (kb - 1)) % KL_NNS) * KL_NPLANE);
+            npl[d + 1] = (const char *)(nring + ((unsigned)(k + d - (kb - 1)) % KL_NNS) * KL_NPLANE);
 #define KL_N(dk, dx, row) kl_npr<(dk), (dx)>(npl, lx, (row))
         // nu summed over the two columns (c-1, c) of an xh edge
 #define KL_NSX(dk, row) vadd(vcross(KL_N(dk, -2, row), KL_N(dk, 0, row)), KL_N(dk, 0, row))
@@ -1516,15 +1642,21 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
 #endif
 
             // ---- z faces: bottom carried, top formed here
+#if KL_CARRY
+#define KL_QM2(f) zc[r][f]
+#else
+#define KL_QM2(f) KL_Q(f, -2, 0, yr)
+#endif
             V fz_u = kl_vflux(K, vadd(vcross(KL_Q(2, 1, -2, yr), KL_Q(2, 1, 0, yr)), KL_Q(2, 1, 0, yr)),
-                              KL_A5(KL_Q(0, -2, 0, yr)), KL_A5(KL_Q(0, -1, 0, yr)), u_0,
+                              KL_A5(KL_QM2(0)), KL_A5(KL_Q(0, -1, 0, yr)), u_0,
                               KL_Q(0, 1, 0, yr), KL_A5(KL_Q(0, 2, 0, yr)), KL_A5(KL_Q(0, 3, 0, yr)), vkzu_top);
             V fz_v = kl_vflux(K, vadd(KL_Q(2, 1, 0, yr - 1), KL_Q(2, 1, 0, yr)),
-                              KL_A5(KL_Q(1, -2, 0, yr)), KL_A5(KL_Q(1, -1, 0, yr)), v_0,
+                              KL_A5(KL_QM2(1)), KL_A5(KL_Q(1, -1, 0, yr)), v_0,
                               KL_Q(1, 1, 0, yr), KL_A5(KL_Q(1, 2, 0, yr)), KL_A5(KL_Q(1, 3, 0, yr)), vkzu_top);
             V fz_w = kl_vflux(K, vadd(w_0, KL_Q(2, 1, 0, yr)),
-                              KL_A5(KL_Q(2, -2, 0, yr)), KL_A5(KL_Q(2, -1, 0, yr)), w_0,
+                              KL_A5(KL_QM2(2)), KL_A5(KL_Q(2, -1, 0, yr)), w_0,
                               KL_Q(2, 1, 0, yr), KL_A5(KL_Q(2, 2, 0, yr)), KL_A5(KL_Q(2, 3, 0, yr)), vkzw_top);
+#if !KL_CARRY
             if (k == kb) {
                 // bottom faces of the first level: u, v at zh_k, w at z_{k-1}
                 const V kzu_b = vsplat(nu * Z.dzhi / KL_FS), kzw_b = vsplat(nu * Z.dzi_dn / KL_FS);
@@ -1538,6 +1670,7 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
                                     KL_A5(KL_Q(2, -3, 0, yr)), KL_A5(KL_Q(2, -2, 0, yr)), KL_Q(2, -1, 0, yr),
                                     w_0, KL_A5(KL_Q(2, 1, 0, yr)), KL_A5(KL_Q(2, 2, 0, yr)), kzw_b);
             }
+#endif
 #if KL_DIFF == 2
             {
                 // top z faces: xz and yz edges at zh_{k+1}, w's normal stress at z_k
@@ -1567,6 +1700,13 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
             zb[r][0] = fz_u;
             zb[r][1] = fz_v;
             zb[r][2] = fz_w;
+#if KL_CARRY
+            // plane k-1 is the next level's plane k-2
+            zc[r][0] = KL_Q(0, -1, 0, yr);
+            zc[r][1] = KL_Q(1, -1, 0, yr);
+            zc[r][2] = KL_Q(2, -1, 0, yr);
+#endif
+#undef KL_QM2
             fuy_b = fuy_t;
             fvy_b = fvy_t;
             fwy_b = fwy_t;
@@ -1587,9 +1727,9 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
                     vsto(a.vt + o, tv);
                     vsto(a.wt + o, tw);
                 } else if (c0 < nx) {
-                    out(a.ut + o, vlo(tu));
-                    out(a.vt + o, vlo(tv));
-                    out(a.wt + o, vlo(tw));
+                    outg(a.ut + o, vlo(tu));
+                    outg(a.vt + o, vlo(tv));
+                    outg(a.wt + o, vlo(tw));
                 }
             }
         }

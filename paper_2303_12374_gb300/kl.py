@@ -35,7 +35,7 @@ class Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("g", ctypes.c_int32), ("sj", ctypes.c_int64), ("sk", ctypes.c_int64),
                 ("origin", ctypes.c_int64), ("extent", ctypes.c_int64),
-                ("zbc", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("zbc", ctypes.c_int32), ("xybc", ctypes.c_int32),
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
                 ("nu", ctypes.c_double), ("zh", ctypes.POINTER(ctypes.c_double))]
 
@@ -114,6 +114,11 @@ SIGNATURES = {
     "kl_def_tune": ([_P, _P, _S, _S, _S], ctypes.c_int),
     "kl_smagorinsky": ([_P, _I32, ctypes.POINTER(Grid), _D, _P, _P, _P, _P, _I32, _P],
                        ctypes.c_int),
+    "kl_halo_bytes": ([ctypes.POINTER(Grid), _I32, _I32, _I32, ctypes.POINTER(_I64)], ctypes.c_int),
+    "kl_halo_pack": ([_P, _I32, ctypes.POINTER(Grid), _I32, _I32, _I32, ctypes.POINTER(_P), _P, _P],
+                     ctypes.c_int),
+    "kl_halo_unpack": ([_P, _I32, ctypes.POINTER(Grid), _I32, _I32, _I32, ctypes.POINTER(_P), _P,
+                        _P], ctypes.c_int),
     "kl_batch_shard": ([_I32, ctypes.POINTER(_I64), _I32, _I32, ctypes.POINTER(_I32),
                         ctypes.POINTER(_I32), ctypes.POINTER(_I64)], ctypes.c_int),
     "kl_version": ([], _S),
@@ -176,6 +181,24 @@ def kl_layout(nx, ny, nz, g, dtype):
 
 def kl_fill_ghosts(ctx, dtype, grid: Grid, u, v, w, nu=None, stream=None) -> None:
     check(load().kl_fill_ghosts(ctx, dtype, ctypes.byref(grid), u, v, w, nu, stream))
+
+
+def kl_halo_bytes(grid: Grid, dtype, axis, nf) -> int:
+    out = ctypes.c_int64()
+    check(load().kl_halo_bytes(ctypes.byref(grid), dtype, axis, nf, ctypes.byref(out)))
+    return out.value
+
+
+def kl_halo_pack(ctx, dtype, grid: Grid, axis, side, fields, buf, stream=None) -> None:
+    arr = (_P * len(fields))(*fields)
+    check(load().kl_halo_pack(ctx, dtype, ctypes.byref(grid), axis, side, len(fields), arr, buf,
+                              stream))
+
+
+def kl_halo_unpack(ctx, dtype, grid: Grid, axis, side, fields, buf, stream=None) -> None:
+    arr = (_P * len(fields))(*fields)
+    check(load().kl_halo_unpack(ctx, dtype, ctypes.byref(grid), axis, side, len(fields), arr, buf,
+                                stream))
 
 
 def kl_launch(ctx, op: Op, grid: Grid, fields: Fields, stream=None) -> None:

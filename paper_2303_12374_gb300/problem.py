@@ -21,7 +21,7 @@ class Problem:
     """Layout and scalars of one grid; buffers are 1D torch tensors of `extent` elements."""
 
     def __init__(self, nx, ny, nz, *, g, dtype, walls, dx=None, dy=None, dz=None, zh=None,
-                 nu=0.0, device="cuda"):
+                 nu=0.0, device="cuda", xybc=False):
         self.nx, self.ny, self.nz, self.g = nx, ny, nz, g
         self.dtype = kl.DTYPES[dtype] if isinstance(dtype, str) else dtype
         self.tdtype = TORCH_DTYPES[self.dtype]
@@ -33,7 +33,8 @@ class Problem:
             self._zh = np.ascontiguousarray(zh, dtype=np.float64)
             zh_ptr = self._zh.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         self.grid = kl.Grid(nx, ny, nz, g, self.sj, self.sk, self.origin, self.extent,
-                            1 if walls else 0, 0, dx if dx else 1.0 / nx, dy if dy else 1.0 / ny,
+                            1 if walls else 0, 1 if xybc else 0,
+                            dx if dx else 1.0 / nx, dy if dy else 1.0 / ny,
                             dz if dz else (0.0 if zh is not None else 1.0 / nz), nu, zh_ptr)
 
     # ---------------------------------------------------------- buffers

@@ -31,6 +31,7 @@ GAMMA = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
 BASE_SEED = 2303123740
+_BLOCK = 1 << 18
 
 
 def _mix(z: np.ndarray) -> np.ndarray:
@@ -47,15 +48,36 @@ class SplitMix64:
         self.pos = 0
 
     def u64(self, n: int) -> np.ndarray:
+        out = np.empty(n, dtype=np.uint64)
         with np.errstate(over="ignore"):
-            ctr = np.arange(self.pos + 1, self.pos + 1 + n, dtype=np.uint64)
-            out = _mix(self.seed + ctr * GAMMA)
+            # blocks of counters small enough for the temporaries to stay in cache
+            t = np.empty(min(n, _BLOCK), dtype=np.uint64)
+            for s in range(0, n, _BLOCK):
+                m = min(_BLOCK, n - s)
+                z = out[s:s + m]
+                z[:] = np.arange(self.pos + 1 + s, self.pos + 1 + s + m, dtype=np.uint64)
+                z *= GAMMA
+                z += self.seed
+                # the mix of _mix, in place
+                tt = t[:m]
+                np.right_shift(z, np.uint64(30), out=tt)
+                z ^= tt
+                z *= _M1
+                np.right_shift(z, np.uint64(27), out=tt)
+                z ^= tt
+                z *= _M2
+                np.right_shift(z, np.uint64(31), out=tt)
+                z ^= tt
         self.pos += n
         return out
 
     def uniform(self, n: int) -> np.ndarray:
         """n uniforms on [0, 1)."""
-        return (self.u64(n) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+        u = self.u64(n)
+        u >>= np.uint64(11)
+        f = u.astype(np.float64)
+        f *= 2.0 ** -53
+        return f
 
     def normal(self) -> float:
         u1, u2 = self.uniform(2)

@@ -64,6 +64,7 @@ def test_single_process_needs_no_group(monkeypatch):
 def test_reference_arm_prints_on_rank_zero_only(monkeypatch):
     import bench
     monkeypatch.setattr(bench, "REF_SECONDS", 0.5)
+    monkeypatch.setattr(bench, "WORKLOAD", "walls256_adv5_diff")   # a grid quick to draw
     args = SimpleNamespace(steps=2, warmup=1, gpus=2)
     monkeypatch.setenv("RANK", "1")
     buf = io.StringIO()
@@ -76,5 +77,17 @@ def test_reference_arm_prints_on_rank_zero_only(monkeypatch):
         bench.run_reference(args)
     line = json.loads(buf.getvalue())
     assert line["impl"] == "reference" and line["value"] > 0
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle"
+    assert line["cpu_baseline"]["cores"] == bench.host_threads() >= 1
+    assert line["config"]["grid"] == "256x256x256"
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_cpu_baseline_reports_one_thread_and_all_cores(monkeypatch):
+    import bench
+    monkeypatch.setattr(bench, "WORKLOAD", "walls256_adv5_diff")
+    cb, _ = bench.cpu_baseline(0.3)
+    assert cb["kind"] == "oracle" and cb["value"] > 0
+    assert cb["single_thread"]["cores"] == 1
+    assert cb["cores"] == bench.host_threads()
+    assert cb["host_cpus"] == os.cpu_count()

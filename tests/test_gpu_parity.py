@@ -32,6 +32,10 @@ CONFIGS_DIRECT = [
     "zpack:w=2,ly=4,kc=8,ns=9,minb=1,cs=1",
     "zpack:w=1,ly=1,kc=4,ns=8,minb=1,cs=1",
     "zpack:w=8,ly=2,kc=32,ns=10,minb=1,cs=1",
+    # rings of 2R and 2R+1 slots: plane k-2 carried in registers
+    "zpack:w=6,ly=2,kc=8,ns=6,minb=2",
+    "zpack:w=4,ly=3,kc=4,ns=7,minb=1",
+    "zpack:w=2,ly=2,kc=16,ns=6,minb=1,yx=1",
 ]
 
 
@@ -125,6 +129,23 @@ def test_component_split_is_bit_identical(ctx, dtype, walls, adv, diff):
 
 
 @pytest.mark.parametrize("dtype", [0, 1, 3])
+@pytest.mark.parametrize("walls,adv", [(True, 5), (False, 5), (False, 2)])
+def test_carried_plane_ring_is_bit_identical(ctx, dtype, walls, adv):
+    """A ring of 2R slots (plane k-2 carried in registers, the first level's
+    bottom faces formed before the level loop) gives the same bits as the
+    2R+2-slot ring: the same values enter the same expressions."""
+    f = make_inputs(131, 45, 23, seed=12, walls=walls, stretch=2.0)
+    res = []
+    for ns in (8, 6):
+        cfg = f"zpack:w=2,ly=2,kc=8,ns={ns},minb=1"
+        p, _, outs, _ = run_gpu(ctx, f, adv=adv, diff=1, dtype=dtype, walls=walls,
+                                g=3 if adv == 5 else 1, stretched=True, config=cfg)
+        res.append([p.download(outs[k]) for k in ("ut", "vt", "wt")])
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("dtype", [0, 1, 3])
 @pytest.mark.parametrize("nx,ny,nz,walls,adv", [
     (67, 20, 9, True, 5),     # narrowest grid the kernel wraps itself (64 + 3)
     (128, 12, 7, False, 5),   # the right halo lies in the last tile
@@ -141,7 +162,8 @@ def test_zpack_x_wrap_in_kernel(ctx, oracle_mod, dtype, nx, ny, nz, walls, adv):
     g = 3 if adv == 5 else 1
     wraps = nx >= 64 + g
     f = make_inputs(nx, ny, nz, seed=nx + ny, walls=walls, stretch=2.0)
-    for cfg in ("zpack:w=2,ly=2,kc=4,ns=8,minb=1", "zpack:w=4,ly=2,kc=16,ns=9,minb=1,cs=1"):
+    for cfg in ("zpack:w=2,ly=2,kc=4,ns=8,minb=1", "zpack:w=4,ly=2,kc=16,ns=9,minb=1,cs=1",
+                "zpack:w=6,ly=2,kc=4,ns=6,minb=2"):
         try:
             kl.kl_config_normalize(kl.Op(adv, 1, dtype, 0), cfg)
         except kl.KLError:
