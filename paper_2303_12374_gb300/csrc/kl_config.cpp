@@ -163,9 +163,13 @@ size_t zmarch_smem_bytes(const kl_op &op, const Config &c)
         // zpack x-wrap strips: 3 fields x rows x 32 bytes per slot (128-B multiples)
         bytes += 3 * (size_t)((z.rows * 32 + 127) / 128 * 128) * c.ns;
     }
-    // zpack y-face exchange: 3 fields x warps x 32 lanes x one packed pair
-    if (c.family == 2 && c.yx)
-        bytes += 3 * (size_t)c.mby * 32 * (op.dtype == KL_F64 ? 16 : 8) + 16;
+    // zpack y-face exchange: 3 fields x warps x 32 lanes x one packed pair;
+    // one level ahead (yx=2) by level parity, with the tile's top faces and
+    // its scalar x side faces
+    const size_t pair = op.dtype == KL_F64 ? 16 : 8, scal = op.dtype == KL_F64 ? 8 : 4;
+    if (c.family == 2 && c.yx == 1) bytes += 3 * (size_t)c.mby * 32 * pair + 16;
+    if (c.family == 2 && c.yx == 2)
+        bytes += 2 * 3 * ((size_t)c.mby * 32 * pair + 32 * pair + (size_t)z.tys * scal) + 16;
     return bytes;
 }
 
@@ -211,13 +215,13 @@ bool config_check(const kl_op &op, const Config &c, std::string *err)
             return false;
         }
         if (c.family == 2 && (c.mbx != 32 || c.mpx != 2 || !in(c.mby, {1, 2, 3, 4, 6, 8, 16}) ||
-                              !in(c.mpy, {1, 2, 3, 4, 6, 8}))) {
+                              !in(c.mpy, {1, 2, 3, 4, 5, 6, 8}))) {
             *err = "zpack parameter outside the space (w 1..16, ly 1..8)";
             return false;
         }
         if (c.family == 2 &&
-            ((c.yx != 0 && c.yx != 1) || (c.pk != 0 && c.pk != 1) || (c.cs != 0 && c.cs != 1))) {
-            *err = "yx, pk and cs must be 0 or 1";
+            ((c.yx < 0 || c.yx > 2) || (c.pk != 0 && c.pk != 1) || (c.cs != 0 && c.cs != 1))) {
+            *err = "yx must be 0..2, pk and cs 0 or 1";
             return false;
         }
         if (c.family == 2 && c.cs && c.yx) {
@@ -245,7 +249,11 @@ bool config_check(const kl_op &op, const Config &c, std::string *err)
         int reach = halo_of(op);
         // zpack with constant nu may carry plane k-2 in registers (ring of
         // planes k-1 .. k+R plus one in flight: 2R slots)
-        const bool carry_ok = c.family == 2 && op.diff != 2 && !c.cs;
+        const bool carry_ok = c.family == 2 && op.diff != 2 && !c.cs && reach >= 2;
+        if (c.family == 2 && c.yx == 2 && !(carry_ok && c.ns < 2 * reach + 2)) {
+            *err = "yx=2 needs a ring of fewer than 2R+2 slots (2R or 2R+1), constant nu and cs=0";
+            return false;
+        }
         if (c.ns < 2 * reach + 2 && !(carry_ok && c.ns >= 2 * reach)) {
             *err = carry_ok ? "plane ring needs at least 2R slots"
                             : "plane ring needs at least 2R+2 slots";
@@ -273,13 +281,13 @@ static const int kBX[] = {16, 32, 64, 128, 256}, kBYZ[] = {1, 2, 4, 8, 16}, kT[]
 static const int kMBX[] = {32, 64, 128}, kMBY[] = {1, 2, 4, 8, 16}, kMP[] = {1, 2, 4},
                  kKC[] = {4, 8, 16, 32, 64, 128, 256}, kNS[] = {8, 9, 10, 12};
 
-static const int kW[] = {1, 2, 3, 4, 6, 8, 16}, kLY[] = {1, 2, 3, 4, 6, 8}, kNSP[] = {6, 7, 8, 9, 10, 12};
+static const int kW[] = {1, 2, 3, 4, 6, 8, 16}, kLY[] = {1, 2, 3, 4, 5, 6, 8}, kNSP[] = {6, 7, 8, 9, 10, 12};
 
 int64_t space_size(int family)
 {
     if (family == 0) return 5LL * 5 * 5 * 27 * 8 * 8 * 6 * 6;
     if (family == 1) return 3LL * 5 * 3 * 3 * 7 * 4 * 4;
-    if (family == 2) return 7LL * 6 * 7 * 6 * 4 * 2 * 2;
+    if (family == 2) return 7LL * 7 * 7 * 6 * 4 * 3 * 2;
     return 0;
 }
 
@@ -308,11 +316,11 @@ bool space_config(int family, int64_t idx, Config *c)
         c->mbx = 32;
         c->mpx = 2;
         c->mby = kW[take(7)];
-        c->mpy = kLY[take(6)];
+        c->mpy = kLY[take(7)];
         c->kc = kKC[take(7)];
         c->ns = kNSP[take(6)];
         c->mminb = 1 + take(4);
-        c->yx = take(2);
+        c->yx = take(3);
         c->cs = take(2);
     } else {
         c->mbx = kMBX[take(3)];

@@ -324,8 +324,13 @@ __device__ __forceinline__ double ff_value(const kl_ff &acc) { return (double)ac
 // and the sums run in float-float; a lane folds its float-float partials into
 // FP64 once per level it touches (the dz-weighted sum takes that level's sum
 // times w_k).  GB300 runs FP64 at a small fraction of its FP32 rate, which is
-// what this keeps off the per-element path.  With a reference, or f64
-// storage, every element is reduced in FP64.
+// what this keeps off the per-element path.  With f64 storage every element
+// is reduced in FP64.  With an FP64 reference and f32 or 16-bit storage the
+// difference e = t - ref and the two sums of squares stay FP64 (one
+// subtraction, two FMAs per element: their relative accuracy is the FP64
+// one), the two maxima are taken as integer maxima of the magnitudes' bit
+// patterns (IEEE order of non-negative doubles, no FP64 work) and the sum of
+// t runs in float-float as above.
 template <typename T, bool REF>
 __global__ void __launch_bounds__(256) diag_kernel(DiagArgs a)
 {
@@ -342,9 +347,34 @@ __global__ void __launch_bounds__(256) diag_kernel(DiagArgs a)
         float tmax = 0.0f;
         kl_ff s1 = {0.0f, 0.0f}, s2 = {0.0f, 0.0f};      // this level's sum and squares
         double rs = 0.0;                                 // this level's sum (FP64 path)
+        unsigned long long emax = 0, rmax = 0;           // |e|, |ref| maxima as bit patterns
+        constexpr unsigned long long kMag = 0x7fffffffffffffffull;
         for (long long r = rb; r < re; ++r) {
             const long long o0 = j * a.sj + (long long)k * a.sk;
-            if (REF || sizeof(T) == 8) {
+            if (REF && sizeof(T) != 8) {
+                for (int i0 = lane; i0 < a.nx; i0 += 32 * 4) {
+                    float x[4];
+                    double rv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const bool in = i0 + 32 * u < a.nx;
+                        x[u] = in ? (float)to_d(t[o0 + i0 + 32 * u]) : 0.0f;
+                        rv[u] = in ? a.ref[o0 + i0 + 32 * u] : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const double e = (double)x[u] - rv[u];
+                        const unsigned long long eb = (unsigned long long)__double_as_longlong(e) & kMag;
+                        const unsigned long long rbits =
+                            (unsigned long long)__double_as_longlong(rv[u]) & kMag;
+                        emax = eb > emax ? eb : emax;
+                        rmax = rbits > rmax ? rbits : rmax;
+                        v[1] = fma(e, e, v[1]);
+                        v[3] = fma(rv[u], rv[u], v[3]);
+                        ff_add(s1, x[u]);
+                    }
+                }
+            } else if (REF || sizeof(T) == 8) {
 #pragma unroll 4
                 for (int i = lane; i < a.nx; i += 32) {
                     const double tv = to_d(t[o0 + i]);
@@ -375,7 +405,7 @@ __global__ void __launch_bounds__(256) diag_kernel(DiagArgs a)
             }
             // next row; at the end of a level (or of the block) fold the level's sum
             if (++j == a.ny || r + 1 == re) {
-                const double ls = (REF || sizeof(T) == 8) ? rs : ff_value(s1);
+                const double ls = sizeof(T) == 8 ? rs : ff_value(s1);
                 v[4] += ls;
                 v[5] = fma(ls, a.wz[k], v[5]);
                 if (!(REF || sizeof(T) == 8)) v[1] += ff_value(s2);
@@ -389,6 +419,10 @@ __global__ void __launch_bounds__(256) diag_kernel(DiagArgs a)
             }
         }
         if (!(REF || sizeof(T) == 8)) v[0] = fmax(v[0], (double)tmax);
+        if (REF && sizeof(T) != 8) {
+            v[0] = fmax(v[0], __longlong_as_double((long long)emax));
+            v[2] = fmax(v[2], __longlong_as_double((long long)rmax));
+        }
     }
     reduce6(v, a.partial + 6 * (size_t)blockIdx.x);
 }

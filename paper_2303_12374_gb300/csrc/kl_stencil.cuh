@@ -39,7 +39,9 @@
 #define KL_PK 1       // zpack: packed f32x2 arithmetic for f32 compute
 #endif
 #ifndef KL_YX
-#define KL_YX 0       // zpack: exchange y faces between warps through shared memory
+#define KL_YX 0       // zpack: 1 exchange y faces between warps through shared memory
+                      // (a second barrier per level); 2 the same one level ahead
+                      // with the side and tile-top faces (one barrier per level)
 #endif
 #ifndef KL_CS
 #define KL_CS 0       // zpack: one warp group per tendency component
@@ -1199,6 +1201,50 @@ __device__ __forceinline__ V kl_npr(const char *const *npl, int lx, int row)
 }
 #endif
 
+#if KL_YX == 2
+// bottom y face of field F at tile row yr, on the level whose ring planes are
+// P (P[R] the level's plane, P[R-1] the one below): the expressions of the
+// row loop
+template <int F>
+__device__ __forceinline__ V kl_yface(const kl_vk &K, const char *const *P, int lx, int yr, V kd)
+{
+#define KL_P2(f, dk, dx, row) kl_pr<(f), (dk), (dx)>(P, lx, (row))
+    V us;
+    if constexpr (F == 0) us = vadd(vcross(KL_P2(1, 0, -2, yr), KL_P2(1, 0, 0, yr)), KL_P2(1, 0, 0, yr));
+    else if constexpr (F == 1) us = vadd(KL_P2(1, 0, 0, yr - 1), KL_P2(1, 0, 0, yr));
+    else us = vadd(KL_P2(1, -1, 0, yr), KL_P2(1, 0, 0, yr));
+    return kl_vflux(K, us, KL_A5(KL_P2(F, 0, 0, yr - 3)), KL_A5(KL_P2(F, 0, 0, yr - 2)),
+                    KL_P2(F, 0, 0, yr - 1), KL_P2(F, 0, 0, yr), KL_A5(KL_P2(F, 0, 0, yr + 1)),
+                    KL_A5(KL_P2(F, 0, 0, yr + 2)), kd);
+#undef KL_P2
+}
+
+// x face of field f beyond the tile's 64 columns at tile row `row` (u: the
+// face at centre x0-1; v, w: the face at edge x0+64), scalar, as the side
+// pass forms it
+__device__ __forceinline__ C kl_xside(const char *const *P, int f, int row, C kdx)
+{
+    const int xs = f == 0 ? KL_LPAD - 3 : KL_LPAD + 61;
+    const char *base = P[KL_R] + f * KL_PLANE_BYTES;
+    C a2 = lds((const T *)(base + KL_OFF(xs + 2, row)));
+    C a3 = lds((const T *)(base + KL_OFF(xs + 3, row)));
+#if KL_ADV == 5
+    C a0 = lds((const T *)(base + KL_OFF(xs, row)));
+    C a1 = lds((const T *)(base + KL_OFF(xs + 1, row)));
+    C a4 = lds((const T *)(base + KL_OFF(xs + 4, row)));
+    C a5 = lds((const T *)(base + KL_OFF(xs + 5, row)));
+#else
+    C a0 = C(0), a1 = C(0), a4 = C(0), a5 = C(0);
+#endif
+    const char *p1 = f == 0 ? base + KL_OFF(xs + 2, row)
+                   : (f == 1 ? P[KL_R] + KL_OFF(KL_LPAD + 64, row - 1)
+                             : P[KL_R - 1] + KL_OFF(KL_LPAD + 64, row));
+    const char *p2 = f == 0 ? base + KL_OFF(xs + 3, row) : P[KL_R] + KL_OFF(KL_LPAD + 64, row);
+    const C us = lds((const T *)p1) + lds((const T *)p2);
+    return kl_sflux(us, a0, a1, a2, a3, a4, a5, kdx);
+}
+#endif
+
 __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *const *maps,
                                               int bxi, int byi, int bzi)
 {
@@ -1219,9 +1265,16 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
 #else
     unsigned long long *bars = (unsigned long long *)(ring + KL_NS * KL_ZSLOT);
 #endif
-#if KL_YX
+#if KL_YX == 1
     // y-face exchange buffer after the barriers: [3 fields][warps][32 lanes]
     V *xbuf = (V *)((unsigned char *)bars + KL_RUP(8 * KL_NS, 16));
+#elif KL_YX == 2
+    // one level ahead, by level parity: the bottom y faces of each warp's
+    // first row [2][3][warps][32 lanes], the tile's top y faces [2][3][32]
+    // and the x faces beyond the tile's columns [2][3][TYS]
+    V *ysh = (V *)((unsigned char *)bars + KL_RUP(8 * KL_NS, 16));
+    V *ytop = ysh + 2 * 3 * KL_MBY * 32;
+    C *sside = (C *)(ytop + 2 * 3 * 32);
 #endif
     const int lane = threadIdx.x;
     const int warp = KL_CS ? (int)threadIdx.y % KL_MBY : (int)threadIdx.y;
@@ -1310,6 +1363,30 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
     const int r0 = warp * KL_MPY;                       // first row of this thread (tile local)
     const int lx = KL_LPAD + 2 * lane;                  // local x of column c0 (even)
     const int c0 = tx0 + 2 * lane;                      // global interior column of c0
+#if KL_YX == 2
+    static_assert(KL_CARRY && KL_DIFF != 2 && !KL_CS, "yx=2 needs the carried ring and constant nu");
+    // the next level's shared values, formed from its planes P: this warp's
+    // first-row bottom y faces (kept in fyb0 and published for the warp
+    // below), and, spread over the warps, the tile's x side faces and its
+    // top y faces, all by level parity
+    V fyb0[3];
+    auto publish = [&](const char *const *P, int par) {
+        fyb0[0] = kl_yface<0>(K, P, lx, r0, vkdy);
+        fyb0[1] = kl_yface<1>(K, P, lx, r0, vkdy);
+        fyb0[2] = kl_yface<2>(K, P, lx, r0, vkdy);
+#pragma unroll
+        for (int f = 0; f < 3; ++f) ysh[((par * 3 + f) * KL_MBY + warp) * 32 + lane] = fyb0[f];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            if (warp == f % KL_MBY)
+                for (int row = lane; row < KL_TYS; row += 32)
+                    sside[(par * 3 + f) * KL_TYS + row] = kl_xside(P, f, row, kdx);
+        }
+        if (warp == (KL_MBY - 1) % KL_MBY) ytop[(par * 3 + 0) * 32 + lane] = kl_yface<0>(K, P, lx, KL_TYS, vkdy);
+        if (warp == (KL_MBY + KL_MBY - 2) % KL_MBY) ytop[(par * 3 + 1) * 32 + lane] = kl_yface<1>(K, P, lx, KL_TYS, vkdy);
+        if (warp == (KL_MBY + KL_MBY - 3) % KL_MBY) ytop[(par * 3 + 2) * 32 + lane] = kl_yface<2>(K, P, lx, KL_TYS, vkdy);
+    };
+#endif
 
 #if KL_CS
     const int grp = (int)threadIdx.y / KL_MBY;           // tendency component of this warp
@@ -1372,6 +1449,9 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
             zc[r][1] = kl_pr<1, -2, 0>(pl, lx, yr);
             zc[r][2] = kl_pr<2, -2, 0>(pl, lx, yr);
         }
+#if KL_YX == 2
+        publish(pl, kb & 1);
+#endif
         __syncthreads();                            // planes kb-R, kb-R+1 read for the last time
         if (tid == 0)
             for (int t = 0; t < 2 && p_next <= p_last; ++t) issue(p_next++);
@@ -1441,6 +1521,7 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
 #endif
 
         // ---- side pass: the x face beyond the warp's columns, every row
+#if KL_YX != 2
         C extra;
         {
             int e = lane < 3 * KL_MPY ? lane : 0;
@@ -1488,9 +1569,10 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
             }
 #endif
         }
+#endif
 
         // ---- y faces
-#if KL_YX
+#if KL_YX == 1
         // every thread forms the bottom faces of its rows; the top face of
         // its last row is the bottom face of the warp above, exchanged
         // through shared memory (the last warp forms the tile's top face)
@@ -1530,6 +1612,9 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
             for (int f = 0; f < 3; ++f) fyt_last[f] = xbuf[(f * KL_MBY + warp + 1) * 32 + lane];
         }
         V fuy_b = fyb[0][0], fvy_b = fyb[0][1], fwy_b = fyb[0][2];
+#elif KL_YX == 2
+        const int par = k & 1;
+        V fuy_b = fyb0[0], fvy_b = fyb0[1], fwy_b = fyb0[2];
 #else
         V fuy_b, fvy_b, fwy_b;
         {
@@ -1589,15 +1674,20 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
             C ul_hi = __shfl_sync(0xffffffffu, vhi(fux), (lane + 31) & 31);
             C vr_lo = __shfl_sync(0xffffffffu, vlo(fvx), (lane + 1) & 31);
             C wr_lo = __shfl_sync(0xffffffffu, vlo(fwx), (lane + 1) & 31);
+#if KL_YX == 2
+            const C eu = sside[(par * 3 + 0) * KL_TYS + yr], ev = sside[(par * 3 + 1) * KL_TYS + yr],
+                    ew = sside[(par * 3 + 2) * KL_TYS + yr];
+#else
             C eu = __shfl_sync(0xffffffffu, extra, r);
             C ev = __shfl_sync(0xffffffffu, extra, KL_MPY + r);
             C ew = __shfl_sync(0xffffffffu, extra, 2 * KL_MPY + r);
+#endif
             V ul = vmk(lane == 0 ? eu : ul_hi, vlo(fux));
             V vr = vmk(vhi(fvx), lane == 31 ? ev : vr_lo);
             V wr = vmk(vhi(fwx), lane == 31 ? ew : wr_lo);
 
             // ---- top y faces of this row
-#if KL_YX
+#if KL_YX == 1
             V fuy_t, fvy_t, fwy_t;
             if (r + 1 < KL_MPY) {
                 fuy_t = fyb[r + 1 < KL_MPY ? r + 1 : 0][0];
@@ -1610,15 +1700,29 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
             }
 #else
             const int yt = yr + 1;
-            V fuy_t = kl_vflux(K, vadd(vcross(KL_Q(1, 0, -2, yt), KL_Q(1, 0, 0, yt)), KL_Q(1, 0, 0, yt)),
-                               KL_A5(KL_Q(0, 0, 0, yt - 3)), KL_A5(KL_Q(0, 0, 0, yt - 2)), KL_Q(0, 0, 0, yt - 1),
-                               KL_Q(0, 0, 0, yt), KL_A5(KL_Q(0, 0, 0, yt + 1)), KL_A5(KL_Q(0, 0, 0, yt + 2)), vkdy);
-            V fvy_t = kl_vflux(K, vadd(KL_Q(1, 0, 0, yt - 1), KL_Q(1, 0, 0, yt)),
-                               KL_A5(KL_Q(1, 0, 0, yt - 3)), KL_A5(KL_Q(1, 0, 0, yt - 2)), KL_Q(1, 0, 0, yt - 1),
-                               KL_Q(1, 0, 0, yt), KL_A5(KL_Q(1, 0, 0, yt + 1)), KL_A5(KL_Q(1, 0, 0, yt + 2)), vkdy);
-            V fwy_t = kl_vflux(K, vadd(KL_Q(1, -1, 0, yt), KL_Q(1, 0, 0, yt)),
-                               KL_A5(KL_Q(2, 0, 0, yt - 3)), KL_A5(KL_Q(2, 0, 0, yt - 2)), KL_Q(2, 0, 0, yt - 1),
-                               KL_Q(2, 0, 0, yt), KL_A5(KL_Q(2, 0, 0, yt + 1)), KL_A5(KL_Q(2, 0, 0, yt + 2)), vkdy);
+            V fuy_t, fvy_t, fwy_t;
+            if (KL_YX != 2 || r + 1 < KL_MPY) {
+                fuy_t = kl_vflux(K, vadd(vcross(KL_Q(1, 0, -2, yt), KL_Q(1, 0, 0, yt)), KL_Q(1, 0, 0, yt)),
+                                 KL_A5(KL_Q(0, 0, 0, yt - 3)), KL_A5(KL_Q(0, 0, 0, yt - 2)), KL_Q(0, 0, 0, yt - 1),
+                                 KL_Q(0, 0, 0, yt), KL_A5(KL_Q(0, 0, 0, yt + 1)), KL_A5(KL_Q(0, 0, 0, yt + 2)), vkdy);
+                fvy_t = kl_vflux(K, vadd(KL_Q(1, 0, 0, yt - 1), KL_Q(1, 0, 0, yt)),
+                                 KL_A5(KL_Q(1, 0, 0, yt - 3)), KL_A5(KL_Q(1, 0, 0, yt - 2)), KL_Q(1, 0, 0, yt - 1),
+                                 KL_Q(1, 0, 0, yt), KL_A5(KL_Q(1, 0, 0, yt + 1)), KL_A5(KL_Q(1, 0, 0, yt + 2)), vkdy);
+                fwy_t = kl_vflux(K, vadd(KL_Q(1, -1, 0, yt), KL_Q(1, 0, 0, yt)),
+                                 KL_A5(KL_Q(2, 0, 0, yt - 3)), KL_A5(KL_Q(2, 0, 0, yt - 2)), KL_Q(2, 0, 0, yt - 1),
+                                 KL_Q(2, 0, 0, yt), KL_A5(KL_Q(2, 0, 0, yt + 1)), KL_A5(KL_Q(2, 0, 0, yt + 2)), vkdy);
+            } else {
+#if KL_YX == 2
+                // the first-row bottom faces of the warp above, or the tile's
+                // top faces, formed one level earlier
+                const V *src = warp + 1 < KL_MBY ? ysh + (par * 3 * KL_MBY + warp + 1) * 32 + lane
+                                                 : ytop + par * 3 * 32 + lane;
+                const int fs = warp + 1 < KL_MBY ? KL_MBY * 32 : 32;
+                fuy_t = src[0];
+                fvy_t = src[fs];
+                fwy_t = src[2 * fs];
+#endif
+            }
 #endif
 #if KL_DIFF == 2
             V sxy_t;
@@ -1733,6 +1837,17 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
                 }
             }
         }
+#if KL_YX == 2
+        if (k + 1 < ke) {
+            // planes of level k+1: the ring's, shifted by one (its plane
+            // k+1+R, still in flight, is never read here)
+            const char *pln[2 * KL_R + 1];
+#pragma unroll
+            for (int d = 0; d < 2 * KL_R; ++d) pln[d] = pl[d + 1];
+            pln[2 * KL_R] = pl[2 * KL_R];
+            publish(pln, (k + 1) & 1);
+        }
+#endif
 #if KL_DIFF == 2
 #undef KL_N
 #undef KL_NSX

@@ -461,7 +461,7 @@ static bool valid_for(const kl_op &op, const kl_grid &g, int family, int64_t idx
 static std::vector<int> radices(int family)
 {
     if (family == 0) return {5, 5, 5, 3, 3, 3, 2, 2, 2, 2, 2, 2, 6, 6};
-    if (family == 2) return {7, 6, 7, 6, 4, 2, 2};
+    if (family == 2) return {7, 7, 7, 6, 4, 3, 2};
     return {3, 5, 3, 3, 7, 4, 4};
 }
 
@@ -498,8 +498,8 @@ static bool config_digits(const Config &c, std::vector<int> *digits)
                 {1, 2, 4}, {0, 1}, {0, 1}, {0, 1}, {0, 1}, {0, 1}, {0, 1}, {0, 1, 2, 3, 4, 5},
                 {1, 2, 3, 4, 5, 6}};
     else if (c.family == 2)
-        vals = {{1, 2, 3, 4, 6, 8, 16}, {1, 2, 3, 4, 6, 8}, {4, 8, 16, 32, 64, 128, 256},
-                {6, 7, 8, 9, 10, 12}, {1, 2, 3, 4}, {0, 1}, {0, 1}};
+        vals = {{1, 2, 3, 4, 6, 8, 16}, {1, 2, 3, 4, 5, 6, 8}, {4, 8, 16, 32, 64, 128, 256},
+                {6, 7, 8, 9, 10, 12}, {1, 2, 3, 4}, {0, 1, 2}, {0, 1}};
     else
         vals = {{32, 64, 128}, {1, 2, 4, 8, 16}, {1, 2, 4}, {1, 2, 4}, {4, 8, 16, 32, 64, 128, 256},
                 {8, 9, 10, 12}, {1, 2, 3, 4}};

@@ -53,8 +53,12 @@ def main(argv=None):
                         kl.kl_launch(ctx, op, p.grid, fl)
                     else:
                         kl.kl_launch_with_config(ctx, op, cfg, p.grid, fl)
-                for _ in range(3):
-                    launch()
+                try:
+                    for _ in range(3):
+                        launch()
+                except kl.KLError as e:          # outside the space for this problem
+                    res[cfg] = {"error": str(e)}
+                    continue
                 ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                       for _ in range(args.reps)]
                 for a, b in ev:
