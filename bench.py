@@ -448,22 +448,35 @@ def workload_sweep(ctx, device, stream, reps, peak_gbs, op_peaks):
 
 
 def diag_timing(ctx, p, outs, stream, reps=20, ins=None):
-    """kl_diag (FP64 max, rms, sums, metric-weighted sum) on one 256^3 tendency,
-    per call including the 48-byte read-back it synchronises on."""
+    """kl_diag (FP64 max, rms, sums, metric-weighted sum) on one tendency of the
+    bench grid, without and with an FP64 reference field.  Per call: `us` the
+    wall time including the 48-byte read-back it synchronises on and the host
+    round trip; `device_us` the stream time between events recorded around
+    each call (the reduction kernels and the read-back only)."""
     import torch
     from paper_2303_12374_gb300 import kl
-    out = None
-    for _ in range(3):
-        out = kl.kl_diag(ctx, p.dtype, p.grid, 0, outs[0].data_ptr(), None, stream.cuda_stream)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(reps):
-        kl.kl_diag(ctx, p.dtype, p.grid, 0, outs[0].data_ptr(), None, stream.cuda_stream)
-    b.record(stream)
-    torch.cuda.synchronize()
-    us = a.elapsed_time(b) / reps * 1e3
-    nbytes = p.nx * p.nz * p.ny * outs[0].element_size()
-    res = {"us": us, "read_gbs": nbytes / us / 1e3, "values": list(out)}
+    ref = torch.zeros(p.extent, dtype=torch.float64, device=outs[0].device)
+    p.view(ref).copy_(p.view(outs[0]).to(torch.float64) * (1.0 + 1e-6))
+    res = {}
+    for label, rp in (("no_reference", None), ("fp64_reference", ref.data_ptr())):
+        out = None
+        for _ in range(3):
+            out = kl.kl_diag(ctx, p.dtype, p.grid, 0, outs[0].data_ptr(), rp, stream.cuda_stream)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(reps)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for a, b in evs:
+            a.record(stream)
+            kl.kl_diag(ctx, p.dtype, p.grid, 0, outs[0].data_ptr(), rp, stream.cuda_stream)
+            b.record(stream)
+        wall = (time.perf_counter() - t0) / reps * 1e6
+        torch.cuda.synchronize()
+        dev = statistics.fmean(a.elapsed_time(b) for a, b in evs) * 1e3
+        nbytes = p.nx * p.nz * p.ny * (outs[0].element_size() + (8 if rp else 0))
+        res[label] = {"us": wall, "device_us": dev, "read_gbs_device": nbytes / dev / 1e3,
+                      "values": list(out)}
+    del ref
     if ins is not None:
         # kinetic-energy tendency of the step (three FP64 inner products)
         t0 = time.perf_counter()

@@ -77,6 +77,8 @@ kl_status driver_load(Driver *d)
         {"cuModuleGetFunction", (void **)&d->ModuleGetFunction},
         {"cuLaunchKernel", (void **)&d->LaunchKernel},
         {"cuFuncSetAttribute", (void **)&d->FuncSetAttribute},
+        {"cuOccupancyMaxActiveBlocksPerMultiprocessor",
+         (void **)&d->OccupancyMaxActiveBlocksPerMultiprocessor},
         {"cuFuncGetAttribute", (void **)&d->FuncGetAttribute},
         {"cuTensorMapEncodeTiled", (void **)&d->TensorMapEncodeTiled},
     };
@@ -547,9 +549,20 @@ kl_status launch_config(kl_ctx *ctx, const kl_op &op, const Config &cfg, const k
         if (a.nby > 65535 || a.nbz > 65535) return fail(KL_ERR_UNSUPPORTED, "grid too large");
         // zmarch takes the first four descriptors, zpack all seven
         void *params[] = {&a, &maps[0], &maps[1], &maps[2], &maps[3], &maps[4], &maps[5], &maps[6]};
-        r = ctx->drv.LaunchKernel(k->fn, (unsigned)a.nbx, (unsigned)a.nby, (unsigned)a.nbz,
-                                  cfg.mbx, zmarch_block_y(cfg), 1, (unsigned)k->smem, (CUstream)s, params,
-                                  nullptr);
+        unsigned gx = (unsigned)a.nbx, gy = (unsigned)a.nby, gz = (unsigned)a.nbz;
+        if (cfg.family == 2 && cfg.pe) {
+            // persistent: as many CTAs as fit on the device at once, each
+            // taking an equal range of the (tile, level) pairs
+            int per_sm = 0;
+            r = ctx->drv.OccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, k->fn, cfg.mbx * zmarch_block_y(cfg), k->smem);
+            if (r != CUDA_SUCCESS) return cu_fail(r, "cuOccupancyMaxActiveBlocksPerMultiprocessor");
+            const long long pairs = a.nbx * a.nby * g.nz;
+            gx = (unsigned)std::max(1LL, std::min<long long>(pairs, (long long)std::max(1, per_sm) * ctx->nsm));
+            gy = gz = 1;
+        }
+        r = ctx->drv.LaunchKernel(k->fn, gx, gy, gz, cfg.mbx, zmarch_block_y(cfg), 1, (unsigned)k->smem,
+                                  (CUstream)s, params, nullptr);
     }
     if (r != CUDA_SUCCESS) return cu_fail(r, "cuLaunchKernel");
     if (miss) ctx->t_launch_ms += ms_since(t_launch);

@@ -30,8 +30,8 @@ std::string config_string(const Config &c)
         snprintf(b, sizeof b, "zmarch:bx=%d,by=%d,px=%d,py=%d,kc=%d,ns=%d,minb=%d", c.mbx, c.mby,
                  c.mpx, c.mpy, c.kc, c.ns, c.mminb);
     } else {
-        snprintf(b, sizeof b, "zpack:w=%d,ly=%d,kc=%d,ns=%d,minb=%d,yx=%d,pk=%d,cs=%d", c.mby,
-                 c.mpy, c.kc, c.ns, c.mminb, c.yx, c.pk, c.cs);
+        snprintf(b, sizeof b, "zpack:w=%d,ly=%d,kc=%d,ns=%d,minb=%d,yx=%d,pk=%d,cs=%d%s", c.mby,
+                 c.mpy, c.kc, c.ns, c.mminb, c.yx, c.pk, c.cs, c.pe ? ",pe=1" : "");
     }
     return b;
 }
@@ -107,6 +107,7 @@ bool config_parse(const std::string &text, Config *c, std::string *err)
             else if (k == "yx") dst = &c->yx;
             else if (k == "pk") dst = &c->pk;
             else if (k == "cs") dst = &c->cs;
+            else if (k == "pe") dst = &c->pe;
             else if (k == "kc") dst = &c->kc; else if (k == "ns") dst = &c->ns;
             else if (k == "minb") dst = &c->mminb;
         } else {
@@ -214,14 +215,15 @@ bool config_check(const kl_op &op, const Config &c, std::string *err)
             *err = "zmarch parameter outside the space";
             return false;
         }
-        if (c.family == 2 && (c.mbx != 32 || c.mpx != 2 || !in(c.mby, {1, 2, 3, 4, 6, 8, 16}) ||
+        if (c.family == 2 && (c.mbx != 32 || c.mpx != 2 || !in(c.mby, {1, 2, 3, 4, 6, 7, 8, 9, 16}) ||
                               !in(c.mpy, {1, 2, 3, 4, 5, 6, 8}))) {
             *err = "zpack parameter outside the space (w 1..16, ly 1..8)";
             return false;
         }
         if (c.family == 2 &&
-            ((c.yx < 0 || c.yx > 2) || (c.pk != 0 && c.pk != 1) || (c.cs != 0 && c.cs != 1))) {
-            *err = "yx must be 0..2, pk and cs 0 or 1";
+            ((c.yx < 0 || c.yx > 2) || (c.pk != 0 && c.pk != 1) || (c.cs != 0 && c.cs != 1) ||
+             (c.pe != 0 && c.pe != 1))) {
+            *err = "yx must be 0..2, pk, cs and pe 0 or 1";
             return false;
         }
         if (c.family == 2 && c.cs && c.yx) {
@@ -281,13 +283,13 @@ static const int kBX[] = {16, 32, 64, 128, 256}, kBYZ[] = {1, 2, 4, 8, 16}, kT[]
 static const int kMBX[] = {32, 64, 128}, kMBY[] = {1, 2, 4, 8, 16}, kMP[] = {1, 2, 4},
                  kKC[] = {4, 8, 16, 32, 64, 128, 256}, kNS[] = {8, 9, 10, 12};
 
-static const int kW[] = {1, 2, 3, 4, 6, 8, 16}, kLY[] = {1, 2, 3, 4, 5, 6, 8}, kNSP[] = {6, 7, 8, 9, 10, 12};
+static const int kW[] = {1, 2, 3, 4, 6, 7, 8, 9, 16}, kLY[] = {1, 2, 3, 4, 5, 6, 8}, kNSP[] = {6, 7, 8, 9, 10, 12};
 
 int64_t space_size(int family)
 {
     if (family == 0) return 5LL * 5 * 5 * 27 * 8 * 8 * 6 * 6;
     if (family == 1) return 3LL * 5 * 3 * 3 * 7 * 4 * 4;
-    if (family == 2) return 7LL * 7 * 7 * 6 * 4 * 3 * 2;
+    if (family == 2) return 9LL * 7 * 7 * 6 * 4 * 3 * 2 * 2;
     return 0;
 }
 
@@ -315,13 +317,14 @@ bool space_config(int family, int64_t idx, Config *c)
     } else if (family == 2) {
         c->mbx = 32;
         c->mpx = 2;
-        c->mby = kW[take(7)];
+        c->mby = kW[take(9)];
         c->mpy = kLY[take(7)];
         c->kc = kKC[take(7)];
         c->ns = kNSP[take(6)];
         c->mminb = 1 + take(4);
         c->yx = take(3);
         c->cs = take(2);
+        c->pe = take(2);
     } else {
         c->mbx = kMBX[take(3)];
         c->mby = kMBY[take(5)];
@@ -448,13 +451,17 @@ int wisdom_select(const std::vector<WisdomRecord> &recs, const std::string &devi
         *config = exact->config;
         return 1;
     }
+    // nearest problem size; records of one size (several tuning sessions)
+    // compete as in rule 1 (the fastest, ties to the newest), different
+    // sizes at the same distance go by file order
     auto nearest = [&](auto pred) -> const WisdomRecord * {
         const WisdomRecord *best = nullptr;
         double bd = 0;
         for (const WisdomRecord &r : recs) {
             if (r.zbc != zbc || !pred(r)) continue;
             double d = dist(r);
-            if (!best || d < bd) {
+            const bool same_size = best && r.nx == best->nx && r.ny == best->ny && r.nz == best->nz;
+            if (!best || d < bd || (same_size && r.time_us <= best->time_us)) {
                 best = &r;
                 bd = d;
             }
@@ -536,9 +543,9 @@ std::string compile_defines(const kl_op &op, const Config &c, int zbc, int zuni)
     } else {
         snprintf(b + n, sizeof b - n,
                  " -DKL_MBX=%d -DKL_MBY=%d -DKL_MPX=%d -DKL_MPY=%d -DKL_KC=%d -DKL_NS=%d"
-                 " -DKL_MMINB=%d -DKL_YX=%d -DKL_PK=%d -DKL_CS=%d",
+                 " -DKL_MMINB=%d -DKL_YX=%d -DKL_PK=%d -DKL_CS=%d -DKL_PE=%d",
                  c.mbx, c.mby, c.mpx, c.mpy, c.kc, c.ns, c.mminb, c.family == 2 ? c.yx : 0,
-                 c.family == 2 ? c.pk : 1, c.family == 2 ? c.cs : 0);
+                 c.family == 2 ? c.pk : 1, c.family == 2 ? c.cs : 0, c.family == 2 ? c.pe : 0);
     }
     return b;
 }

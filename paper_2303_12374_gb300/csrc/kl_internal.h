@@ -40,6 +40,7 @@ struct Config {
     int yx = 0;                // zpack: exchange y faces between warps (shared memory)
     int pk = 1;                // zpack: packed f32x2 arithmetic (f32 compute)
     int cs = 0;                // zpack: one warp group per tendency component (3 x w warps)
+    int pe = 0;                // zpack: persistent CTAs over (tile, level) ranges
 };
 
 // default deadline of one device wait, SM clock cycles (about a second)
@@ -123,6 +124,7 @@ struct Driver {
     CUresult (*LaunchKernel)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned,
                              unsigned, unsigned, CUstream, void **, void **) = nullptr;
     CUresult (*FuncSetAttribute)(CUfunction, CUfunction_attribute, int) = nullptr;
+    CUresult (*OccupancyMaxActiveBlocksPerMultiprocessor)(int *, CUfunction, int, size_t) = nullptr;
     CUresult (*FuncGetAttribute)(int *, CUfunction_attribute, CUfunction) = nullptr;
     CUresult (*TensorMapEncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                      const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,

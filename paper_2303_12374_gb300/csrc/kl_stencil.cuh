@@ -46,6 +46,9 @@
 #ifndef KL_CS
 #define KL_CS 0       // zpack: one warp group per tendency component
 #endif
+#ifndef KL_PE
+#define KL_PE 0       // zpack: persistent CTAs over ranges of (tile, level) pairs
+#endif
 #if KL_CS && KL_YX
 #error "KL_CS forms every y face in its own warp group; KL_YX must be 0"
 #endif
@@ -1245,8 +1248,12 @@ __device__ __forceinline__ C kl_xside(const char *const *P, int f, int row, C kd
 }
 #endif
 
-__device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *const *maps,
-                                              int bxi, int byi, int bzi)
+// One tile (bxi, byi) over levels [kb, ke): the ring's prologue, then the
+// level loop.  reinit: the ring's mbarriers were used by an earlier segment
+// of the same CTA (all of their copies completed); they are invalidated and
+// initialised again.  Returns false when a device wait gave up.
+__device__ __forceinline__ bool kl_zpack_body(const kl_args &a, const kl_tmap *const *maps,
+                                              int bxi, int byi, int kb, int ke, bool reinit)
 {
     static_assert(KL_MBX == 32 && KL_MPX == 2, "zpack tiles are 64 columns wide");
     static_assert(3 * KL_MPY <= 32, "side pass needs 3 x rows <= 32 lanes");
@@ -1280,13 +1287,14 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
     const int warp = KL_CS ? (int)threadIdx.y % KL_MBY : (int)threadIdx.y;
     const int tid = lane + 32 * (int)threadIdx.y;
     const int nx = (int)a.nx, ny = (int)a.ny, nz = (int)a.nz;
-    const int kb = bzi * (int)a.kchunk;
-    const int ke = min(kb + (int)a.kchunk, nz);
     const int tx0 = bxi * 64, ty0 = byi * KL_TYS;
     const int gx = (int)a.tile_x0 + tx0 - KL_LPAD, gy = (int)a.tile_y0 + ty0 - KL_H;
     const int gz0 = (int)a.tile_z0;
 
     if (tid == 0) {
+        if (reinit)
+            for (int s = 0; s < KL_NS; ++s)
+                asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(kl_smem_addr(&bars[s])) : "memory");
         for (int s = 0; s < KL_NS; ++s) kl_mbar_init(kl_smem_addr(&bars[s]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1879,6 +1887,7 @@ __device__ __forceinline__ void kl_zpack_body(const kl_args &a, const kl_tmap *c
         }
         __syncthreads();
     }
+    return !timed_out;
 }
 
 #if KL_BATCH
@@ -1892,7 +1901,8 @@ kl_tendency(const kl_args *argv, const int4 *blocks, const kl_tmap *tmaps)
     if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int f = 0; f < 7; ++f)
             if (f != 3) kl_tmap_acquire(maps[f]);
-    kl_zpack_body(a, maps, d.y, d.z, d.w);
+    const int kb = d.w * (int)a.kchunk;
+    kl_zpack_body(a, maps, d.y, d.z, kb, min(kb + (int)a.kchunk, (int)a.nz), false);
 }
 #else
 extern "C" __global__ void __launch_bounds__(32 * KL_MBY * (KL_CS ? 3 : 1), KL_MMINB)
@@ -1903,7 +1913,33 @@ kl_tendency(const kl_args a, const __grid_constant__ kl_tmap tm_u,
 {
     // tm_su .. tm_sw: the same fields with the 32-byte x-wrap strip box
     const kl_tmap *maps[7] = {&tm_u, &tm_v, &tm_w, &tm_n, &tm_su, &tm_sv, &tm_sw};
-    kl_zpack_body(a, maps, blockIdx.x, blockIdx.y, blockIdx.z);
+#if KL_PE
+    // persistent CTAs: CTA b takes the b-th of gridDim.x nearly equal,
+    // contiguous ranges of the (tile, level) pairs, tiles x fastest and each
+    // tile's levels consecutive.  It marches one tile column upwards and
+    // crosses to the next tile only where its range does, so the plane ring's
+    // prologue (and the re-read of the planes below a z chunk) happens about
+    // once per CTA instead of once per chunk, and every CTA gets the same
+    // number of levels (no partial last wave).
+    const long long ntl = a.nbx * a.nby * a.nz;
+    const long long per = (ntl + gridDim.x - 1) / gridDim.x;
+    long long i = (long long)blockIdx.x * per;
+    const long long end = ntl < i + per ? ntl : i + per;
+    bool first = true;
+    while (i < end) {
+        const long long t = i / a.nz;
+        const int k0 = (int)(i - t * a.nz);
+        const long long left = end - i;
+        const int k1 = left < a.nz - k0 ? k0 + (int)left : (int)a.nz;
+        if (!first) __syncthreads();               // the last segment's ring is idle
+        if (!kl_zpack_body(a, maps, (int)(t % a.nbx), (int)(t / a.nbx), k0, k1, !first)) break;
+        first = false;
+        i += k1 - k0;
+    }
+#else
+    const int kb = (int)blockIdx.z * (int)a.kchunk;
+    kl_zpack_body(a, maps, blockIdx.x, blockIdx.y, kb, min(kb + (int)a.kchunk, (int)a.nz), false);
+#endif
 }
 #endif
 #endif  // KL_FAMILY == 2

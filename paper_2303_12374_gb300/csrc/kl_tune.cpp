@@ -461,7 +461,7 @@ static bool valid_for(const kl_op &op, const kl_grid &g, int family, int64_t idx
 static std::vector<int> radices(int family)
 {
     if (family == 0) return {5, 5, 5, 3, 3, 3, 2, 2, 2, 2, 2, 2, 6, 6};
-    if (family == 2) return {7, 7, 7, 6, 4, 3, 2};
+    if (family == 2) return {9, 7, 7, 6, 4, 3, 2, 2};
     return {3, 5, 3, 3, 7, 4, 4};
 }
 
@@ -498,14 +498,14 @@ static bool config_digits(const Config &c, std::vector<int> *digits)
                 {1, 2, 4}, {0, 1}, {0, 1}, {0, 1}, {0, 1}, {0, 1}, {0, 1}, {0, 1, 2, 3, 4, 5},
                 {1, 2, 3, 4, 5, 6}};
     else if (c.family == 2)
-        vals = {{1, 2, 3, 4, 6, 8, 16}, {1, 2, 3, 4, 5, 6, 8}, {4, 8, 16, 32, 64, 128, 256},
-                {6, 7, 8, 9, 10, 12}, {1, 2, 3, 4}, {0, 1, 2}, {0, 1}};
+        vals = {{1, 2, 3, 4, 6, 7, 8, 9, 16}, {1, 2, 3, 4, 5, 6, 8}, {4, 8, 16, 32, 64, 128, 256},
+                {6, 7, 8, 9, 10, 12}, {1, 2, 3, 4}, {0, 1, 2}, {0, 1}, {0, 1}};
     else
         vals = {{32, 64, 128}, {1, 2, 4, 8, 16}, {1, 2, 4}, {1, 2, 4}, {4, 8, 16, 32, 64, 128, 256},
                 {8, 9, 10, 12}, {1, 2, 3, 4}};
     std::vector<int> cur = c.family == 0
         ? std::vector<int>{c.bx, c.by, c.bz, c.tx, c.ty, c.tz, c.ux, c.uy, c.uz, c.cx, c.cy, c.cz, c.perm, c.minb}
-        : c.family == 2 ? std::vector<int>{c.mby, c.mpy, c.kc, c.ns, c.mminb, c.yx, c.cs}
+        : c.family == 2 ? std::vector<int>{c.mby, c.mpy, c.kc, c.ns, c.mminb, c.yx, c.cs, c.pe}
                         : std::vector<int>{c.mbx, c.mby, c.mpx, c.mpy, c.kc, c.ns, c.mminb};
     digits->resize(vals.size());
     for (size_t p = 0; p < vals.size(); ++p) {
@@ -517,11 +517,11 @@ static bool config_digits(const Config &c, std::vector<int> *digits)
 }
 
 // Surrogate features of a configuration: a one-hot of the family (3 values),
-// then one block per family (14 direct, 7 zmarch, 7 zpack digits), the
+// then one block per family (14 direct, 7 zmarch, 8 zpack digits), the
 // configuration's own block holding each digit scaled to [0, 1] and the others
 // zero.  The value lists of the space are ordered (powers of two, counts), so
 // neighbouring digits are neighbouring settings.
-static const int kFeatDims = 3 + 14 + 7 + 7;
+static const int kFeatDims = 3 + 14 + 7 + 8;
 
 static bool config_features(const Config &c, double *f)
 {

@@ -40,6 +40,12 @@ CONFIGS_DIRECT = [
     "zpack:w=4,ly=3,kc=8,ns=6,minb=1,yx=2",
     "zpack:w=3,ly=2,kc=4,ns=7,minb=1,yx=2",
     "zpack:w=1,ly=1,kc=16,ns=6,minb=1,yx=2",
+    # persistent CTAs over (tile, level) ranges (segments start mid-column)
+    "zpack:w=4,ly=3,kc=8,ns=6,minb=2,pe=1",
+    "zpack:w=2,ly=2,kc=8,ns=8,minb=1,yx=1,pe=1",
+    "zpack:w=2,ly=4,kc=4,ns=9,minb=1,cs=1,pe=1",
+    "zpack:w=9,ly=3,kc=256,ns=7,minb=1",
+    "zpack:w=7,ly=4,kc=16,ns=6,minb=1,pe=1",
 ]
 
 
@@ -138,13 +144,14 @@ def test_carried_plane_ring_is_bit_identical(ctx, dtype, walls, adv):
     """A ring of 2R slots (plane k-2 carried in registers, the first level's
     bottom faces formed before the level loop) gives the same bits as the
     2R+2-slot ring, and so do the y, side and top faces formed one level
-    ahead (yx=2): the same values enter the same expressions."""
+    ahead (yx=2) and persistent CTAs whose segments start and end anywhere in
+    a column (pe=1): the same values enter the same expressions."""
     f = make_inputs(131, 45, 23, seed=12, walls=walls, stretch=2.0)
     res = []
-    for ns, yx in ((8, 0), (6, 0), (6, 2), (7, 2)):
+    for ns, yx, pe in ((8, 0, 0), (6, 0, 0), (6, 2, 0), (7, 2, 0), (6, 0, 1), (8, 0, 1), (6, 2, 1)):
         if yx == 2 and adv != 5:
             continue
-        cfg = f"zpack:w=2,ly=2,kc=8,ns={ns},minb=1,yx={yx}"
+        cfg = f"zpack:w=2,ly=2,kc=8,ns={ns},minb=1,yx={yx},pe={pe}"
         p, _, outs, _ = run_gpu(ctx, f, adv=adv, diff=1, dtype=dtype, walls=walls,
                                 g=3 if adv == 5 else 1, stretched=True, config=cfg)
         res.append([p.download(outs[k]) for k in ("ut", "vt", "wt")])
@@ -171,7 +178,8 @@ def test_zpack_x_wrap_in_kernel(ctx, oracle_mod, dtype, nx, ny, nz, walls, adv):
     wraps = nx >= 64 + g
     f = make_inputs(nx, ny, nz, seed=nx + ny, walls=walls, stretch=2.0)
     for cfg in ("zpack:w=2,ly=2,kc=4,ns=8,minb=1", "zpack:w=4,ly=2,kc=16,ns=9,minb=1,cs=1",
-                "zpack:w=6,ly=2,kc=4,ns=6,minb=2", "zpack:w=4,ly=3,kc=4,ns=6,minb=1,yx=2"):
+                "zpack:w=6,ly=2,kc=4,ns=6,minb=2", "zpack:w=4,ly=3,kc=4,ns=6,minb=1,yx=2",
+                "zpack:w=4,ly=2,kc=4,ns=6,minb=2,pe=1"):
         try:
             kl.kl_config_normalize(kl.Op(adv, 1, dtype, 0), cfg)
         except kl.KLError:

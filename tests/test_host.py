@@ -162,7 +162,8 @@ def test_wisdom_rules(tmp_path):
     assert sel("GPU A", (10, 3), 1, (256, 256, 256)) == ("direct:bx=32,by=2", 1)
     # rule 2: same device, nearest size
     assert sel("GPU A", (10, 3), 1, (500, 500, 250)) == ("direct:bx=64", 2)
-    assert sel("GPU A", (10, 3), 1, (300, 300, 300)) == ("direct:bx=32", 2)
+    # ... where the nearest size has two sessions, they compete as in rule 1
+    assert sel("GPU A", (10, 3), 1, (300, 300, 300)) == ("direct:bx=32,by=2", 2)
     # zbc never crosses
     assert sel("GPU A", (10, 3), 0, (512, 512, 256)) == ("direct:by=2", 2)
     # rule 3: other device, same architecture, nearest size
@@ -180,6 +181,15 @@ def test_wisdom_duplicates_fastest_session_wins(tmp_path):
                rec("G", "10.3", 0, (64, 64, 64), "direct:bx=32").replace("time_us=1.0", "time_us=3.0"),
                rec("G", "10.3", 0, (64, 64, 64), "direct:bx=64").replace("time_us=1.0", "time_us=5.0")])
     assert kl.kl_wisdom_select(p, "G", 10, 3, 0, 64, 64, 64) == ("direct:bx=32", 1)
+
+
+def test_wisdom_nearest_size_takes_its_fastest_session(tmp_path):
+    p = str(tmp_path / "w.wisdom")
+    _write(p, [rec("G", "10.3", 0, (64, 64, 64), "direct:bx=16").replace("time_us=1.0", "time_us=9.0"),
+               rec("G", "10.3", 0, (256, 256, 256), "direct:bx=128"),
+               rec("G", "10.3", 0, (64, 64, 64), "direct:bx=32").replace("time_us=1.0", "time_us=3.0"),
+               rec("G", "10.3", 0, (64, 64, 64), "direct:bx=64").replace("time_us=1.0", "time_us=5.0")])
+    assert kl.kl_wisdom_select(p, "G", 10, 3, 0, 70, 60, 64) == ("direct:bx=32", 2)
 
 
 def test_wisdom_distance_tie_takes_first_record(tmp_path):
