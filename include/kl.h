@@ -327,7 +327,12 @@ kl_status kl_diag_noalloc(int32_t dtype, const kl_grid *grid, const void *t, con
  * aliasing them) gets the interior, and with fill_ghosts != 0 also its ghost
  * cells by the rules of kl_fill_ghosts (even mirror at walls).  Arithmetic
  * in f64 for f64 storage, else f32.  KL_ERR_INVALID_ARG for NULL or
- * misaligned fields, a bad dtype or a negative or non-finite cs.
+ * misaligned fields, a bad dtype or a negative or non-finite cs.  The
+ * context keeps one device table of delta_k^2 per vertical grid (dz profile,
+ * dx, dy); cs is a kernel argument and creates none.  The first call for a
+ * grid allocates its table (cudaMalloc) and uploads it synchronously, so make
+ * it before any stream capture; later calls on that grid allocate nothing.
+ * Tables are freed by kl_destroy.
  */
 kl_status kl_smagorinsky(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, double cs,
                          const void *u, const void *v, const void *w, void *nu,

@@ -945,13 +945,15 @@ kl_status kl_smagorinsky(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, double
     Profile *prof = nullptr;
     st = get_profile(ctx, *grid, &prof);
     if (st) return st;
-    // (cs delta_k)^2 per level, f64 then f32, one table per z grid, dx, dy and cs
+    // delta_k^2 per level, f64 then f32, one table per z grid, dx and dy (cs
+    // enters as a kernel argument, so a new cs creates no table): the first
+    // call on a grid allocates its table and uploads it synchronously
     std::vector<double> dzi, dzhi;
     zprofile_host(grid->nz, grid->g, grid->zbc, grid->zh, grid->dz, &dzi, &dzhi);
     std::vector<double> c64((size_t)grid->nz);
     for (int k = 0; k < grid->nz; ++k) {
-        const double cd = cs * std::cbrt(grid->dx * grid->dy / dzi[(size_t)(k + grid->g)]);
-        c64[(size_t)k] = cd * cd;
+        const double d = std::cbrt(grid->dx * grid->dy / dzi[(size_t)(k + grid->g)]);
+        c64[(size_t)k] = d * d;
     }
     std::string key = "smag:" + std::to_string(fnv1a(c64.data(), c64.size() * sizeof(double)));
     auto it = ctx->tables.find(key);
@@ -974,7 +976,8 @@ kl_status kl_smagorinsky(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, double
     const double *cc64 = (const double *)it->second.first;
     const float *cc32 = (const float *)(cc64 + grid->nz);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = smag_launch(dtype, *grid, u, v, w, nu, prof->d64, prof->d32, prof->n, cc64, cc32, s);
+    cudaError_t e = smag_launch(dtype, *grid, u, v, w, nu, prof->d64, prof->d32, prof->n, cc64, cc32,
+                                cs * cs, s);
     if (e != cudaSuccess) return cuda_fail(e, "smagorinsky launch");
     ctx->launches++;
     if (fill_ghosts) {

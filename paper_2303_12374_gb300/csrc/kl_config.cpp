@@ -31,7 +31,8 @@ std::string config_string(const Config &c)
                  c.mpx, c.mpy, c.kc, c.ns, c.mminb);
     } else {
         snprintf(b, sizeof b, "zpack:w=%d,ly=%d,kc=%d,ns=%d,minb=%d,yx=%d,pk=%d,cs=%d%s", c.mby,
-                 c.mpy, c.kc, c.ns, c.mminb, c.yx, c.pk, c.cs, c.pe ? ",pe=1" : "");
+                 c.mpy, c.kc, c.ns, c.mminb, c.yx, c.pk, c.cs,
+                 c.pe == 1 ? ",pe=1" : c.pe == 2 ? ",pe=2" : "");
     }
     return b;
 }
@@ -222,8 +223,8 @@ bool config_check(const kl_op &op, const Config &c, std::string *err)
         }
         if (c.family == 2 &&
             ((c.yx < 0 || c.yx > 2) || (c.pk != 0 && c.pk != 1) || (c.cs != 0 && c.cs != 1) ||
-             (c.pe != 0 && c.pe != 1))) {
-            *err = "yx must be 0..2, pk, cs and pe 0 or 1";
+             (c.pe < 0 || c.pe > 2))) {
+            *err = "yx and pe must be 0..2, pk and cs 0 or 1";
             return false;
         }
         if (c.family == 2 && c.cs && c.yx) {
@@ -289,7 +290,7 @@ int64_t space_size(int family)
 {
     if (family == 0) return 5LL * 5 * 5 * 27 * 8 * 8 * 6 * 6;
     if (family == 1) return 3LL * 5 * 3 * 3 * 7 * 4 * 4;
-    if (family == 2) return 9LL * 7 * 7 * 6 * 4 * 3 * 2 * 2;
+    if (family == 2) return 9LL * 7 * 7 * 6 * 4 * 3 * 2 * 3;
     return 0;
 }
 
@@ -324,7 +325,7 @@ bool space_config(int family, int64_t idx, Config *c)
         c->mminb = 1 + take(4);
         c->yx = take(3);
         c->cs = take(2);
-        c->pe = take(2);
+        c->pe = take(3);
     } else {
         c->mbx = kMBX[take(3)];
         c->mby = kMBY[take(5)];

@@ -819,8 +819,9 @@ struct SmagArgs {
     void *nu;
     const double *dzi64, *dzhi64;          // index k + g
     const float *dzi32, *dzhi32;
-    const double *cc64;                    // (cs delta_k)^2, index k
+    const double *cc64;                    // delta_k^2, index k
     const float *cc32;
+    double cs2;                            // cs^2
     long long sj, sk;
     int nx, ny, nz, g, kc;
     double dxi, dyi;
@@ -895,7 +896,7 @@ __global__ void __launch_bounds__(SMAG_BX * SMAG_BY) smag_kernel(SmagArgs a)
         s2 += e00 * e00 + e10 * e10 + e01 * e01 + e11 * e11;
         s2 += exz0 * exz0 + exz1 * exz1 + exz0n * exz0n + exz1n * exz1n;
         s2 += eyz0 * eyz0 + eyz1 * eyz1 + eyz0n * eyz0n + eyz1n * eyz1n;
-        const C cc = sizeof(C) == 8 ? (C)a.cc64[k] : (C)a.cc32[k];
+        const C cc = (C)a.cs2 * (sizeof(C) == 8 ? (C)a.cc64[k] : (C)a.cc32[k]);
         const C val = cc * sqrt(s2);
         if (sizeof(C) == 8) ((double *)nu)[o] = (double)val;
         else stf<T>(nu + o, (float)val);
@@ -1049,7 +1050,7 @@ __global__ void __launch_bounds__(SMAG_BX * SMAG_BY, sizeof(C) == 8 ? 1 : 3) sma
             EYZ0n[q] = half * ((V0n[q] - V0[q]) * zi + (Wn[q] - Wjm[q]) * dyi);
             EYZ1n[q] = half * ((V1n[q] - V1[q]) * zi + (Wjp[q] - Wn[q]) * dyi);
         }
-        const C cc = sizeof(C) == 8 ? (C)a.cc64[k] : (C)a.cc32[k];
+        const C cc = (C)a.cs2 * (sizeof(C) == 8 ? (C)a.cc64[k] : (C)a.cc32[k]);
         C out[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -1084,11 +1085,12 @@ namespace kl {
 
 cudaError_t smag_launch(int dtype, const kl_grid &g, const void *u, const void *v, const void *w,
                         void *nu, const double *d64, const float *d32, int nprof,
-                        const double *cc64, const float *cc32, cudaStream_t s)
+                        const double *cc64, const float *cc32, double cs2, cudaStream_t s)
 {
     const int es = esize_of(dtype);
     const size_t off = (size_t)g.origin * es;
     SmagArgs a;
+    a.cs2 = cs2;
     a.u = (const char *)u + off;
     a.v = (const char *)v + off;
     a.w = (const char *)w + off;

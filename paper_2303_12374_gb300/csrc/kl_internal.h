@@ -265,7 +265,7 @@ cudaError_t compare_launch(int dtype, const kl_grid &g, const void *a, const voi
 // Smagorinsky viscosity at the interior cell centres (profile arrays of get_profile)
 cudaError_t smag_launch(int dtype, const kl_grid &g, const void *u, const void *v, const void *w,
                         void *nu, const double *d64, const float *d32, int nprof,
-                        const double *cc64, const float *cc32, cudaStream_t s);
+                        const double *cc64, const float *cc32, double cs2, cudaStream_t s);
 // load a compiled cubin into the context's cache under its compile key
 kl_status load_compiled(kl_ctx *ctx, const kl_op &op, const Config &cfg, const std::string &key,
                         const Compiled &c, Kernel **out);

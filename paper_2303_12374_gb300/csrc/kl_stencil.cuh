@@ -1914,27 +1914,51 @@ kl_tendency(const kl_args a, const __grid_constant__ kl_tmap tm_u,
     // tm_su .. tm_sw: the same fields with the 32-byte x-wrap strip box
     const kl_tmap *maps[7] = {&tm_u, &tm_v, &tm_w, &tm_n, &tm_su, &tm_sv, &tm_sw};
 #if KL_PE
-    // persistent CTAs: CTA b takes the b-th of gridDim.x nearly equal,
-    // contiguous ranges of the (tile, level) pairs, tiles x fastest and each
-    // tile's levels consecutive.  It marches one tile column upwards and
-    // crosses to the next tile only where its range does, so the plane ring's
-    // prologue (and the re-read of the planes below a z chunk) happens about
-    // once per CTA instead of once per chunk, and every CTA gets the same
-    // number of levels (no partial last wave).
-    const long long ntl = a.nbx * a.nby * a.nz;
-    const long long per = (ntl + gridDim.x - 1) / gridDim.x;
-    long long i = (long long)blockIdx.x * per;
-    const long long end = ntl < i + per ? ntl : i + per;
+    // Persistent CTAs.  A range [i, end) of a space of (tile, level) pairs,
+    // tiles x fastest and each tile's levels lev0 .. lev0+nlev-1 consecutive,
+    // runs as segments of consecutive levels of one tile: the plane ring's
+    // prologue (and the re-read of the planes below a z chunk) happens once
+    // per segment instead of once per chunk.
     bool first = true;
-    while (i < end) {
-        const long long t = i / a.nz;
-        const int k0 = (int)(i - t * a.nz);
-        const long long left = end - i;
-        const int k1 = left < a.nz - k0 ? k0 + (int)left : (int)a.nz;
-        if (!first) __syncthreads();               // the last segment's ring is idle
-        if (!kl_zpack_body(a, maps, (int)(t % a.nbx), (int)(t / a.nbx), k0, k1, !first)) break;
-        first = false;
-        i += k1 - k0;
+    auto run = [&](long long i, long long end, int nlev, int lev0) {
+        while (i < end) {
+            const long long t = i / nlev;
+            const int k0 = (int)(i - t * nlev);
+            const long long left = end - i;
+            const int k1 = left < nlev - k0 ? k0 + (int)left : nlev;
+            if (!first) __syncthreads();           // the last segment's ring is idle
+            if (!kl_zpack_body(a, maps, (int)(t % a.nbx), (int)(t / a.nbx), lev0 + k0, lev0 + k1, !first))
+                return false;
+            first = false;
+            i += k1 - k0;
+        }
+        return true;
+    };
+    const long long G = gridDim.x, ntile = a.nbx * a.nby, nz = a.nz;
+    if (KL_PE == 2 && G > ntile) {
+        // column-synchronous: CTA b < ntile marches tile b from level 0 to h,
+        // so that these CTAs climb their columns together and a tile's halo
+        // rows (its neighbours' rows of the same level) are read at about the
+        // same time by both (the L2 keeps them); the other CTAs share the
+        // levels h .. nz-1 of every tile in equal ranges.  h balances the two
+        // kinds, counting about two levels of work for each ring prologue.
+        const long long ne = G - ntile;
+        const long long nseg = (ntile + ne - 1) / ne + 1;
+        long long h = (ntile * nz + 2 * ne * (nseg - 1)) / G;
+        h = h < 1 ? 1 : (h > nz ? nz : h);
+        if ((long long)blockIdx.x < ntile) {
+            run((long long)blockIdx.x * h, (long long)blockIdx.x * h + h, (int)h, 0);
+        } else if (h < nz) {
+            const long long tops = ntile * (nz - h), per = (tops + ne - 1) / ne;
+            const long long i = ((long long)blockIdx.x - ntile) * per;
+            run(i, i + per < tops ? i + per : tops, (int)(nz - h), (int)h);
+        }
+    } else {
+        // equal contiguous ranges of all (tile, level) pairs: every CTA gets
+        // the same number of levels (no partial last wave)
+        const long long ntl = ntile * nz, per = (ntl + G - 1) / G;
+        const long long i = (long long)blockIdx.x * per;
+        run(i, ntl < i + per ? ntl : i + per, (int)nz, 0);
     }
 #else
     const int kb = (int)blockIdx.z * (int)a.kchunk;

@@ -461,7 +461,7 @@ static bool valid_for(const kl_op &op, const kl_grid &g, int family, int64_t idx
 static std::vector<int> radices(int family)
 {
     if (family == 0) return {5, 5, 5, 3, 3, 3, 2, 2, 2, 2, 2, 2, 6, 6};
-    if (family == 2) return {9, 7, 7, 6, 4, 3, 2, 2};
+    if (family == 2) return {9, 7, 7, 6, 4, 3, 2, 3};
     return {3, 5, 3, 3, 7, 4, 4};
 }
 
@@ -499,7 +499,7 @@ static bool config_digits(const Config &c, std::vector<int> *digits)
                 {1, 2, 3, 4, 5, 6}};
     else if (c.family == 2)
         vals = {{1, 2, 3, 4, 6, 7, 8, 9, 16}, {1, 2, 3, 4, 5, 6, 8}, {4, 8, 16, 32, 64, 128, 256},
-                {6, 7, 8, 9, 10, 12}, {1, 2, 3, 4}, {0, 1, 2}, {0, 1}, {0, 1}};
+                {6, 7, 8, 9, 10, 12}, {1, 2, 3, 4}, {0, 1, 2}, {0, 1}, {0, 1, 2}};
     else
         vals = {{32, 64, 128}, {1, 2, 4, 8, 16}, {1, 2, 4}, {1, 2, 4}, {4, 8, 16, 32, 64, 128, 256},
                 {8, 9, 10, 12}, {1, 2, 3, 4}};
@@ -1010,6 +1010,13 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
         Config cfg;
         st = select_config(ctx, *op, grids[i], &cfg);
         if (st) return st;
+        // a batch runs z chunks from its tile table, never persistent CTAs; a
+        // record tuned with pe=1 (whose launches ignore kc) takes chunks of at
+        // most 16 levels here
+        if (cfg.family == 2 && cfg.pe) {
+            cfg.pe = 0;
+            cfg.kc = std::min(cfg.kc, 16);
+        }
         std::string err;
         if (!config_fits(*op, cfg, grids[i], &fields[i], &err)) cfg = Config();
         items[i].cfg = cfg;

@@ -46,6 +46,8 @@ CONFIGS_DIRECT = [
     "zpack:w=2,ly=4,kc=4,ns=9,minb=1,cs=1,pe=1",
     "zpack:w=9,ly=3,kc=256,ns=7,minb=1",
     "zpack:w=7,ly=4,kc=16,ns=6,minb=1,pe=1",
+    "zpack:w=4,ly=2,kc=8,ns=6,minb=2,pe=2",
+    "zpack:w=8,ly=2,kc=8,ns=8,minb=1,pe=2",
 ]
 
 
@@ -148,7 +150,8 @@ def test_carried_plane_ring_is_bit_identical(ctx, dtype, walls, adv):
     a column (pe=1): the same values enter the same expressions."""
     f = make_inputs(131, 45, 23, seed=12, walls=walls, stretch=2.0)
     res = []
-    for ns, yx, pe in ((8, 0, 0), (6, 0, 0), (6, 2, 0), (7, 2, 0), (6, 0, 1), (8, 0, 1), (6, 2, 1)):
+    for ns, yx, pe in ((8, 0, 0), (6, 0, 0), (6, 2, 0), (7, 2, 0), (6, 0, 1), (8, 0, 1), (6, 2, 1),
+                       (6, 0, 2), (8, 0, 2)):
         if yx == 2 and adv != 5:
             continue
         cfg = f"zpack:w=2,ly=2,kc=8,ns={ns},minb=1,yx={yx},pe={pe}"

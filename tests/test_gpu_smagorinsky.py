@@ -124,3 +124,32 @@ def test_les_1024x1024x64_sampled_levels(ctx, oracle_mod):
     slabs = ((0, 2), (31, 33), (62, 64))
     ref = np.concatenate([_oracle_nu(oracle_mod, rin, zh, walls=True, g=3, levels=s) for s in slabs])
     assert rel_err(np.concatenate([got[a:b] for a, b in slabs]), ref) <= TOL[1]
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_cs_creates_no_table_and_scales_nu_by_cs_squared(dtype):
+    """cs is a kernel argument: one delta_k^2 table per vertical grid, however
+    many values of cs a caller uses, and nu scales as cs^2."""
+    import json
+
+    import torch
+    from paper_2303_12374_gb300 import kl
+    from paper_2303_12374_gb300.problem import Problem
+    f = make_inputs(40, 24, 12, seed=31, walls=True, stretch=2.0)
+    c = kl.kl_create(0, None)
+    try:
+        p = Problem(40, 24, 12, g=3, dtype=dtype, walls=True, zh=f["zh"], nu=1e-3)
+        bufs = [p.upload(f[k]) for k in ("u", "v", "w")]
+        kl.kl_fill_ghosts(c, p.dtype, p.grid, *[b.data_ptr() for b in bufs])
+        res = []
+        for cs in (0.1, 0.17, 0.2):
+            nu = p.empty()
+            kl.kl_smagorinsky(c, p.dtype, p.grid, cs, *[b.data_ptr() for b in bufs], nu.data_ptr(), False)
+            torch.cuda.synchronize()
+            res.append(p.download(nu))
+        assert json.loads(kl.kl_stats(c))["tables"] == 1
+        tol = 1e-14 if dtype == 0 else 1e-6
+        for cs, r in zip((0.17, 0.2), res[1:]):
+            assert np.abs(r - res[0] * (cs / 0.1) ** 2).max() <= tol * np.abs(r).max()
+    finally:
+        kl.kl_destroy(c)
