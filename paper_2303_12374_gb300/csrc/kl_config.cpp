@@ -216,7 +216,7 @@ bool config_check(const kl_op &op, const Config &c, std::string *err)
             *err = "zmarch parameter outside the space";
             return false;
         }
-        if (c.family == 2 && (c.mbx != 32 || c.mpx != 2 || !in(c.mby, {1, 2, 3, 4, 6, 7, 8, 9, 16}) ||
+        if (c.family == 2 && (c.mbx != 32 || c.mpx != 2 || !in(c.mby, {1, 2, 3, 4, 6, 7, 8, 9, 12, 16}) ||
                               !in(c.mpy, {1, 2, 3, 4, 5, 6, 8}))) {
             *err = "zpack parameter outside the space (w 1..16, ly 1..8)";
             return false;
@@ -284,13 +284,13 @@ static const int kBX[] = {16, 32, 64, 128, 256}, kBYZ[] = {1, 2, 4, 8, 16}, kT[]
 static const int kMBX[] = {32, 64, 128}, kMBY[] = {1, 2, 4, 8, 16}, kMP[] = {1, 2, 4},
                  kKC[] = {4, 8, 16, 32, 64, 128, 256}, kNS[] = {8, 9, 10, 12};
 
-static const int kW[] = {1, 2, 3, 4, 6, 7, 8, 9, 16}, kLY[] = {1, 2, 3, 4, 5, 6, 8}, kNSP[] = {6, 7, 8, 9, 10, 12};
+static const int kW[] = {1, 2, 3, 4, 6, 7, 8, 9, 12, 16}, kLY[] = {1, 2, 3, 4, 5, 6, 8}, kNSP[] = {6, 7, 8, 9, 10, 12};
 
 int64_t space_size(int family)
 {
     if (family == 0) return 5LL * 5 * 5 * 27 * 8 * 8 * 6 * 6;
     if (family == 1) return 3LL * 5 * 3 * 3 * 7 * 4 * 4;
-    if (family == 2) return 9LL * 7 * 7 * 6 * 4 * 3 * 2 * 3;
+    if (family == 2) return 10LL * 7 * 7 * 6 * 4 * 3 * 2 * 3;
     return 0;
 }
 
@@ -318,7 +318,7 @@ bool space_config(int family, int64_t idx, Config *c)
     } else if (family == 2) {
         c->mbx = 32;
         c->mpx = 2;
-        c->mby = kW[take(9)];
+        c->mby = kW[take(10)];
         c->mpy = kLY[take(7)];
         c->kc = kKC[take(7)];
         c->ns = kNSP[take(6)];

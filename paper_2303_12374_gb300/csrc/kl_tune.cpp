@@ -461,7 +461,7 @@ static bool valid_for(const kl_op &op, const kl_grid &g, int family, int64_t idx
 static std::vector<int> radices(int family)
 {
     if (family == 0) return {5, 5, 5, 3, 3, 3, 2, 2, 2, 2, 2, 2, 6, 6};
-    if (family == 2) return {9, 7, 7, 6, 4, 3, 2, 3};
+    if (family == 2) return {10, 7, 7, 6, 4, 3, 2, 3};
     return {3, 5, 3, 3, 7, 4, 4};
 }
 
@@ -498,7 +498,7 @@ static bool config_digits(const Config &c, std::vector<int> *digits)
                 {1, 2, 4}, {0, 1}, {0, 1}, {0, 1}, {0, 1}, {0, 1}, {0, 1}, {0, 1, 2, 3, 4, 5},
                 {1, 2, 3, 4, 5, 6}};
     else if (c.family == 2)
-        vals = {{1, 2, 3, 4, 6, 7, 8, 9, 16}, {1, 2, 3, 4, 5, 6, 8}, {4, 8, 16, 32, 64, 128, 256},
+        vals = {{1, 2, 3, 4, 6, 7, 8, 9, 12, 16}, {1, 2, 3, 4, 5, 6, 8}, {4, 8, 16, 32, 64, 128, 256},
                 {6, 7, 8, 9, 10, 12}, {1, 2, 3, 4}, {0, 1, 2}, {0, 1}, {0, 1, 2}};
     else
         vals = {{32, 64, 128}, {1, 2, 4, 8, 16}, {1, 2, 4}, {1, 2, 4}, {4, 8, 16, 32, 64, 128, 256},
@@ -1010,13 +1010,10 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
         Config cfg;
         st = select_config(ctx, *op, grids[i], &cfg);
         if (st) return st;
-        // a batch runs z chunks from its tile table, never persistent CTAs; a
-        // record tuned with pe=1 (whose launches ignore kc) takes chunks of at
-        // most 16 levels here
-        if (cfg.family == 2 && cfg.pe) {
-            cfg.pe = 0;
-            cfg.kc = std::min(cfg.kc, 16);
-        }
+        // a record tuned with persistent CTAs (pe=1 or 2) runs its class as
+        // persistent CTAs over the class's tiles (equal ranges; the
+        // column-synchronous split of pe=2 is a single-grid schedule)
+        if (cfg.family == 2 && cfg.pe) cfg.pe = 1;
         std::string err;
         if (!config_fits(*op, cfg, grids[i], &fields[i], &err)) cfg = Config();
         items[i].cfg = cfg;
@@ -1033,6 +1030,8 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
         Config cfg;
         size_t nblocks;
         void *argv, *tl, *tm;
+        int ntiles;              // persistent classes: tile entries, pairs
+        long long total;
     };
     std::vector<Launch> plan;
     for (auto &gp : groups) {
@@ -1040,9 +1039,22 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
         const Config &cfg = items[ids[0]].cfg;
         const kl_grid &g0 = grids[ids[0]];
         std::vector<int> tiles;                 // 4 ints per block
+        const bool pers = cfg.family == 2 && cfg.pe;
+        long long npairs = 0;
         for (size_t q = 0; q < ids.size(); ++q) {
             const KArgs &a = items[ids[q]].a;
-            if (cfg.family == 0) {
+            if (pers) {
+                // one entry per tile column: {grid, bx, by, first pair index}
+                for (int by = 0; by < (int)a.nby; ++by)
+                    for (int bx = 0; bx < (int)a.nbx; ++bx) {
+                        if (npairs > 0x7fffffffLL) return fail(KL_ERR_UNSUPPORTED, "batch too large");
+                        tiles.push_back((int)q);
+                        tiles.push_back(bx);
+                        tiles.push_back(by);
+                        tiles.push_back((int)npairs);
+                        npairs += grids[ids[q]].nz;
+                    }
+            } else if (cfg.family == 0) {
                 long long nb = a.nbx * a.nby * a.nbz;
                 for (long long b = 0; b < nb; ++b) {
                     tiles.push_back((int)q);
@@ -1105,7 +1117,16 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
         st = get_kernel(ctx, *op, cfg, g0.zbc, g0.zh ? 0 : 1, &k, true);
         if (st) return st;
         char *base = (char *)dev;
-        plan.push_back({k, cfg, nblocks, base + off_args, base + off_tiles, base + off_maps});
+        const int ntiles = (int)nblocks;
+        if (pers) {
+            // as many CTAs as fit on the device at once
+            int per_sm = 0;
+            CUresult r = ctx->drv.OccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, k->fn, cfg.mbx * zmarch_block_y(cfg), k->smem);
+            if (r != CUDA_SUCCESS) return cu_fail(r, "cuOccupancyMaxActiveBlocksPerMultiprocessor");
+            nblocks = (size_t)std::max(1LL, std::min<long long>(npairs, (long long)std::max(1, per_sm) * ctx->nsm));
+        }
+        plan.push_back({k, cfg, nblocks, base + off_args, base + off_tiles, base + off_maps, ntiles, npairs});
     }
 
     // streams: with several configuration classes, the classes run side by
@@ -1141,6 +1162,13 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
                 void *params[] = {&argv, &tl};
                 r = ctx->drv.LaunchKernel(L.k->fn, (unsigned)L.nblocks, 1, 1, L.cfg.bx, L.cfg.by,
                                           L.cfg.bz, 0, (CUstream)ls, params, nullptr);
+            } else if (L.cfg.family == 2 && L.cfg.pe) {
+                int ntiles = L.ntiles;
+                long long total = L.total;
+                void *params[] = {&argv, &tl, &tm, &ntiles, &total};
+                r = ctx->drv.LaunchKernel(L.k->fn, (unsigned)L.nblocks, 1, 1, L.cfg.mbx,
+                                          zmarch_block_y(L.cfg), 1, (unsigned)L.k->smem, (CUstream)ls,
+                                          params, nullptr);
             } else {
                 void *params[] = {&argv, &tl, &tm};
                 r = ctx->drv.LaunchKernel(L.k->fn, (unsigned)L.nblocks, 1, 1, L.cfg.mbx,

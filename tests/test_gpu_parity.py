@@ -48,6 +48,7 @@ CONFIGS_DIRECT = [
     "zpack:w=7,ly=4,kc=16,ns=6,minb=1,pe=1",
     "zpack:w=4,ly=2,kc=8,ns=6,minb=2,pe=2",
     "zpack:w=8,ly=2,kc=8,ns=8,minb=1,pe=2",
+    "zpack:w=12,ly=2,kc=8,ns=6,minb=1,pe=1",
 ]
 
 

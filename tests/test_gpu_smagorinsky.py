@@ -53,6 +53,8 @@ CASES = [
     (40, 24, 10, 1, False, 0.0),
     (13, 11, 9, 1, True, 0.0),
     (33, 9, 40, 3, False, 1.5),
+    (64, 34, 40, 3, True, 2.0),     # two rows per thread, ragged in y, several level chunks
+    (36, 10, 7, 1, False, 0.0),     # two rows per thread, g = 1
 ]
 
 
