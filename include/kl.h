@@ -214,11 +214,13 @@ kl_status kl_step(kl_ctx *ctx, const kl_op *op, const kl_grid *grid, const kl_fi
  *   "zmarch:bx=,by=,px=,py=,kc=,ns=,minb="
  *              z-marching CTAs over a TMA plane ring: threads along x and y,
  *              points per thread along x and y, z levels per CTA, ring slots
- *   "zpack:w=,ly=,kc=,ns=,minb=,yx=,pk=,cs="
+ *   "zpack:w=,ly=,kc=,ns=,minb=,yx=,pk=,cs=,pe="
  *              z-marching over 64-column tiles with packed column pairs: warps,
  *              rows per warp, z levels per CTA, ring slots, minimum blocks,
  *              y faces exchanged between warps (yx), packed f32x2 arithmetic
- *              (pk), one warp group per tendency component (cs)
+ *              (pk), one warp group per tendency component (cs), persistent
+ *              CTAs over (tile, level) ranges (pe: 1 equal ranges, 2 column-
+ *              synchronous; kc is then unused)
  * A configuration outside the space or the op's constraints (threads, shared
  * memory, TMA box) is rejected with KL_ERR_INVALID_ARG.
  */
@@ -226,10 +228,16 @@ kl_status kl_launch_with_config(kl_ctx *ctx, const kl_op *op, const char *config
                                 const kl_grid *grid, const kl_fields *fields, void *stream);
 
 /*
- * n independent grids (HOST arrays grids[n], fields[n]) of one op: each grid
- * gets the configuration of its nearest tuned size (Sec. 4.5 fuzzy matching,
- * Sec. 6), grids sharing a configuration run in one launch over a device tile
- * table, and the launches of all size classes are issued on `stream`.
+ * n independent grids (HOST arrays grids[n], fields[n]) of one op.  The
+ * batch takes one configuration: the wisdom record tuned for the problem
+ * whose point count is nearest to the batch's total (kl_wisdom_select_points,
+ * per zbc), since the batch offers the parallelism of all its grids
+ * together.  A grid that configuration does not fit (shared memory, TMA box)
+ * takes the record of its own nearest tuned size (Sec. 4.5 fuzzy matching,
+ * Sec. 6).  Records tuned with persistent CTAs (pe) run here as z chunks of
+ * at most 16 levels.  Grids sharing a configuration run in one launch over a
+ * device tile table, and the launches of all classes are issued on
+ * `stream`; kl_stats reports the classes of the last batch planned.
  */
 kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_grid *grids,
                             const kl_fields *fields, void *stream);
@@ -540,6 +548,16 @@ kl_status kl_compile_only(const kl_op *op, const char *config, int32_t zbc, int3
 kl_status kl_wisdom_select(const char *path, const char *device, int32_t cc_major,
                            int32_t cc_minor, int32_t zbc, int32_t nx, int32_t ny, int32_t nz,
                            char *cfg, size_t n, int32_t *rule);
+
+/*
+ * The selection kl_launch_batched makes for a batch of `points` interior
+ * points in all: rules 2..5 of kl_wisdom_select with the distance between a
+ * record and the batch taken as |ln(record nx*ny*nz) - ln(points)| (no rule
+ * 1).  Same arguments, output and error behaviour as kl_wisdom_select.
+ */
+kl_status kl_wisdom_select_points(const char *path, const char *device, int32_t cc_major,
+                                  int32_t cc_minor, int32_t zbc, int64_t points, char *cfg,
+                                  size_t n, int32_t *rule);
 
 /* Append one record (host strings) to the wisdom file at path, creating it. */
 kl_status kl_wisdom_append(const char *path, const char *device, int32_t cc_major,

@@ -612,6 +612,43 @@ kl_status select_config(kl_ctx *ctx, const kl_op &op, const kl_grid &g, Config *
     return KL_OK;
 }
 
+kl_status select_batch_config(kl_ctx *ctx, const kl_op &op, int zbc, long long points, Config *cfg)
+{
+    char key[160];
+    snprintf(key, sizeof key, "batch/%d/%d/%d/%d/%d/%lld", op.adv, op.diff, op.dtype, op.accumulate,
+             zbc, points);
+    auto it = ctx->selection.find(key);
+    std::string text;
+    if (it != ctx->selection.end()) {
+        text = it->second;
+    } else {
+        auto t0 = std::chrono::steady_clock::now();
+        std::vector<WisdomRecord> recs;
+        std::string err;
+        int rule = 5;
+        text = "default";
+        if (!ctx->wisdom_dir.empty()) {
+            std::string path = ctx->wisdom_dir + "/" + wisdom_file_name(op);
+            if (wisdom_read(path, &recs, &err))
+                rule = wisdom_select_points(recs, ctx->name, ctx->cc_major, ctx->cc_minor, zbc,
+                                            (double)points, &text);
+            else
+                ctx->last_rule_text = err;
+        }
+        Config c;
+        if (!config_parse(text, &c, &err) || !config_check(op, c, &err)) {
+            text = "default";
+            rule = 5;
+        }
+        ctx->selection[key] = text;
+        ctx->selection_rule[key] = rule;
+        ctx->t_wisdom_ms += ms_since(t0);
+    }
+    std::string err;
+    if (!config_parse(text, cfg, &err)) return fail(KL_ERR_WISDOM_PARSE, err);
+    return KL_OK;
+}
+
 }  // namespace kl
 
 using namespace kl;
@@ -1023,13 +1060,13 @@ kl_status kl_stats(kl_ctx *ctx, char *buf, size_t n)
                      "{\"device\":\"%s\",\"cc\":\"%d.%d\",\"sms\":%d,\"launches\":%lld,"
                      "\"cache_hits\":%lld,\"cache_misses\":%lld,\"modules\":%zu,"
                      "\"stage_ms\":{\"wisdom\":%.3f,\"nvrtc\":%.3f,\"module_load\":%.3f,"
-                     "\"launch\":%.3f},\"last_config\":\"%s\",\"rules\":{%s},\"note\":\"%s\","
+                     "\"launch\":%.3f},\"last_config\":\"%s\",\"last_batch\":\"%s\",\"rules\":{%s},\"note\":\"%s\","
                      "\"tables\":%zu,\"graphs\":%zu,\"graph_replays\":%lld,"
                      "\"disk_cache\":{\"on\":%s,\"hits\":%lld,\"writes\":%lld,\"read_ms\":%.3f}}",
                      ctx->name.c_str(), ctx->cc_major, ctx->cc_minor, ctx->nsm, ctx->launches,
                      ctx->cache_hits, ctx->cache_misses, ctx->kernels.size(), ctx->t_wisdom_ms,
                      ctx->t_nvrtc_ms, ctx->t_load_ms, ctx->t_launch_ms, ctx->last_config.c_str(),
-                     rules.c_str(), ctx->last_rule_text.c_str(), ctx->tables.size(),
+                     ctx->last_batch.c_str(), rules.c_str(), ctx->last_rule_text.c_str(), ctx->tables.size(),
                      ctx->graphs.size(), ctx->graph_replays, ctx->cache_dir.empty() ? "false" : "true",
                      ctx->disk_hits, ctx->disk_writes, ctx->t_disk_ms);
     if (m < 0 || (size_t)m >= n) return fail(KL_ERR_INVALID_ARG, "stats buffer too small");
@@ -1162,6 +1199,24 @@ kl_status kl_wisdom_select(const char *path, const char *device, int32_t cc_majo
     memcpy(cfg, text.c_str(), text.size() + 1);
     *rule = r;
     return st;
+}
+
+kl_status kl_wisdom_select_points(const char *path, const char *device, int32_t cc_major,
+                                  int32_t cc_minor, int32_t zbc, int64_t points, char *cfg,
+                                  size_t n, int32_t *rule)
+{
+    if (!path || !device || !cfg || !n || !rule) return fail(KL_ERR_INVALID_ARG, "NULL argument");
+    std::vector<WisdomRecord> recs;
+    std::string err, text = "default";
+    int r = 5;
+    if (wisdom_read(path, &recs, &err))
+        r = wisdom_select_points(recs, device, cc_major, cc_minor, zbc, (double)points, &text);
+    else
+        set_error(err);
+    if (text.size() + 1 > n) return fail(KL_ERR_INVALID_ARG, "buffer too small");
+    memcpy(cfg, text.c_str(), text.size() + 1);
+    *rule = r;
+    return KL_OK;
 }
 
 kl_status kl_wisdom_append(const char *path, const char *device, int32_t cc_major,

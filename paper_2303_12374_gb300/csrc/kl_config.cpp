@@ -432,29 +432,16 @@ bool wisdom_read(const std::string &path, std::vector<WisdomRecord> *out, std::s
     return true;
 }
 
-// Sec. 4.5 heuristic.  Several records with the same device and size (one per
-// tuning session): the fastest (smallest time_us) wins, ties go to the newest.
-// Distance ties: the first record in file order.  Records of another zbc are
-// never chosen.
-int wisdom_select(const std::vector<WisdomRecord> &recs, const std::string &device, int ccM,
-                  int ccm, int zbc, int nx, int ny, int nz, std::string *config)
+// Rules 2-5 of the Sec. 4.5 heuristic with a given distance between a
+// record's size and the problem: the nearest record of this device, else of
+// this compute capability, else of any device, else the default.  Records of
+// one size (several tuning sessions) compete as in rule 1 (the fastest, ties
+// to the newest); different sizes at the same distance go by file order.
+// Records of another zbc are never chosen.
+template <class Dist>
+static int select_nearest(const std::vector<WisdomRecord> &recs, const std::string &device, int ccM,
+                          int ccm, int zbc, Dist dist, std::string *config)
 {
-    auto dist = [&](const WisdomRecord &r) {
-        double a = r.nx - nx, b = r.ny - ny, c = r.nz - nz;
-        return std::sqrt(a * a + b * b + c * c);
-    };
-    // rule 1
-    const WisdomRecord *exact = nullptr;
-    for (const WisdomRecord &r : recs)
-        if (r.zbc == zbc && r.device == device && r.nx == nx && r.ny == ny && r.nz == nz)
-            if (!exact || r.time_us <= exact->time_us) exact = &r;
-    if (exact) {
-        *config = exact->config;
-        return 1;
-    }
-    // nearest problem size; records of one size (several tuning sessions)
-    // compete as in rule 1 (the fastest, ties to the newest), different
-    // sizes at the same distance go by file order
     auto nearest = [&](auto pred) -> const WisdomRecord * {
         const WisdomRecord *best = nullptr;
         double bd = 0;
@@ -485,6 +472,41 @@ int wisdom_select(const std::vector<WisdomRecord> &recs, const std::string &devi
     }
     *config = "default";
     return 5;
+}
+
+// Sec. 4.5 heuristic.  Rule 1: a record of this device and exactly this size
+// (several: the fastest, ties to the newest); then the nearest size in
+// Euclidean distance over (nx, ny, nz), by the tiers of select_nearest.
+int wisdom_select(const std::vector<WisdomRecord> &recs, const std::string &device, int ccM,
+                  int ccm, int zbc, int nx, int ny, int nz, std::string *config)
+{
+    const WisdomRecord *exact = nullptr;
+    for (const WisdomRecord &r : recs)
+        if (r.zbc == zbc && r.device == device && r.nx == nx && r.ny == ny && r.nz == nz)
+            if (!exact || r.time_us <= exact->time_us) exact = &r;
+    if (exact) {
+        *config = exact->config;
+        return 1;
+    }
+    return select_nearest(recs, device, ccM, ccm, zbc, [&](const WisdomRecord &r) {
+        double a = r.nx - nx, b = r.ny - ny, c = r.nz - nz;
+        return std::sqrt(a * a + b * b + c * c);
+    }, config);
+}
+
+// A batch's configuration: the record whose tuned problem has the point count
+// nearest (in ratio) to the batch's total, by the tiers of select_nearest.  A
+// batch offers the parallelism of all its grids together, so the record
+// tuned for a problem of that size fits it better than the small-grid
+// records, tuned to spread one small grid over the device.
+int wisdom_select_points(const std::vector<WisdomRecord> &recs, const std::string &device, int ccM,
+                         int ccm, int zbc, double points, std::string *config)
+{
+    const double lp = std::log(std::max(points, 1.0));
+    return select_nearest(recs, device, ccM, ccm, zbc, [&](const WisdomRecord &r) {
+        const double v = std::max(1.0, (double)r.nx * r.ny * r.nz);
+        return std::fabs(std::log(v) - lp);
+    }, config);
 }
 
 static const char *dtype_name(int d)

@@ -98,6 +98,9 @@ bool wisdom_read(const std::string &path, std::vector<WisdomRecord> *out, std::s
 // returns rule 1..5 and the chosen configuration string
 int wisdom_select(const std::vector<WisdomRecord> &recs, const std::string &device, int ccM,
                   int ccm, int zbc, int nx, int ny, int nz, std::string *config);
+// rules 2..5 by the nearest point count (batched launches)
+int wisdom_select_points(const std::vector<WisdomRecord> &recs, const std::string &device, int ccM,
+                         int ccm, int zbc, double points, std::string *config);
 std::string wisdom_file_name(const kl_op &op);
 bool wisdom_append(const std::string &path, const WisdomRecord &r, std::string *err);
 
@@ -223,6 +226,7 @@ struct kl_ctx {
     std::map<std::string, kl::DefKernel> def_kernels;
     double t_disk_ms = 0;
     std::string last_config, last_rule_text;
+    std::string last_batch;    // classes of the last batch planned: "config xN; ..."
 };
 
 namespace kl {
@@ -239,6 +243,8 @@ kl_status get_kernel(kl_ctx *ctx, const kl_op &op, const Config &cfg, int zbc, i
 kl_status make_kargs(kl_ctx *ctx, const kl_op &op, const Config &cfg, const kl_grid &g,
                      const kl_fields &f, KArgs *a, CUtensorMap maps[KL_NMAPS]);
 kl_status select_config(kl_ctx *ctx, const kl_op &op, const kl_grid &g, Config *cfg);
+// the configuration of a batch of `points` interior points of boundary zbc
+kl_status select_batch_config(kl_ctx *ctx, const kl_op &op, int zbc, long long points, Config *cfg);
 kl_status check_op(const kl_op *op);
 kl_status check_fields(const kl_op &op, const kl_fields *f);
 kl_status get_profile(kl_ctx *ctx, const kl_grid &g, Profile **out);

@@ -1890,47 +1890,7 @@ __device__ __forceinline__ bool kl_zpack_body(const kl_args &a, const kl_tmap *c
     return !timed_out;
 }
 
-#if KL_BATCH && KL_PE
-// Persistent CTAs over a batch: the class's tiles (one entry per tile column
-// of one grid, tiles[t] = {grid, bx, by, index of the tile's first (tile,
-// level) pair}) with each tile's levels 0 .. nz-1 consecutive form `total`
-// pairs; CTA b takes the b-th of gridDim.x equal contiguous ranges and runs
-// it as segments of consecutive levels of one tile, crossing from one grid
-// to the next inside the range.
-extern "C" __global__ void __launch_bounds__(32 * KL_MBY * (KL_CS ? 3 : 1), KL_MMINB)
-kl_tendency(const kl_args *argv, const int4 *tiles, const kl_tmap *tmaps, int ntiles, long long total)
-{
-    const long long G = gridDim.x, per = (total + G - 1) / G;
-    long long i = (long long)blockIdx.x * per;
-    const long long end = i + per < total ? i + per : total;
-    if (i >= end) return;
-    // the tile holding pair i: the last t with tiles[t].w <= i
-    int lo = 0, hi = ntiles - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if ((long long)tiles[mid].w <= i) lo = mid;
-        else hi = mid - 1;
-    }
-    bool first = true;
-    int q_prev = -1;
-    for (int t = lo; i < end && t < ntiles; ++t) {
-        const int4 d = tiles[t];
-        const kl_args &a = argv[d.x];
-        const kl_tmap *maps[7];
-        for (int f = 0; f < 7; ++f) maps[f] = &tmaps[7 * d.x + f];
-        if (d.x != q_prev && threadIdx.x == 0 && threadIdx.y == 0)
-            for (int f = 0; f < 7; ++f) kl_tmap_acquire(maps[f]);
-        q_prev = d.x;
-        const int nzq = (int)a.nz, k0 = (int)(i - d.w);
-        const long long left = end - i;
-        const int k1 = left < nzq - k0 ? k0 + (int)left : nzq;
-        if (!first) __syncthreads();               // the last segment's ring is idle
-        if (!kl_zpack_body(a, maps, d.y, d.z, k0, k1, !first)) return;
-        first = false;
-        i += k1 - k0;
-    }
-}
-#elif KL_BATCH
+#if KL_BATCH
 extern "C" __global__ void __launch_bounds__(32 * KL_MBY * (KL_CS ? 3 : 1), KL_MMINB)
 kl_tendency(const kl_args *argv, const int4 *blocks, const kl_tmap *tmaps)
 {

@@ -994,7 +994,10 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
         }
     }
 
-    // per grid: the configuration of its nearest tuned size (Sec. 4.5 rules)
+    // the batch's configuration: the record tuned for the problem size
+    // nearest to the batch's total point count (per boundary kind), for
+    // every grid it fits; a grid it does not fit takes the record of its own
+    // nearest tuned size (Sec. 4.5 rules)
     struct Item {
         Config cfg;
         KArgs a;
@@ -1002,18 +1005,36 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
     };
     std::vector<Item> items((size_t)n);
     std::map<std::string, std::vector<int>> groups;       // compile key -> grids
+    long long points[2] = {0, 0};
     for (int i = 0; i < n; ++i) {
         st = check_fields(*op, &fields[i]);
         if (st) return fail(st, "grid " + std::to_string(i) + ": " + kl_last_error());
         st = check_grid(&grids[i], halo_of(*op), nullptr);
         if (st) return fail(st, "grid " + std::to_string(i) + ": " + kl_last_error());
-        Config cfg;
-        st = select_config(ctx, *op, grids[i], &cfg);
-        if (st) return st;
-        // a record tuned with persistent CTAs (pe=1 or 2) runs its class as
-        // persistent CTAs over the class's tiles (equal ranges; the
-        // column-synchronous split of pe=2 is a single-grid schedule)
-        if (cfg.family == 2 && cfg.pe) cfg.pe = 1;
+        points[grids[i].zbc] += (long long)grids[i].nx * grids[i].ny * grids[i].nz;
+    }
+    Config bcfg[2];
+    for (int z = 0; z < 2; ++z)
+        if (points[z]) {
+            st = select_batch_config(ctx, *op, z, points[z], &bcfg[z]);
+            if (st) return st;
+        }
+    for (int i = 0; i < n; ++i) {
+        Config cfg = bcfg[grids[i].zbc];
+        std::string err0;
+        if (!config_fits(*op, cfg, grids[i], &fields[i], &err0)) {
+            st = select_config(ctx, *op, grids[i], &cfg);
+            if (st) return st;
+        }
+        // a batch runs z chunks from its tile table, never persistent CTAs
+        // (persistent CTAs over a class's tiles, in equal ranges that cross
+        // from one grid to the next, measured slower than chunks that the
+        // block scheduler balances); a record tuned with pe=1 or 2 (whose
+        // launches ignore kc) takes chunks of at most 16 levels here
+        if (cfg.family == 2 && cfg.pe) {
+            cfg.pe = 0;
+            cfg.kc = std::min(cfg.kc, 16);
+        }
         std::string err;
         if (!config_fits(*op, cfg, grids[i], &fields[i], &err)) cfg = Config();
         items[i].cfg = cfg;
@@ -1023,6 +1044,10 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
         groups[compile_defines(*op, cfg, grids[i].zbc, zuni)].push_back(i);
     }
 
+    ctx->last_batch.clear();
+    for (auto &gp : groups)
+        ctx->last_batch += (ctx->last_batch.empty() ? "" : "; ") + config_string(items[gp.second[0]].cfg) +
+                           " x" + std::to_string(gp.second.size());
     // per configuration class: its device table [descriptors | argument
     // blocks | tile list] (uploaded once per content) and its compiled kernel
     struct Launch {
@@ -1030,8 +1055,6 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
         Config cfg;
         size_t nblocks;
         void *argv, *tl, *tm;
-        int ntiles;              // persistent classes: tile entries, pairs
-        long long total;
     };
     std::vector<Launch> plan;
     for (auto &gp : groups) {
@@ -1039,22 +1062,9 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
         const Config &cfg = items[ids[0]].cfg;
         const kl_grid &g0 = grids[ids[0]];
         std::vector<int> tiles;                 // 4 ints per block
-        const bool pers = cfg.family == 2 && cfg.pe;
-        long long npairs = 0;
         for (size_t q = 0; q < ids.size(); ++q) {
             const KArgs &a = items[ids[q]].a;
-            if (pers) {
-                // one entry per tile column: {grid, bx, by, first pair index}
-                for (int by = 0; by < (int)a.nby; ++by)
-                    for (int bx = 0; bx < (int)a.nbx; ++bx) {
-                        if (npairs > 0x7fffffffLL) return fail(KL_ERR_UNSUPPORTED, "batch too large");
-                        tiles.push_back((int)q);
-                        tiles.push_back(bx);
-                        tiles.push_back(by);
-                        tiles.push_back((int)npairs);
-                        npairs += grids[ids[q]].nz;
-                    }
-            } else if (cfg.family == 0) {
+            if (cfg.family == 0) {
                 long long nb = a.nbx * a.nby * a.nbz;
                 for (long long b = 0; b < nb; ++b) {
                     tiles.push_back((int)q);
@@ -1117,16 +1127,7 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
         st = get_kernel(ctx, *op, cfg, g0.zbc, g0.zh ? 0 : 1, &k, true);
         if (st) return st;
         char *base = (char *)dev;
-        const int ntiles = (int)nblocks;
-        if (pers) {
-            // as many CTAs as fit on the device at once
-            int per_sm = 0;
-            CUresult r = ctx->drv.OccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, k->fn, cfg.mbx * zmarch_block_y(cfg), k->smem);
-            if (r != CUDA_SUCCESS) return cu_fail(r, "cuOccupancyMaxActiveBlocksPerMultiprocessor");
-            nblocks = (size_t)std::max(1LL, std::min<long long>(npairs, (long long)std::max(1, per_sm) * ctx->nsm));
-        }
-        plan.push_back({k, cfg, nblocks, base + off_args, base + off_tiles, base + off_maps, ntiles, npairs});
+        plan.push_back({k, cfg, nblocks, base + off_args, base + off_tiles, base + off_maps});
     }
 
     // streams: with several configuration classes, the classes run side by
@@ -1162,13 +1163,6 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
                 void *params[] = {&argv, &tl};
                 r = ctx->drv.LaunchKernel(L.k->fn, (unsigned)L.nblocks, 1, 1, L.cfg.bx, L.cfg.by,
                                           L.cfg.bz, 0, (CUstream)ls, params, nullptr);
-            } else if (L.cfg.family == 2 && L.cfg.pe) {
-                int ntiles = L.ntiles;
-                long long total = L.total;
-                void *params[] = {&argv, &tl, &tm, &ntiles, &total};
-                r = ctx->drv.LaunchKernel(L.k->fn, (unsigned)L.nblocks, 1, 1, L.cfg.mbx,
-                                          zmarch_block_y(L.cfg), 1, (unsigned)L.k->smem, (CUstream)ls,
-                                          params, nullptr);
             } else {
                 void *params[] = {&argv, &tl, &tm};
                 r = ctx->drv.LaunchKernel(L.k->fn, (unsigned)L.nblocks, 1, 1, L.cfg.mbx,

@@ -87,6 +87,8 @@ SIGNATURES = {
                         ctypes.c_int),
     "kl_wisdom_select": ([_S, _S, _I32, _I32, _I32, _I32, _I32, _I32, ctypes.c_char_p,
                           ctypes.c_size_t, ctypes.POINTER(_I32)], ctypes.c_int),
+    "kl_wisdom_select_points": ([_S, _S, _I32, _I32, _I32, _I64, ctypes.c_char_p, ctypes.c_size_t,
+                                 ctypes.POINTER(_I32)], ctypes.c_int),
     "kl_wisdom_append": ([_S, _S, _I32, _I32, _I32, _I32, _I32, _I32, _S, _D, _S], ctypes.c_int),
     "kl_bo_posterior": ([_I32, _I32, _P, _P, _I32, _P, _D, _D, _P, _P, ctypes.POINTER(_D)],
                         ctypes.c_int),
@@ -369,6 +371,14 @@ def kl_wisdom_select(path, device, cc_major, cc_minor, zbc, nx, ny, nz):
     rule = ctypes.c_int32()
     check(load().kl_wisdom_select(_b(path), _b(device), cc_major, cc_minor, zbc, nx, ny, nz, buf,
                                   len(buf), ctypes.byref(rule)))
+    return buf.value.decode(), rule.value
+
+
+def kl_wisdom_select_points(path, device, cc_major, cc_minor, zbc, points):
+    buf = ctypes.create_string_buffer(1024)
+    rule = ctypes.c_int32()
+    check(load().kl_wisdom_select_points(_b(path), _b(device), cc_major, cc_minor, zbc, points, buf,
+                                         len(buf), ctypes.byref(rule)))
     return buf.value.decode(), rule.value
 
 

@@ -7,8 +7,9 @@ wisdom selection.
     python -m paper_2303_12374_gb300.run_batch --reps 3
     python -m paper_2303_12374_gb300.run_batch --reps 3 --separate
 
-Prints the configuration class of every grid (the wisdom record each one
-selects) and the context statistics.
+Prints the configuration classes of the batch (a configuration and its
+number of grids), the record each grid selects in a single launch, and the
+context statistics.
 """
 
 from __future__ import annotations
@@ -62,7 +63,8 @@ def main(argv=None):
                 kl.kl_launch_batched(ctx, op, grids, fields)
         torch.cuda.synchronize()
         kl.kl_check(ctx)
-        print(json.dumps({"classes": {k: len(v) for k, v in classes.items()},
+        print(json.dumps({"batch_classes": json.loads(kl.kl_stats(ctx))["last_batch"],
+                          "single_launch_classes": {k: len(v) for k, v in classes.items()},
                           "grids": {k: v for k, v in classes.items()}}))
         print(kl.kl_stats(ctx))
     finally:

@@ -89,57 +89,6 @@ def test_batched_matches_oracle_and_single_launches(tmp_path, oracle_mod, dtype,
         kl.kl_destroy(ctx)
 
 
-@pytest.mark.parametrize("diff,dtype,tag", [(1, 1, "f32"), (2, 1, "f32"), (1, 3, "f16")])
-def test_batched_persistent_classes(tmp_path, oracle_mod, diff, dtype, tag):
-    """Records tuned with persistent CTAs run their class as persistent CTAs
-    over the class's tiles: equal ranges of (tile, level) pairs that start in
-    the middle of a column and cross from one grid to the next.  The fields
-    equal the oracle's and the single launches' of the same records."""
-    import torch
-    from paper_2303_12374_gb300 import kl
-    from paper_2303_12374_gb300.problem import Problem
-    small = "zpack:w=2,ly=2,kc=8,ns=8,minb=1,pe=2"
-    big = "zpack:w=4,ly=2,kc=16,ns=8,minb=2,pe=1"
-    _wisdom(tmp_path / f"tendency_adv5_diff{diff}_{tag}.wisdom", tag,
-            [((32, 32, 16), small), ((80, 48, 24), big)])
-    ctx = kl.kl_create(0, str(tmp_path))
-    try:
-        probs = []
-        for q, (nx, ny, nz) in enumerate(SIZES):
-            f = make_inputs(nx, ny, nz, seed=500 + q, walls=True, stretch=1.5, var_nu=diff == 2)
-            p = Problem(nx, ny, nz, g=3, dtype=dtype, walls=True, zh=f["zh"], nu=1e-3)
-            keys = ("u", "v", "w", "nu") if diff == 2 else ("u", "v", "w")
-            bufs = {k: p.upload(f[k]) for k in keys}
-            outs = [p.empty() for _ in range(3)]
-            fl = kl.Fields(bufs["u"].data_ptr(), bufs["v"].data_ptr(), bufs["w"].data_ptr(),
-                           bufs["nu"].data_ptr() if diff == 2 else None, *[o.data_ptr() for o in outs])
-            kl.kl_fill_ghosts(ctx, p.dtype, p.grid, bufs["u"].data_ptr(), bufs["v"].data_ptr(),
-                              bufs["w"].data_ptr(), bufs["nu"].data_ptr() if diff == 2 else None)
-            probs.append((f, p, bufs, outs, fl))
-        op = kl.Op(5, diff, dtype, 0)
-        kl.kl_launch_batched(ctx, op, [pr[1].grid for pr in probs], [pr[4] for pr in probs])
-        torch.cuda.synchronize()
-        kl.kl_check(ctx)
-        got = [[p.download(o) for o in outs] for f, p, bufs, outs, fl in probs]
-        for (f, p, bufs, outs, fl), g3 in zip(probs, got):
-            rin = {k: p.rounded(f[k]) for k in bufs}
-            ref = oracle_ref(oracle_mod, rin, f["zh"], adv=5, diff=diff, walls=True, g=3)
-            for name, a, r in zip(("ut", "vt", "wt"), g3, ref):
-                assert rel_err(a, r) <= TOL[p.dtype], (p.nx, p.ny, p.nz, name)
-        classes = set()
-        for (f, p, bufs, outs, fl), g3 in zip(probs, got):
-            for o in outs:
-                o.zero_()
-            kl.kl_launch(ctx, op, p.grid, fl)
-            classes.add(json.loads(kl.kl_stats(ctx))["last_config"])
-            torch.cuda.synchronize()
-            for o, a in zip(outs, g3):
-                assert np.array_equal(p.download(o), a)
-        assert any(",pe=1" in c for c in classes) and any(",pe=2" in c for c in classes)
-    finally:
-        kl.kl_destroy(ctx)
-
-
 def test_batched_inside_a_caller_capture(tmp_path):
     """A batch seen before can be recorded into the caller's own CUDA graph:
     its launches join the caller's capture instead of a graph of its own."""

@@ -196,7 +196,10 @@ def test_batch64_uneven_as_bench_times_it(oracle_mod):
         kl.kl_launch_batched(ctx, op, grids, fields)       # the replay of its graph
         torch.cuda.synchronize()
         kl.kl_check(ctx)
-        assert json.loads(kl.kl_stats(ctx))["graph_replays"] == 1
+        st = json.loads(kl.kl_stats(ctx))
+        assert st["graph_replays"] == 1
+        # the classes of the batch cover its 64 grids
+        assert sum(int(c.rsplit(" x", 1)[1]) for c in st["last_batch"].split("; ")) == 64
         for f, p, outs, fl, bufs in probs:
             rin = {k: p.rounded(f[k]) for k in ("u", "v", "w")}
             slabs = ((0, 2), (p.nz // 2, p.nz // 2 + 1))    # w: level 1 (0 is the wall)

@@ -192,6 +192,29 @@ def test_wisdom_nearest_size_takes_its_fastest_session(tmp_path):
     assert kl.kl_wisdom_select(p, "G", 10, 3, 0, 70, 60, 64) == ("direct:bx=32", 2)
 
 
+def test_batch_selection_by_total_points(tmp_path):
+    """A batch takes the record whose tuned problem has the point count
+    nearest (in ratio) to the batch's total: 64 grids of ~1 M points go to the
+    512 x 512 x 256 record, not to the small grids' records; the device and
+    zbc tiers and the fastest session of a size apply as for one grid."""
+    p = str(tmp_path / "w.wisdom")
+    _write(p, [
+        rec("G", "10.3", 1, (64, 64, 64), "zpack:w=4,ly=1"),
+        rec("G", "10.3", 1, (256, 256, 256), "zpack:w=4,ly=3"),
+        rec("G", "10.3", 1, (512, 512, 256), "zpack:w=8,ly=4").replace("time_us=1.0", "time_us=9.0"),
+        rec("G", "10.3", 1, (512, 512, 256), "zpack:w=8,ly=3").replace("time_us=1.0", "time_us=5.0"),
+        rec("G", "10.3", 0, (64, 64, 64), "zpack:w=2,ly=2"),
+        rec("H", "10.3", 1, (1024, 1024, 1024), "zpack:w=16,ly=2"),
+    ])
+    sel = lambda dev, zbc, n: kl.kl_wisdom_select_points(p, dev, 10, 3, zbc, n)
+    assert sel("G", 1, 64 * 1_100_000) == ("zpack:w=8,ly=3", 2)      # fastest 512x512x256 session
+    assert sel("G", 1, 300_000) == ("zpack:w=4,ly=1", 2)            # 262 144 points
+    assert sel("G", 1, 10_000_000) == ("zpack:w=4,ly=3", 2)         # ln ratio 0.52 vs 1.90
+    assert sel("G", 0, 10 ** 9) == ("zpack:w=2,ly=2", 2)            # zbc never crosses
+    assert sel("X", 1, 10 ** 9) == ("zpack:w=16,ly=2", 3)           # same architecture
+    assert kl.kl_wisdom_select_points(str(tmp_path / "none"), "G", 10, 3, 1, 5) == ("default", 5)
+
+
 def test_wisdom_distance_tie_takes_first_record(tmp_path):
     p = str(tmp_path / "w.wisdom")
     _write(p, [rec("G", "10.3", 0, (100, 100, 100), "direct:bx=16"),
