@@ -7,7 +7,9 @@ Fills the ghosts once, then calls kl_launch_with_config `reps` times (or
 kl_launch with the committed wisdom when --config is "wisdom").  With --time
 the launches are timed with CUDA events (after three warm-up launches) and a
 JSON line gives the median kernel time, Gpts/s and algorithmic GB/s for each
-configuration of a list separated by ';'.
+configuration of a list separated by ';'.  With --diag none|ref, one launch
+is followed by `reps` FP64 diagnostics (kl_diag) of ut, without a reference
+or against an FP64 copy of it.
 """
 
 from __future__ import annotations
@@ -28,6 +30,9 @@ def main(argv=None):
     ap.add_argument("--config", default="wisdom")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--time", action="store_true", help="time the launches (CUDA events)")
+    ap.add_argument("--diag", choices=["none", "ref"], default=None,
+                    help="after one launch, `reps` kl_diag calls on ut: without a reference, "
+                         "or with an FP64 reference field")
     args = ap.parse_args(argv)
     import torch
     from paper_2303_12374_gb300 import kl
@@ -38,7 +43,18 @@ def main(argv=None):
         p, op, bufs, outs, fl = build_problem(args.workload, args.dtype, size)
         kl.kl_fill_ghosts(ctx, p.dtype, p.grid, bufs["u"].data_ptr(), bufs["v"].data_ptr(),
                           bufs["w"].data_ptr(), bufs["nu"].data_ptr() if "nu" in bufs else None)
-        if args.time:
+        if args.diag:
+            kl.kl_launch(ctx, op, p.grid, fl)
+            ref = None
+            if args.diag == "ref":
+                ref = torch.zeros(p.extent, dtype=torch.float64, device=outs[0].device)
+                p.view(ref).copy_(p.view(outs[0]).to(torch.float64))
+            for _ in range(args.reps):
+                vals = kl.kl_diag(ctx, p.dtype, p.grid, 0, outs[0].data_ptr(),
+                                  None if ref is None else ref.data_ptr())
+            torch.cuda.synchronize()
+            print("diag", list(vals))
+        elif args.time:
             import json
             import statistics
             from paper_2303_12374_gb300 import synth
