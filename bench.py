@@ -284,8 +284,9 @@ def e2e_run(ctx, p, f, op, device, steps, overlap=True):
     """Steps from host data to host results through the public API.
 
     Every step copies the interior of u, v, w from pinned host memory into the
-    padded device buffers, runs kl_step (ghost fill + tendencies) and copies
-    the interior of ut, vt, wt back to pinned host memory.  overlap=True runs
+    padded device buffers (kl_copy_in: one strided DMA copy per field), runs
+    kl_step (ghost fill + tendencies) and copies the interior of ut, vt, wt
+    back to pinned host memory (kl_copy_out).  overlap=True runs
     the three stages of consecutive steps on three streams with two device
     buffer sets (step i's copy-in overlaps step i-1's kernels and step i-2's
     copy-out); overlap=False runs them one after the other on one stream.
@@ -314,7 +315,7 @@ def e2e_run(ctx, p, f, op, device, steps, overlap=True):
             if i >= nbuf:
                 s_in.wait_event(ev_c[b])        # step i - nbuf's kernels read dev_in[b]
             for h, d in zip(host_in, dev_in[b]):
-                p.view(d).copy_(h, non_blocking=True)
+                kl.kl_copy_in(p.dtype, p.grid, h.data_ptr(), d.data_ptr(), s_in.cuda_stream)
             ev_in[b].record(s_in)
         with torch.cuda.stream(s_c):
             s_c.wait_event(ev_in[b])
@@ -325,7 +326,7 @@ def e2e_run(ctx, p, f, op, device, steps, overlap=True):
         with torch.cuda.stream(s_out):
             s_out.wait_event(ev_c[b])
             for h, d in zip(host_out, dev_out[b]):
-                h.copy_(p.view(d), non_blocking=True)
+                kl.kl_copy_out(p.dtype, p.grid, d.data_ptr(), h.data_ptr(), s_out.cuda_stream)
             ev_out[b].record(s_out)
 
     for i in range(2 * nbuf):                   # warm-up (allocator, module, pinned paths)
@@ -339,6 +340,37 @@ def e2e_run(ctx, p, f, op, device, steps, overlap=True):
     torch.cuda.synchronize()
     es = host_in[0].element_size()
     return a.elapsed_time(b) / steps, 3 * p.nx * p.ny * p.nz * es
+
+
+def link_bound_ms(p, device, reps=5):
+    """The host link's own time for one e2e step's traffic: three interior
+    fields host -> device and three device -> host as plain contiguous copies
+    from and to pinned memory, the two directions at once on two streams."""
+    import torch
+    shape = (p.nz, p.ny, p.nx)
+    h_in = [torch.empty(shape, dtype=p.tdtype).pin_memory() for _ in range(3)]
+    h_out = [torch.empty(shape, dtype=p.tdtype).pin_memory() for _ in range(3)]
+    d_in = [torch.empty(shape, dtype=p.tdtype, device=device) for _ in range(3)]
+    d_out = [torch.empty(shape, dtype=p.tdtype, device=device) for _ in range(3)]
+    s1, s2 = torch.cuda.Stream(device), torch.cuda.Stream(device)
+
+    def once():
+        with torch.cuda.stream(s1):
+            for h, d in zip(h_in, d_in):
+                d.copy_(h, non_blocking=True)
+        with torch.cuda.stream(s2):
+            for h, d in zip(h_out, d_out):
+                h.copy_(d, non_blocking=True)
+
+    once()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        once()
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) / reps * 1e3
+    del h_in, h_out, d_in, d_out
+    return ms
 
 
 def alu_peaks_live():
@@ -785,6 +817,7 @@ def main():
               for _ in range(3)]
     s_runs = [e2e_run(ctx, p, f, op, device, max(5, args.steps // 200), overlap=False)
               for _ in range(3)]
+    link_ms = link_bound_ms(p, device)
     barrier()
     e_ms, e_bytes = statistics.median(r[0] for r in e_runs), e_runs[0][1]
     s_ms = statistics.median(r[0] for r in s_runs)
@@ -793,9 +826,12 @@ def main():
     e2e = {"value": job_value(world, pts, 1, e_ms), "unit": "Gpts/s",
            "h2d_bytes_per_step": e_bytes, "d2h_bytes_per_step": e_bytes,
            "ms_per_step": e_ms,
-           "api": "kl_step; torch copies of the interior u, v, w in and ut, vt, wt out",
+           "api": "kl_copy_in (u, v, w), kl_step, kl_copy_out (ut, vt, wt)",
            "pipeline": "copy-in, kl_step and copy-out of consecutive steps overlap on three "
                        "streams (two device buffer sets)",
+           "link_bound": {"ms_per_step": link_ms, "frac": link_ms / e_ms,
+                          "note": "the same bytes as plain contiguous copies, both directions "
+                                  "at once: the host link's time for one step"},
            "repeats_ms": [r[0] for r in e_runs],
            "serial": {"value": job_value(world, pts, 1, s_ms), "ms_per_step": s_ms,
                       "repeats_ms": [r[0] for r in s_runs]}}

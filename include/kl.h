@@ -176,6 +176,23 @@ kl_status kl_halo_unpack(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, int32_
                          void *stream);
 
 /*
+ * Interior data between a HOST array and a padded DEVICE field of layout
+ * `grid` (storage dtype): kl_copy_in copies host[k][j][i] (nz x ny x nx,
+ * contiguous, i fastest) to the interior points (i, j, k) of `dev` (the
+ * padded buffer's base, as in kl_fields); kl_copy_out copies the interior of
+ * `dev` to `host`.  Ghost cells are neither read nor written.  One strided
+ * DMA copy per call (the layout's row and plane pitches), asynchronous on
+ * `stream` when `host` is page-locked (cudaHostAlloc / cudaHostRegister),
+ * otherwise as cudaMemcpy3DAsync behaves for pageable memory.  The copies
+ * are the data movement around the paper's hot path (MicroHH keeps its
+ * fields on the GPU; a caller whose data starts on the host uses these):
+ * no stencil arithmetic.  KL_ERR_INVALID_ARG for NULL pointers, a bad dtype
+ * or layout; KL_ERR_CUDA if the copy cannot be issued.
+ */
+kl_status kl_copy_in(int32_t dtype, const kl_grid *grid, const void *host, void *dev, void *stream);
+kl_status kl_copy_out(int32_t dtype, const kl_grid *grid, const void *dev, void *host, void *stream);
+
+/*
  * Tendencies ut, vt, wt of (u, v, w) on the interior (Sec. 5.2 stencils),
  * ghosts of the inputs already filled.  The configuration is selected from
  * the wisdom file of (op, dtype) by the heuristic of Sec. 4.5 and compiled
@@ -235,7 +252,7 @@ kl_status kl_launch_with_config(kl_ctx *ctx, const kl_op *op, const char *config
  * together.  A grid that configuration does not fit (shared memory, TMA box)
  * takes the record of its own nearest tuned size (Sec. 4.5 fuzzy matching,
  * Sec. 6).  Records tuned with persistent CTAs (pe) run here as z chunks of
- * at most 16 levels.  Grids sharing a configuration run in one launch over a
+ * at most 32 levels.  Grids sharing a configuration run in one launch over a
  * device tile table, and the launches of all classes are issued on
  * `stream`; kl_stats reports the classes of the last batch planned.
  */

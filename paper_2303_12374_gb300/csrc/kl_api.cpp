@@ -759,6 +759,51 @@ kl_status kl_fill_ghosts(kl_ctx *ctx, int32_t dtype, const kl_grid *grid, void *
 
 // ------------------------------------------------------- halo strips
 
+// one strided copy between a contiguous host array and the interior of a
+// padded device field: cudaMemcpy3DAsync when the plane pitch is a whole
+// number of rows, else one 2D copy per level
+static kl_status copy_interior(int32_t dtype, const kl_grid *grid, const void *host, void *dev,
+                               bool in, void *stream)
+{
+    if (!host || !dev) return fail(KL_ERR_INVALID_ARG, "host and dev must not be NULL");
+    if (dtype < 0 || dtype > 3) return fail(KL_ERR_INVALID_ARG, "dtype must be 0..3");
+    kl_status st = check_grid(grid, 0, nullptr);
+    if (st) return st;
+    const size_t es = (size_t)esize_of(dtype);
+    const kl_grid &g = *grid;
+    char *d0 = (char *)dev + (size_t)g.origin * es;
+    const size_t row = (size_t)g.nx * es;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (g.sk % g.sj == 0) {
+        cudaMemcpy3DParms p = {};
+        cudaPitchedPtr dp = make_cudaPitchedPtr(d0, (size_t)g.sj * es, row, (size_t)(g.sk / g.sj));
+        cudaPitchedPtr hp = make_cudaPitchedPtr((void *)host, row, row, (size_t)g.ny);
+        p.extent = make_cudaExtent(row, (size_t)g.ny, (size_t)g.nz);
+        if (in) {
+            p.srcPtr = hp;
+            p.dstPtr = dp;
+            p.kind = cudaMemcpyHostToDevice;
+        } else {
+            p.srcPtr = dp;
+            p.dstPtr = hp;
+            p.kind = cudaMemcpyDeviceToHost;
+        }
+        e = cudaMemcpy3DAsync(&p, s);
+    } else {
+        for (int k = 0; k < g.nz && e == cudaSuccess; ++k) {
+            char *dk = d0 + (size_t)k * g.sk * es;
+            char *hk = (char *)host + (size_t)k * g.ny * row;
+            e = in ? cudaMemcpy2DAsync(dk, (size_t)g.sj * es, hk, row, row, (size_t)g.ny,
+                                       cudaMemcpyHostToDevice, s)
+                   : cudaMemcpy2DAsync(hk, row, dk, (size_t)g.sj * es, row, (size_t)g.ny,
+                                       cudaMemcpyDeviceToHost, s);
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(e, in ? "kl_copy_in" : "kl_copy_out");
+    return KL_OK;
+}
+
 static kl_status halo_check(int32_t dtype, const kl_grid *grid, int32_t axis, int32_t side,
                             int32_t nf)
 {
@@ -767,6 +812,16 @@ static kl_status halo_check(int32_t dtype, const kl_grid *grid, int32_t axis, in
     if (side != 0 && side != 1) return fail(KL_ERR_INVALID_ARG, "side must be 0 or 1");
     if (nf < 1 || nf > 4) return fail(KL_ERR_INVALID_ARG, "nf must be 1..4");
     return check_grid(grid, 1, nullptr);
+}
+
+kl_status kl_copy_in(int32_t dtype, const kl_grid *grid, const void *host, void *dev, void *stream)
+{
+    return copy_interior(dtype, grid, host, dev, true, stream);
+}
+
+kl_status kl_copy_out(int32_t dtype, const kl_grid *grid, const void *dev, void *host, void *stream)
+{
+    return copy_interior(dtype, grid, host, (void *)dev, false, stream);
 }
 
 kl_status kl_halo_bytes(const kl_grid *grid, int32_t dtype, int32_t axis, int32_t nf,

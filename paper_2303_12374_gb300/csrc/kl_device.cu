@@ -262,7 +262,6 @@ struct DiagArgs {
     int nx, ny, nz;
     long long n;
     double *partial;         // nblocks x 6
-    int vec4;                // f32 rows read as float4 (nx, strides, base: multiples of 4 floats)
 };
 
 template <typename T> __device__ __forceinline__ double to_d(T x) { return (double)x; }
@@ -388,25 +387,6 @@ __global__ void __launch_bounds__(256) diag_kernel(DiagArgs a)
                         v[3] = fma(rv, rv, v[3]);
                     }
                     rs += tv;
-                }
-            } else if (sizeof(T) == 4 && a.vec4) {
-                // four 16-byte loads per lane in flight (512 values per warp)
-                for (int i0 = 4 * lane; i0 < a.nx; i0 += 128 * 4) {
-                    float4 x4[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        x4[u] = i0 + 128 * u < a.nx ? *(const float4 *)(t + o0 + i0 + 128 * u)
-                                                    : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const float x[4] = {x4[u].x, x4[u].y, x4[u].z, x4[u].w};
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            tmax = fmaxf(tmax, fabsf(x[c]));
-                            ff_add(s1, x[c]);
-                            ff_add_square(s2, x[c]);
-                        }
-                    }
                 }
             } else {
                 // eight loads per lane in flight before the arithmetic
@@ -573,6 +553,20 @@ cudaError_t fill_ghosts_launch(int esize, const kl_grid &g, void *u, void *v, vo
 
 int diag_blocks(int nsm) { return nsm * 8; }
 
+// At most nmax blocks of 256 threads, and no more than fit on the device at
+// once: the reductions give each warp a fixed share of the rows, so a partial
+// second wave would double the time of the blocks it holds.
+template <typename K>
+static int one_wave(K kernel, int nmax)
+{
+    int dev = 0, nsm = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 256, 0) != cudaSuccess)
+        return nmax;
+    return std::max(1, std::min(nmax, per * nsm));
+}
+
 cudaError_t diag_launch(int dtype, const kl_grid &g, int level, const void *t, const double *ref,
                         const double *wz, double *scratch, int nblocks, double *dout,
                         cudaStream_t s)
@@ -590,17 +584,19 @@ cudaError_t diag_launch(int dtype, const kl_grid &g, int level, const void *t, c
     a.nz = g.nz;
     a.n = (long long)g.nx * g.ny * g.nz;
     a.partial = scratch;
-    a.vec4 = dtype == KL_F32 && g.nx % 4 == 0 && g.sj % 4 == 0 && g.sk % 4 == 0 &&
-             (uintptr_t)a.t % 16 == 0;
+    auto go = [&](auto kernel) {
+        nblocks = one_wave(kernel, nblocks);
+        kernel<<<nblocks, 256, 0, s>>>(a);
+    };
     switch (dtype * 2 + (ref ? 1 : 0)) {
-    case 2 * KL_F64: diag_kernel<double, false><<<nblocks, 256, 0, s>>>(a); break;
-    case 2 * KL_F64 + 1: diag_kernel<double, true><<<nblocks, 256, 0, s>>>(a); break;
-    case 2 * KL_F32: diag_kernel<float, false><<<nblocks, 256, 0, s>>>(a); break;
-    case 2 * KL_F32 + 1: diag_kernel<float, true><<<nblocks, 256, 0, s>>>(a); break;
-    case 2 * KL_BF16: diag_kernel<__nv_bfloat16, false><<<nblocks, 256, 0, s>>>(a); break;
-    case 2 * KL_BF16 + 1: diag_kernel<__nv_bfloat16, true><<<nblocks, 256, 0, s>>>(a); break;
-    case 2 * KL_F16: diag_kernel<__half, false><<<nblocks, 256, 0, s>>>(a); break;
-    default: diag_kernel<__half, true><<<nblocks, 256, 0, s>>>(a); break;
+    case 2 * KL_F64: go(diag_kernel<double, false>); break;
+    case 2 * KL_F64 + 1: go(diag_kernel<double, true>); break;
+    case 2 * KL_F32: go(diag_kernel<float, false>); break;
+    case 2 * KL_F32 + 1: go(diag_kernel<float, true>); break;
+    case 2 * KL_BF16: go(diag_kernel<__nv_bfloat16, false>); break;
+    case 2 * KL_BF16 + 1: go(diag_kernel<__nv_bfloat16, true>); break;
+    case 2 * KL_F16: go(diag_kernel<__half, false>); break;
+    default: go(diag_kernel<__half, true>); break;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -624,13 +620,16 @@ cudaError_t dot_launch(int dtype, const kl_grid &g, const void *x, const void *y
     a.nz = g.nz;
     a.n = (long long)g.nx * g.ny * g.nz;
     a.partial = scratch;
-    a.vec4 = 0;
     const void *yb = (const char *)y + (size_t)g.origin * es;
+    auto go = [&](auto kernel) {
+        nblocks = one_wave(kernel, nblocks);
+        kernel<<<nblocks, 256, 0, s>>>(a, yb);
+    };
     switch (dtype) {
-    case KL_F64: dot_kernel<double><<<nblocks, 256, 0, s>>>(a, yb); break;
-    case KL_F32: dot_kernel<float><<<nblocks, 256, 0, s>>>(a, yb); break;
-    case KL_BF16: dot_kernel<__nv_bfloat16><<<nblocks, 256, 0, s>>>(a, yb); break;
-    default: dot_kernel<__half><<<nblocks, 256, 0, s>>>(a, yb); break;
+    case KL_F64: go(dot_kernel<double>); break;
+    case KL_F32: go(dot_kernel<float>); break;
+    case KL_BF16: go(dot_kernel<__nv_bfloat16>); break;
+    default: go(dot_kernel<__half>); break;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -740,7 +739,6 @@ extern "C" kl_status kl_diag_noalloc(int32_t dtype, const kl_grid *grid, const v
     a.nz = grid->nz;
     a.n = n;
     a.partial = scratch;
-    a.vec4 = 0;
     cudaStream_t s = (cudaStream_t)stream;
     switch (dtype) {
     case KL_F64: diag_kernel_fixed<double><<<(unsigned)nb, 256, 0, s>>>(a); break;

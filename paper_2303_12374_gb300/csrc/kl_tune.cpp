@@ -1030,10 +1030,10 @@ kl_status kl_launch_batched(kl_ctx *ctx, const kl_op *op, int32_t n, const kl_gr
         // (persistent CTAs over a class's tiles, in equal ranges that cross
         // from one grid to the next, measured slower than chunks that the
         // block scheduler balances); a record tuned with pe=1 or 2 (whose
-        // launches ignore kc) takes chunks of at most 16 levels here
+        // launches ignore kc) takes chunks of at most 32 levels here
         if (cfg.family == 2 && cfg.pe) {
             cfg.pe = 0;
-            cfg.kc = std::min(cfg.kc, 16);
+            cfg.kc = std::min(cfg.kc, 32);
         }
         std::string err;
         if (!config_fits(*op, cfg, grids[i], &fields[i], &err)) cfg = Config();

@@ -116,6 +116,8 @@ SIGNATURES = {
     "kl_def_tune": ([_P, _P, _S, _S, _S], ctypes.c_int),
     "kl_smagorinsky": ([_P, _I32, ctypes.POINTER(Grid), _D, _P, _P, _P, _P, _I32, _P],
                        ctypes.c_int),
+    "kl_copy_in": ([_I32, ctypes.POINTER(Grid), _P, _P, _P], ctypes.c_int),
+    "kl_copy_out": ([_I32, ctypes.POINTER(Grid), _P, _P, _P], ctypes.c_int),
     "kl_halo_bytes": ([ctypes.POINTER(Grid), _I32, _I32, _I32, ctypes.POINTER(_I64)], ctypes.c_int),
     "kl_halo_pack": ([_P, _I32, ctypes.POINTER(Grid), _I32, _I32, _I32, ctypes.POINTER(_P), _P, _P],
                      ctypes.c_int),
@@ -183,6 +185,15 @@ def kl_layout(nx, ny, nz, g, dtype):
 
 def kl_fill_ghosts(ctx, dtype, grid: Grid, u, v, w, nu=None, stream=None) -> None:
     check(load().kl_fill_ghosts(ctx, dtype, ctypes.byref(grid), u, v, w, nu, stream))
+
+
+def kl_copy_in(dtype, grid: Grid, host, dev, stream=None) -> None:
+    """host: address of a contiguous nz x ny x nx host array; dev: the padded device field."""
+    check(load().kl_copy_in(dtype, ctypes.byref(grid), host, dev, stream))
+
+
+def kl_copy_out(dtype, grid: Grid, dev, host, stream=None) -> None:
+    check(load().kl_copy_out(dtype, ctypes.byref(grid), dev, host, stream))
 
 
 def kl_halo_bytes(grid: Grid, dtype, axis, nf) -> int:

@@ -319,9 +319,8 @@ def test_diag_matches_oracle(ctx, oracle_mod):
 @pytest.mark.parametrize("shape", [(70, 33, 21), (136, 20, 9)])
 def test_diag_without_reference(ctx, oracle_mod, dtype, shape):
     """No reference: f32 and 16-bit sums run in float-float, folded into FP64
-    per level; they must match an FP64 reduction of the same values.  With f32
-    storage, nx = 136 (a multiple of 4 in a padded layout) takes the 16-byte
-    row loads, ragged in the last of the four loads per lane."""
+    per level; they must match an FP64 reduction of the same values (two
+    row lengths)."""
     nx, ny, nz = shape
     f = make_inputs(nx, ny, nz, seed=19, walls=True, stretch=2.0)
     from paper_2303_12374_gb300 import kl

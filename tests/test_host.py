@@ -336,3 +336,14 @@ def test_c_abi_from_plain_c(tmp_path):
     r = subprocess.run([exe, str(tmp_path)], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.strip().endswith("all ok")
+
+
+def test_copy_in_out_reject_bad_arguments_before_any_cuda_call():
+    grid = kl.Grid(8, 8, 8, 1, 10, 100, 111, 1000, 1, 0, 0.125, 0.125, 0.125, 1e-3, None)
+    with pytest.raises(kl.KLError):
+        kl.kl_copy_in(1, grid, None, 1, None)
+    with pytest.raises(kl.KLError):
+        kl.kl_copy_out(7, grid, 1, 1, None)
+    bad = kl.Grid(8, 8, 8, 1, 4, 100, 111, 1000, 1, 0, 0.125, 0.125, 0.125, 1e-3, None)
+    with pytest.raises(kl.KLError):                # sj smaller than a padded row
+        kl.kl_copy_in(1, bad, 1, 1, None)
