@@ -157,10 +157,12 @@ size_t zmarch_smem_bytes(const kl_op &op, const Config &c)
     // ring + 128 B of alignment slack + one 8-byte mbarrier per slot
     size_t bytes = z.plane_bytes * z.nf * c.ns + 256;
     if (c.family == 2 && op.diff == 2) {
-        // zpack, variable nu: u, v, w ring + a nu ring of ns - 2R + 2 planes
-        // of tys + 2 rows; no x-wrap strips
+        // zpack, variable nu: u, v, w ring + a nu ring of tys + 2 rows per
+        // plane, ns - 2R + 2 planes (ns - R + 1 for a carried ring of fewer
+        // than 2R + 2 slots); no x-wrap strips
         size_t nplane = ((size_t)z.pitch * (z.tys + 2) * esize_of(op.dtype) + 127) / 128 * 128;
-        bytes = z.plane_bytes * 3 * c.ns + nplane * (c.ns - 2 * z.halo + 2) + 256;
+        const int nns = c.ns < 2 * z.halo + 2 ? c.ns - z.halo + 1 : c.ns - 2 * z.halo + 2;
+        bytes = z.plane_bytes * 3 * c.ns + nplane * nns + 256;
     } else if (c.family == 2) {
         // zpack x-wrap strips: 3 fields x rows x 32 bytes per slot (128-B multiples)
         bytes += 3 * (size_t)((z.rows * 32 + 127) / 128 * 128) * c.ns;
@@ -250,10 +252,10 @@ bool config_check(const kl_op &op, const Config &c, std::string *err)
             return false;
         }
         int reach = halo_of(op);
-        // zpack with constant nu may carry plane k-2 in registers (ring of
+        // zpack (one warp group) may carry plane k-2 in registers (ring of
         // planes k-1 .. k+R plus one in flight: 2R slots)
-        const bool carry_ok = c.family == 2 && op.diff != 2 && !c.cs && reach >= 2;
-        if (c.family == 2 && c.yx == 2 && !(carry_ok && c.ns < 2 * reach + 2)) {
+        const bool carry_ok = c.family == 2 && !c.cs && reach >= 2;
+        if (c.family == 2 && c.yx == 2 && !(carry_ok && op.diff != 2 && c.ns < 2 * reach + 2)) {
             *err = "yx=2 needs a ring of fewer than 2R+2 slots (2R or 2R+1), constant nu and cs=0";
             return false;
         }

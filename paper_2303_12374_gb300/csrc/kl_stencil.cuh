@@ -1172,20 +1172,25 @@ __device__ __forceinline__ void kl_cs_level(const kl_args &a, const kl_vk &K, co
 #define KL_NROWS (KL_TYS + 2)                                // nu box: tile rows -1 .. TYS
 #define KL_NBOX (KL_PITCH * KL_NROWS * (int)sizeof(T))
 #define KL_NPLANE KL_RUP(KL_NBOX, 128)
-#define KL_NNS (KL_NS - 2 * KL_R + 2)                        // nu ring slots
 #define KL_NLEAD (KL_R - 1)                                  // nu plane p - NLEAD rides with plane p
 #else
 #define KL_ZSLOT (3 * KL_PLANE_BYTES + 3 * KL_STRIP_BYTES)   // zpack ring slot
 #endif
-// carry mode: with constant nu and one warp group, a ring of fewer than 2R+2
-// slots holds planes k-1 .. k+R plus one in flight; the own-column values of
-// plane k-2 that the vertical windows still need were read at the level
-// before and stay in registers.  The first level's bottom faces, which reach
-// down to plane kb-R, are formed before the level loop while planes
-// kb-R .. kb+R-1 fill the ring.
+// carry mode: with one warp group, a ring of fewer than 2R+2 slots holds
+// planes k-1 .. k+R plus one in flight; the own-column values of plane k-2
+// that the vertical windows still need were read at the level before and
+// stay in registers.  The first level's bottom faces, which reach down to
+// plane kb-R, are formed before the level loop while planes kb-R .. kb+R-1
+// fill the ring.  (Variable nu reads plane k-1 and above only.)
 #define KL_CARRY (KL_NS < 2 * KL_R + 2)
-#if KL_CARRY && (KL_DIFF == 2 || KL_CS || KL_NS < 2 * KL_R || KL_R < 2)
-#error "a ring of fewer than 2R+2 slots needs constant nu, cs=0, R >= 2 and at least 2R slots"
+#if KL_CARRY && (KL_CS || KL_NS < 2 * KL_R || KL_R < 2)
+#error "a ring of fewer than 2R+2 slots needs cs=0, R >= 2 and at least 2R slots"
+#endif
+#if KL_DIFF == 2
+// nu ring slots: planes k-1 .. k+1 plus one per u, v, w plane in flight
+// (nu plane q rides with plane q + NLEAD): the ring holds planes k-R .. k+R,
+// or k-1 .. k+R in carry mode, and the rest of its slots are in flight
+#define KL_NNS (KL_CARRY ? KL_NS - KL_R + 1 : KL_NS - 2 * KL_R + 2)
 #endif
 #define KL_NT (32 * KL_MBY * (KL_CS ? 3 : 1))                // threads per block
 #define KL_XW_Q ((3 * KL_ROWS * KL_H + KL_NT - 1) / KL_NT)   // halo values per thread

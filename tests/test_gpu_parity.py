@@ -165,6 +165,24 @@ def test_carried_plane_ring_is_bit_identical(ctx, dtype, walls, adv):
 
 
 @pytest.mark.parametrize("dtype", [0, 1, 3])
+@pytest.mark.parametrize("walls", [True, False])
+def test_carried_plane_ring_variable_nu_is_bit_identical(ctx, dtype, walls):
+    """Variable nu with the carried ring (2R or 2R+1 slots, nu in a ring of
+    ns - R + 1 planes): the same bits as the 2R+2-slot ring, with z chunks and
+    with persistent CTAs."""
+    f = make_inputs(131, 45, 23, seed=13, walls=walls, stretch=2.0, var_nu=True)
+    res = []
+    for ns, pe in ((8, 0), (6, 0), (7, 0), (6, 1), (7, 2), (9, 1)):
+        cfg = f"zpack:w=2,ly=2,kc=8,ns={ns},minb=1,pe={pe}"
+        p, _, outs, _ = run_gpu(ctx, f, adv=5, diff=2, dtype=dtype, walls=walls, g=3,
+                                stretched=True, config=cfg)
+        res.append([p.download(outs[k]) for k in ("ut", "vt", "wt")])
+    for other in res[1:]:
+        for a, b in zip(res[0], other):
+            assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("dtype", [0, 1, 3])
 @pytest.mark.parametrize("nx,ny,nz,walls,adv", [
     (67, 20, 9, True, 5),     # narrowest grid the kernel wraps itself (64 + 3)
     (128, 12, 7, False, 5),   # the right halo lies in the last tile
@@ -211,7 +229,8 @@ def test_zpack_variable_nu(ctx, oracle_mod, dtype, nx, ny, nz, walls, adv, stret
     f = make_inputs(nx, ny, nz, seed=nx * ny, walls=walls, stretch=stretch, var_nu=True)
     ran = 0
     for cfg in ("zpack:w=4,ly=2,kc=8,ns=8,minb=1", "zpack:w=2,ly=4,kc=4,ns=9,minb=1",
-                "zpack:w=1,ly=1,kc=16,ns=10,minb=1"):
+                "zpack:w=1,ly=1,kc=16,ns=10,minb=1", "zpack:w=4,ly=2,kc=8,ns=6,minb=1",
+                "zpack:w=2,ly=3,kc=4,ns=7,minb=1,pe=1"):
         try:
             kl.kl_config_normalize(kl.Op(adv, 2, dtype, 0), cfg)
         except kl.KLError:
