@@ -57,3 +57,39 @@ def test_copy_in_out_interior_bit_exact(dtype, odd_pitch, pinned):
     kl.kl_copy_out(dtype, grid, dev.data_ptr(), out.data_ptr(), stream.cuda_stream)
     stream.synchronize()
     assert torch.equal(out.view(ibits), host.view(ibits))
+
+
+@pytest.mark.parametrize("dtype", [0, 1, 2])
+def test_host_to_host_step_matches_oracle(oracle_mod, dtype):
+    """The path a caller with host data takes (and the bench's e2e times):
+    kl_copy_in of u, v, w from pinned host arrays, kl_step, kl_copy_out of
+    ut, vt, wt, all on one stream; the host results equal the oracle's."""
+    import torch
+    from gpu_cases import TOL, make_inputs, oracle_ref, rel_err
+    from paper_2303_12374_gb300 import kl
+    from paper_2303_12374_gb300.problem import Problem
+    nx, ny, nz = 70, 45, 23
+    f = make_inputs(nx, ny, nz, seed=77, walls=True, stretch=2.0)
+    p = Problem(nx, ny, nz, g=3, dtype=dtype, walls=True, zh=f["zh"], nu=1e-3)
+    ctx = kl.kl_create(0, None)
+    try:
+        host_in = [torch.from_numpy(f[k].copy()).to(p.tdtype).pin_memory() for k in ("u", "v", "w")]
+        host_out = [torch.empty((nz, ny, nx), dtype=p.tdtype).pin_memory() for _ in range(3)]
+        dev_in = [p.empty() for _ in range(3)]
+        dev_out = [p.empty() for _ in range(3)]
+        s = torch.cuda.Stream()
+        for h, d in zip(host_in, dev_in):
+            kl.kl_copy_in(p.dtype, p.grid, h.data_ptr(), d.data_ptr(), s.cuda_stream)
+        fl = kl.Fields(*[d.data_ptr() for d in dev_in], None, *[d.data_ptr() for d in dev_out])
+        kl.kl_step(ctx, kl.Op(5, 1, p.dtype, 0), p.grid, fl, s.cuda_stream)
+        for h, d in zip(host_out, dev_out):
+            kl.kl_copy_out(p.dtype, p.grid, d.data_ptr(), h.data_ptr(), s.cuda_stream)
+        s.synchronize()
+        kl.kl_check(ctx)
+        rin = {k: p.rounded(f[k]) for k in ("u", "v", "w")}
+        ref = oracle_ref(oracle_mod, rin, f["zh"], adv=5, diff=1, walls=True, g=3)
+        for h, r in zip(host_out, ref):
+            got = h.to(torch.float64).numpy()
+            assert rel_err(got, r) <= TOL[dtype]
+    finally:
+        kl.kl_destroy(ctx)
