@@ -562,9 +562,9 @@ def les_step(ctx, stream, peak_gbs, reps=20, cs=0.1):
 
 
 def batched_run(ctx, device, stream, peak_gbs, reps=20):
-    """64 uneven grids: one batched call (tuned size classes, one CUDA graph)
-    vs 64 separate launches with the same wisdom selection (tuned) and vs 64
-    separate default launches."""
+    """64 uneven grids: one batched call (the batch's wisdom configuration,
+    one CUDA graph) vs 64 separate launches, each with its own nearest-size
+    record (tuned), and vs 64 separate default launches."""
     import torch
     from paper_2303_12374_gb300 import kl, synth
     from paper_2303_12374_gb300.problem import Problem

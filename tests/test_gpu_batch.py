@@ -1,5 +1,7 @@
-"""Batched execution: many grids of uneven sizes, one launch per size class,
-configurations from wisdom by nearest size (Sec. 4.5, Sec. 6 fuzzy matching)."""
+"""Batched execution: many grids of uneven sizes under the configuration of
+the wisdom record nearest to the batch's total point count (grids it does
+not fit take their own nearest-size record, Sec. 4.5 and Sec. 6 fuzzy
+matching); one launch per configuration class, one CUDA graph."""
 
 from __future__ import annotations
 

@@ -169,9 +169,9 @@ def test_les_1024x1024x64_stretched_variable_nu_sampled(ctx, oracle_mod):
 
 
 def test_batch64_uneven_as_bench_times_it(oracle_mod):
-    """The 64-grid batch of the bench (uneven sizes, tuned size classes from
-    the committed wisdom, one CUDA graph) against the oracle on three levels of
-    every grid (the two wall-side levels and a middle one)."""
+    """The 64-grid batch of the bench (uneven sizes, the configuration the
+    committed wisdom gives the batch, one CUDA graph) against the oracle on
+    three levels of every grid (the two wall-side levels and a middle one)."""
     import torch
     from paper_2303_12374_gb300 import kl, synth
     from paper_2303_12374_gb300.problem import Problem
