@@ -988,11 +988,97 @@ template <> struct Quad<__half, float> {
     }
 };
 
+// One level of the R-row, four-point layout: the values a thread reads at
+// level k + 1 (its rows, v on their faces, w in the rows below and above
+// them) and at level k (u in rows j - 1 and j + R, v at x = i - 1 and i + 4).
+template <typename C, int R>
+struct SmagLevel {
+    C Un[R][5], Vn[R + 1][4], Wn[R][4], Wm[4], Wp[4], wl[R], wr[R];
+    C Ujm[5], Ujp[5], vm[R + 1], vp[R + 1];
+};
+
+// The strains of one level and nu at the thread's 4 x R points, from the
+// carried level-k values (U, V, W and the vertical-edge strains below) and
+// the level's reads L; EXZn, EYZn are the vertical-edge strains above.
+template <typename C, int R>
+__device__ __forceinline__ void smag_level_math(const SmagLevel<C, R> &L, const C (&U)[R][5],
+                                                const C (&V)[R + 1][4], const C (&W)[R][4],
+                                                const C (&EXZ)[R][5], const C (&EYZ)[R + 1][4],
+                                                C zi, C dzik, C dxi, C dyi, C cc,
+                                                C (&EXZn)[R][5], C (&EYZn)[R + 1][4], C (&out)[R][4])
+{
+    const C half = (C)0.5;
+    C E[R + 1][5];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int e = 0; e < 5; ++e) {
+            const C whi = e == 4 ? L.wr[r] : L.Wn[r][e], wlo = e == 0 ? L.wl[r] : L.Wn[r][e - 1];
+            EXZn[r][e] = half * ((L.Un[r][e] - U[r][e]) * zi + (whi - wlo) * dxi);
+        }
+#pragma unroll
+    for (int y = 0; y <= R; ++y) {
+#pragma unroll
+        for (int e = 0; e < 5; ++e) {
+            const C uhi = y == R ? L.Ujp[e] : U[y][e], ulo = y == 0 ? L.Ujm[e] : U[y - 1][e];
+            const C vr = e == 4 ? L.vp[y] : V[y][e], vl = e == 0 ? L.vm[y] : V[y][e - 1];
+            E[y][e] = half * ((uhi - ulo) * dyi + (vr - vl) * dxi);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const C whi = y == R ? L.Wp[q] : L.Wn[y][q], wlo = y == 0 ? L.Wm[q] : L.Wn[y - 1][q];
+            EYZn[y][q] = half * ((L.Vn[y][q] - V[y][q]) * zi + (whi - wlo) * dyi);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const C sxx = (U[r][q + 1] - U[r][q]) * dxi, syy = (V[r + 1][q] - V[r][q]) * dyi;
+            const C szz = (L.Wn[r][q] - W[r][q]) * dzik;
+            C s2 = (C)2 * (sxx * sxx + syy * syy + szz * szz);
+            s2 += E[r][q] * E[r][q] + E[r][q + 1] * E[r][q + 1] + E[r + 1][q] * E[r + 1][q] +
+                  E[r + 1][q + 1] * E[r + 1][q + 1];
+            s2 += EXZ[r][q] * EXZ[r][q] + EXZ[r][q + 1] * EXZ[r][q + 1] + EXZn[r][q] * EXZn[r][q] +
+                  EXZn[r][q + 1] * EXZn[r][q + 1];
+            s2 += EYZ[r][q] * EYZ[r][q] + EYZ[r + 1][q] * EYZ[r + 1][q] + EYZn[r][q] * EYZn[r][q] +
+                  EYZn[r + 1][q] * EYZn[r + 1][q];
+            out[r][q] = cc * sqrt(s2);
+        }
+}
+
+// Carry level k + 1 into the level-k state.
+template <typename C, int R>
+__device__ __forceinline__ void smag_carry(const SmagLevel<C, R> &L, const C (&EXZn)[R][5],
+                                           const C (&EYZn)[R + 1][4], C (&U)[R][5], C (&V)[R + 1][4],
+                                           C (&W)[R][4], C (&EXZ)[R][5], C (&EYZ)[R + 1][4])
+{
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int e = 0; e < 5; ++e) {
+            U[r][e] = L.Un[r][e];
+            EXZ[r][e] = EXZn[r][e];
+        }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) W[r][q] = L.Wn[r][q];
+#pragma unroll
+    for (int y = 0; y <= R; ++y)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            V[y][q] = L.Vn[y][q];
+            EYZ[y][q] = EYZn[y][q];
+        }
+}
+
 // R consecutive rows per thread (j .. j+R-1): the R + 1 y-edges of those rows
 // are formed once per level, so two rows share the strains of the edge
 // between them and the loads of the rows next to it (25 loads per level for
 // 8 points at R = 2 against 34 at R = 1).  Every point is formed with the
-// same operations in the same order whatever R.
+// same operations in the same order whatever R (the compiler may contract
+// different products into FMAs in the two instances).
 template <typename T, typename C, int R>
 __global__ void __launch_bounds__(SMAG_BX * SMAG_BY, sizeof(C) == 8 ? 1 : (R == 1 ? 3 : 2))
 smag_kernel4(SmagArgs a)
@@ -1053,93 +1139,34 @@ smag_kernel4(SmagArgs a)
     }
     for (int k = k0; k < k1; ++k, o += sk) {
         const long long p = o + sk;
-        // level k + 1: the thread's rows, v on their faces, w in the rows
-        // below and above them
-        C Un[R][5], Vn[R + 1][4], Wn[R][4], Wm[4], Wp[4], wl[R], wr[R];
+        SmagLevel<C, R> L;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            Q::ld(u + p + r * sj, Un[r]);
-            Un[r][4] = ldc<T, C>(u + p + r * sj + 4);
-            Q::ld(w + p + r * sj, Wn[r]);
-            wl[r] = ldc<T, C>(w + p + r * sj - 1);
-            wr[r] = ldc<T, C>(w + p + r * sj + 4);
+            Q::ld(u + p + r * sj, L.Un[r]);
+            L.Un[r][4] = ldc<T, C>(u + p + r * sj + 4);
+            Q::ld(w + p + r * sj, L.Wn[r]);
+            L.wl[r] = ldc<T, C>(w + p + r * sj - 1);
+            L.wr[r] = ldc<T, C>(w + p + r * sj + 4);
         }
 #pragma unroll
-        for (int e = 0; e <= R; ++e) Q::ld(v + p + e * sj, Vn[e]);
-        Q::ld(w + p - sj, Wm);
-        Q::ld(w + p + R * sj, Wp);
-        // level k: u in rows j - 1 and j + R, v at x = i - 1 and i + 4
-        C Ujm[5], Ujp[5], vm[R + 1], vp[R + 1];
-        Q::ld(u + o - sj, Ujm);
-        Ujm[4] = ldc<T, C>(u + o + 4 - sj);
-        Q::ld(u + o + R * sj, Ujp);
-        Ujp[4] = ldc<T, C>(u + o + 4 + R * sj);
+        for (int e = 0; e <= R; ++e) Q::ld(v + p + e * sj, L.Vn[e]);
+        Q::ld(w + p - sj, L.Wm);
+        Q::ld(w + p + R * sj, L.Wp);
+        Q::ld(u + o - sj, L.Ujm);
+        L.Ujm[4] = ldc<T, C>(u + o + 4 - sj);
+        Q::ld(u + o + R * sj, L.Ujp);
+        L.Ujp[4] = ldc<T, C>(u + o + 4 + R * sj);
 #pragma unroll
         for (int e = 0; e <= R; ++e) {
-            vm[e] = ldc<T, C>(v + o + e * sj - 1);
-            vp[e] = ldc<T, C>(v + o + e * sj + 4);
-        }
-
-        const C zi = dzhi(k + 1), dzik = dzi(k);
-        C EXZn[R][5], EYZn[R + 1][4], E[R + 1][5];
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int e = 0; e < 5; ++e) {
-                const C whi = e == 4 ? wr[r] : Wn[r][e], wlo = e == 0 ? wl[r] : Wn[r][e - 1];
-                EXZn[r][e] = half * ((Un[r][e] - U[r][e]) * zi + (whi - wlo) * dxi);
-            }
-#pragma unroll
-        for (int y = 0; y <= R; ++y) {
-#pragma unroll
-            for (int e = 0; e < 5; ++e) {
-                const C uhi = y == R ? Ujp[e] : U[y][e], ulo = y == 0 ? Ujm[e] : U[y - 1][e];
-                const C vr = e == 4 ? vp[y] : V[y][e], vl = e == 0 ? vm[y] : V[y][e - 1];
-                E[y][e] = half * ((uhi - ulo) * dyi + (vr - vl) * dxi);
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const C whi = y == R ? Wp[q] : Wn[y][q], wlo = y == 0 ? Wm[q] : Wn[y - 1][q];
-                EYZn[y][q] = half * ((Vn[y][q] - V[y][q]) * zi + (whi - wlo) * dyi);
-            }
+            L.vm[e] = ldc<T, C>(v + o + e * sj - 1);
+            L.vp[e] = ldc<T, C>(v + o + e * sj + 4);
         }
         const C cc = (C)a.cs2 * (sizeof(C) == 8 ? (C)a.cc64[k] : (C)a.cc32[k]);
+        C EXZn[R][5], EYZn[R + 1][4], out[R][4];
+        smag_level_math<C, R>(L, U, V, W, EXZ, EYZ, dzhi(k + 1), dzi(k), dxi, dyi, cc, EXZn, EYZn, out);
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            C out[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const C sxx = (U[r][q + 1] - U[r][q]) * dxi, syy = (V[r + 1][q] - V[r][q]) * dyi;
-                const C szz = (Wn[r][q] - W[r][q]) * dzik;
-                C s2 = (C)2 * (sxx * sxx + syy * syy + szz * szz);
-                s2 += E[r][q] * E[r][q] + E[r][q + 1] * E[r][q + 1] + E[r + 1][q] * E[r + 1][q] +
-                      E[r + 1][q + 1] * E[r + 1][q + 1];
-                s2 += EXZ[r][q] * EXZ[r][q] + EXZ[r][q + 1] * EXZ[r][q + 1] + EXZn[r][q] * EXZn[r][q] +
-                      EXZn[r][q + 1] * EXZn[r][q + 1];
-                s2 += EYZ[r][q] * EYZ[r][q] + EYZ[r + 1][q] * EYZ[r + 1][q] + EYZn[r][q] * EYZn[r][q] +
-                      EYZn[r + 1][q] * EYZn[r + 1][q];
-                out[q] = cc * sqrt(s2);
-            }
-            Q::st(nu + o + r * sj, out);
-        }
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int e = 0; e < 5; ++e) {
-                U[r][e] = Un[r][e];
-                EXZ[r][e] = EXZn[r][e];
-            }
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) W[r][q] = Wn[r][q];
-#pragma unroll
-        for (int y = 0; y <= R; ++y)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                V[y][q] = Vn[y][q];
-                EYZ[y][q] = EYZn[y][q];
-            }
+        for (int r = 0; r < R; ++r) Q::st(nu + o + r * sj, out[r]);
+        smag_carry<C, R>(L, EXZn, EYZn, U, V, W, EXZ, EYZ);
     }
 }
 
@@ -1189,8 +1216,11 @@ cudaError_t smag_launch(int dtype, const kl_grid &g, const void *u, const void *
         switch (dtype) {
         case KL_F64: smag_kernel4<double, double, 1><<<grid, block, 0, s>>>(a); break;
         case KL_F32:
-            if (R == 2) smag_kernel4<float, float, 2><<<grid, block, 0, s>>>(a);
-            else smag_kernel4<float, float, 1><<<grid, block, 0, s>>>(a);
+            if (R == 2) {
+                smag_kernel4<float, float, 2><<<grid, block, 0, s>>>(a);
+            } else {
+                smag_kernel4<float, float, 1><<<grid, block, 0, s>>>(a);
+            }
             break;
         case KL_BF16:
             if (R == 2) smag_kernel4<__nv_bfloat16, float, 2><<<grid, block, 0, s>>>(a);

@@ -155,3 +155,30 @@ def test_cs_creates_no_table_and_scales_nu_by_cs_squared(dtype):
             assert np.abs(r - res[0] * (cs / 0.1) ** 2).max() <= tol * np.abs(r).max()
     finally:
         kl.kl_destroy(c)
+
+
+def test_two_row_kernel_agrees_with_the_one_row_kernel(ctx):
+    """f32 with an even ny runs two rows per thread, an odd ny one row per
+    thread.  The same values enter the same expressions; the compiler may
+    contract different products into FMAs in the two instances, so on the
+    rows both grids share (away from the y boundary, whose periodic
+    neighbours differ) the viscosities agree to a few units in the last place
+    of f32."""
+    import torch
+    from paper_2303_12374_gb300 import kl
+    from paper_2303_12374_gb300.problem import Problem
+    nx, nz = 64, 40
+    f = make_inputs(nx, 25, nz, seed=31, walls=True, stretch=2.0)
+    res = []
+    for ny in (25, 24):
+        p = Problem(nx, ny, nz, g=3, dtype=1, walls=True, zh=f["zh"], dx=1.0 / nx, dy=1.0 / 25,
+                    nu=1e-3)
+        bufs = [p.upload(f[k][:, :ny, :]) for k in ("u", "v", "w")]
+        nu = p.empty()
+        kl.kl_fill_ghosts(ctx, p.dtype, p.grid, *[b.data_ptr() for b in bufs])
+        kl.kl_smagorinsky(ctx, p.dtype, p.grid, CS, *[b.data_ptr() for b in bufs], nu.data_ptr(),
+                          False)
+        torch.cuda.synchronize()
+        res.append(p.download(nu))
+    a, b = res[0][:, 1:23, :], res[1][:, 1:23, :]
+    assert np.abs(a - b).max() <= 4 * 2.0 ** -24 * np.abs(a).max()
